@@ -1,0 +1,232 @@
+"""Levenberg-Marquardt inversion of the Milne-Eddington model, FP64 (oracle).
+
+TEST INFRASTRUCTURE ONLY -- see the package docstring.
+
+The algorithm follows Sec. 2 (Eqs. 1-6), Sec. 4.2 (Table 2) and Sec. 4.4
+(Fig. 6) step by step, for many independent pixels at once (numpy arrays
+over pixels; each pixel keeps its own model, damping and iteration count,
+exactly as if it were inverted alone).
+
+Readings of points the paper leaves open or prints garbled:
+* Eqs. 3-4 print H_ij as a product of chi-square gradients; read as the
+  Gauss-Newton matrix A = J^T W J with diagonal A_ii (1 + eps), the form of
+  the Levenberg-Marquardt recipe the paper cites (Press et al.).
+* The step solves (A + eps diag(A)) delta = J^T W r; it is computed in the
+  Jacobi-scaled form (A_s + eps I) y = D^-1/2 g, delta = D^-1/2 y, with
+  D = diag(A), by SVD with singular values below 1e-12 * max zeroed (the
+  paper's Svdcmp/Svbksb).  A free parameter whose Jacobian column is exactly
+  zero (D_ii = 0) is held for that step.
+* Table 2's overlapping rows: on success eps > 1e4 -> /100,
+  1e-4 <= eps <= 1e4 -> /10, eps < 1e-4 -> /2; on failure eps < 1e-4 -> x100,
+  1e-4 <= eps <= 1e4 -> x2, eps > 1e4 -> x10; eps is kept in [1e-12, 1e12].
+* A trial is successful iff chi2_trial < chi2_best (strict); equality or a
+  non-finite chi2 is a failure (Fig. 6: derivatives only after a success).
+* Stopping (the paper runs a fixed count): a pixel is converged when a
+  successful step lowers chi2 by less than ``conv_rtol`` relative while the
+  step was close to Gauss-Newton (eps_used <= ``conv_eps``), or when eps
+  exceeds 1e12 after a failure (no decrease possible, status STALLED);
+  otherwise it stops at ``max_iter`` trial steps (status MAXITER).  The
+  iteration count is the number of trial solves (the paper's Svdcmp count).
+* Standard initial guess (the paper uses ANN/weak-field guesses):
+  B = 500 G, gamma = 60 deg, psi = 45 deg, eta0 = 10, dlambdaD = 35 mA,
+  a = 0.25, v = 0, S0 = 0.25 Ic, S1 = 0.75 Ic / mu, alpha = 1, where Ic is the
+  largest observed Stokes I sample.
+* Bounds after each step: B < 0 -> (-B, 180 - gamma); gamma reflected into
+  [0, 180] (the profiles depend on sin^2 gamma and cos gamma only);
+  psi mod 180; B <= 6000 G; eta0 in [0.01, 500]; dlambdaD in [5, 150] mA;
+  a in [0, 5]; |v| <= 20 km/s; S0, S1 in [0, 2].
+* Covariance: (J^T W J)^+ at the final model (eps = 0), computed in the
+  Jacobi-scaled form with the same SVD truncation, zero for held
+  parameters.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import me
+
+NPAR = 10
+DEFAULT_FREE = 0x1FF  # B..S1 free, alpha held
+
+CONVERGED, MAXITER, STALLED, BAD_INPUT, NAN_STATE = 0, 1, 2, 3, 4
+
+EPS_MIN, EPS_MAX = 1e-12, 1e12
+SVD_RCOND = 1e-12
+
+STANDARD_GUESS = np.array([500.0, 60.0, 45.0, 10.0, 35.0, 0.25, 0.0, 0.25, 0.75, 1.0])
+
+
+def chi2(obs, syn, w, nfree):
+    """Eq. 1: sum_ij (I_obs - I_syn)^2 w_ij^2 / sigma_ij^2 / (4L - F); the
+    combined factor w^2/sigma^2 is the ``w`` array."""
+    n_obs = obs.shape[-1]
+    r = obs - syn
+    return (w * r * r).sum(-1) / (n_obs - nfree)
+
+
+def eps_update(eps, success):
+    """Table 2: new damping from the old one and the outcome of the step."""
+    eps = np.asarray(eps, dtype=np.float64)
+    dec = np.where(eps > 1e4, eps / 100.0, np.where(eps >= 1e-4, eps / 10.0, eps / 2.0))
+    inc = np.where(eps < 1e-4, eps * 100.0, np.where(eps <= 1e4, eps * 2.0, eps * 10.0))
+    return np.clip(np.where(success, dec, inc), EPS_MIN, None)
+
+
+def standard_guess(obs, nfilt, mu=1.0):
+    ic = obs[:, :nfilt].max(axis=1)
+    m = np.tile(STANDARD_GUESS, (obs.shape[0], 1))
+    m[:, me.S0] = 0.25 * ic
+    m[:, me.S1] = 0.75 * ic / mu
+    return m
+
+
+def apply_bounds(m):
+    m = m.copy()
+    neg = m[:, me.B] < 0
+    m[neg, me.B] = -m[neg, me.B]
+    m[neg, me.GAMMA] = 180.0 - m[neg, me.GAMMA]
+    g = np.mod(m[:, me.GAMMA], 360.0)
+    m[:, me.GAMMA] = np.where(g > 180.0, 360.0 - g, g)
+    m[:, me.PSI] = np.mod(m[:, me.PSI], 180.0)
+    m[:, me.B] = np.minimum(m[:, me.B], 6000.0)
+    m[:, me.ETA0] = np.clip(m[:, me.ETA0], 0.01, 500.0)
+    m[:, me.DLD] = np.clip(m[:, me.DLD], 5.0, 150.0)
+    m[:, me.DAMP] = np.clip(m[:, me.DAMP], 0.0, 5.0)
+    m[:, me.VLOS] = np.clip(m[:, me.VLOS], -20.0, 20.0)
+    m[:, me.S0] = np.clip(m[:, me.S0], 0.0, 2.0)
+    m[:, me.S1] = np.clip(m[:, me.S1], 0.0, 2.0)
+    return m
+
+
+def normal_equations(J, r, w, free):
+    """A = J^T W J and g = J^T W r over the free parameters (Eqs. 2-4 read as
+    Gauss-Newton); held parameters get zero rows and columns."""
+    Jf = J * free[None, None, :]
+    A = np.einsum("poi,po,poj->pij", Jf, w, Jf)
+    g = np.einsum("poi,po,po->pi", Jf, w, r)
+    return A, g
+
+
+def _scaled(A, free):
+    d = np.diagonal(A, axis1=1, axis2=2)
+    held = (~free[None, :]) | ~(d > 0) | ~np.isfinite(d)
+    s = np.where(held, 0.0, 1.0 / np.sqrt(np.where(held, 1.0, d)))
+    As = A * s[:, :, None] * s[:, None, :]
+    return As, s, held
+
+
+def _svd_solve(Mx, b):
+    U, S, Vt = np.linalg.svd(Mx)
+    keep = S > SVD_RCOND * S[:, :1]
+    Sinv = np.where(keep, 1.0 / np.where(keep, S, 1.0), 0.0)
+    return np.einsum("pji,pj->pi", Vt, Sinv * np.einsum("pji,pj->pi", U, b))
+
+
+def damped_step(A, g, eps, free):
+    """Eqs. 4-5: delta solving (A + eps diag A) delta = g (Jacobi-scaled, SVD)."""
+    As, s, held = _scaled(A, free)
+    n = A.shape[-1]
+    Mx = As + eps[:, None, None] * np.eye(n)[None]
+    Mx[held] = 0.0                       # rows of held parameters
+    Mx = np.where(held[:, None, :], 0.0, Mx)
+    Mx = Mx + np.eye(n)[None] * held[:, :, None]
+    y = _svd_solve(Mx, np.where(held, 0.0, g * s))
+    return np.where(held, 0.0, s * y)
+
+
+def covariance(A, free):
+    """(J^T W J)^+ in parameter units, held parameters zero."""
+    As, s, held = _scaled(A, free)
+    n = A.shape[-1]
+    Mx = np.where(held[:, None, :] | held[:, :, None], 0.0, As)
+    U, S, Vt = np.linalg.svd(Mx)
+    keep = S > SVD_RCOND * S[:, :1]
+    Sinv = np.where(keep, 1.0 / np.where(keep, S, 1.0), 0.0)
+    P = np.einsum("pki,pk,pkj->pij", Vt, Sinv, Vt)
+    return P * s[:, :, None] * s[:, None, :]
+
+
+def invert(obs, w, filters, x, line, init=None, max_iter=50, conv_rtol=1e-4,
+           conv_eps=1.0, eps0=1.0, free_mask=DEFAULT_FREE, trace=False):
+    """Invert observed Stokes [npix, 4*nfilt] with weights w^2/sigma^2.
+
+    Returns a dict with params [npix,10], chi2 [npix], iters [npix],
+    status [npix], cov [npix,10,10], accepted [npix].
+    """
+    obs = np.asarray(obs, dtype=np.float64)
+    w = np.asarray(w, dtype=np.float64)
+    npix, n_obs = obs.shape
+    nfilt = n_obs // 4
+    mu = float(line.get("mu", 1.0))
+    free = np.array([(free_mask >> k) & 1 for k in range(NPAR)], dtype=bool)
+    nfree = int(free.sum())
+
+    bad = ~np.isfinite(obs).all(1) | ~np.isfinite(w).all(1) | ~(w.sum(1) > 0)
+    if init is None:
+        m = standard_guess(np.where(np.isfinite(obs), obs, 0.0), nfilt, mu)
+    else:
+        m = np.asarray(init, dtype=np.float64).copy()
+        bad |= ~np.isfinite(m).all(1)
+        m = np.where(np.isfinite(m), m, STANDARD_GUESS[None, :])
+    m[:, me.ALPHA] = 1.0
+    m = apply_bounds(m)
+    obs_s = np.where(bad[:, None], 0.0, obs)
+    w_s = np.where(bad[:, None], 0.0, w)
+
+    def model(mm, jac):
+        out = me.synth(mm, filters, x, line, jacobian=jac)
+        if jac:
+            s, J = out
+            return s.reshape(len(mm), -1), J.reshape(len(mm), n_obs, NPAR)
+        return out.reshape(len(mm), -1)
+
+    syn, J = model(m, True)
+    c2 = chi2(obs_s, syn, w_s, nfree)
+    A, g = normal_equations(J, obs_s - syn, w_s, free)
+    eps = np.full(npix, float(eps0))
+    iters = np.zeros(npix, dtype=np.int64)
+    nacc = np.zeros(npix, dtype=np.int64)
+    status = np.full(npix, MAXITER, dtype=np.int64)
+    status[bad] = BAD_INPUT
+    nan0 = ~bad & ~np.isfinite(c2)
+    status[nan0] = NAN_STATE
+    done = bad | nan0
+    hist = []
+
+    for _ in range(max_iter):
+        act = np.flatnonzero(~done)
+        if act.size == 0:
+            break
+        delta = damped_step(A[act], g[act], eps[act], free)
+        mt = apply_bounds(m[act] + delta)
+        st = model(mt, False)
+        ct = chi2(obs_s[act], st, w_s[act], nfree)
+        iters[act] += 1
+        ok = np.isfinite(ct) & (ct < c2[act])
+        eps_used = eps[act].copy()
+        eps[act] = eps_update(eps_used, ok)
+        acc = act[ok]
+        if acc.size:
+            rel = (c2[acc] - ct[ok]) / c2[acc]
+            m[acc] = mt[ok]
+            c2[acc] = ct[ok]
+            nacc[acc] += 1
+            sa, Ja = model(m[acc], True)
+            Aa, ga = normal_equations(Ja, obs_s[acc] - sa, w_s[acc], free)
+            A[acc], g[acc] = Aa, ga
+            conv = (rel < conv_rtol) & (eps_used[ok] <= conv_eps)
+            status[acc[conv]] = CONVERGED
+            done[acc[conv]] = True
+        rej = act[~ok]
+        stall = rej[eps[rej] >= EPS_MAX]
+        status[stall] = STALLED
+        done[stall] = True
+        if trace:
+            hist.append((act.size, acc.size))
+
+    cov = covariance(A, free)
+    out = {"params": m, "chi2": c2, "iters": iters, "status": status,
+           "cov": cov, "accepted": nacc}
+    if trace:
+        out["trace"] = hist
+    return out

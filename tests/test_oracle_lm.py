@@ -1,0 +1,156 @@
+"""Pins of the FP64 oracle's Levenberg-Marquardt inversion.
+
+Each test ties the oracle to something other than itself: the printed
+Table 2, closed-form linear least squares where the model is linear,
+noise-free round trips, chi-square statistics of Gaussian noise, a
+brute-force grid search, and the sample scatter of repeated noise draws.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import lm, me
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+X = W.wavelength_grid()
+T = W.hmi_filters(X)
+LINE = W.FE6173
+
+
+def _obs(n, seed, noise=True):
+    p = W.quiet_and_active_params(n, seed)
+    s = me.synth(p, T, X, LINE).reshape(n, -1)
+    nz = W.noise(n, s.shape[1], seed) if noise else np.zeros_like(s)
+    o, w = W.observe(s, p, nz)
+    return p, s, o, w
+
+
+def test_table2_golden():
+    rows = np.loadtxt(os.path.join(GOLD, "table2_eps.txt"))
+    got = lm.eps_update(rows[:, 0], rows[:, 1] > 0.5)
+    np.testing.assert_allclose(got, rows[:, 2], rtol=1e-12)
+
+
+def test_chi2_definition_eq1():
+    # (4L - F) normalisation with L = 6 positions and F = 9 free parameters
+    obs = np.ones((1, 24))
+    syn = np.zeros((1, 24))
+    w = np.full((1, 24), 4.0)
+    assert lm.chi2(obs, syn, w, 9)[0] == pytest.approx(24 * 4.0 / 15)
+
+
+def test_linear_parameters_closed_form():
+    """S0 and S1 enter the model linearly: with only they free, one undamped
+    Gauss-Newton step lands on the linear least-squares solution."""
+    p, s, o, w = _obs(16, 21)
+    init = p.copy()
+    init[:, 7] *= 0.5
+    init[:, 8] *= 1.4
+    free = (1 << 7) | (1 << 8)
+    r = lm.invert(o, w, T, X, LINE, init=init, max_iter=1, eps0=1e-12, free_mask=free)
+    base = p.copy()
+    base[:, 7], base[:, 8] = 1.0, 0.0
+    c0 = me.synth(base, T, X, LINE).reshape(16, -1)
+    base[:, 7], base[:, 8] = 0.0, 1.0
+    c1 = me.synth(base, T, X, LINE).reshape(16, -1)
+    for i in range(16):
+        A = np.stack([c0[i], c1[i]], 1) * np.sqrt(w[i])[:, None]
+        sol = np.linalg.lstsq(A, o[i] * np.sqrt(w[i]), rcond=None)[0]
+        np.testing.assert_allclose(r["params"][i, 7:9], sol, rtol=1e-9)
+
+
+def test_noise_free_round_trip():
+    p, s, o, w = _obs(24, 22, noise=False)
+    init = p.copy()
+    init[:, 0] = init[:, 0] * 1.05 + 10
+    init[:, 1] = np.clip(init[:, 1] + 3, 0, 180)
+    init[:, 3] *= 1.1
+    init[:, 6] += 0.2
+    r = lm.invert(o, w, T, X, LINE, init=init, max_iter=200, conv_rtol=1e-12)
+    assert np.median(r["chi2"]) < 1e-8
+    good = r["chi2"] < 1e-8
+    assert good.mean() > 0.9
+    strong = good & (p[:, 0] > 100) & (np.sin(np.radians(p[:, 1])) > 0.2)
+    np.testing.assert_allclose(r["params"][strong, 0], p[strong, 0], rtol=1e-4)
+    np.testing.assert_allclose(r["params"][strong, 1], p[strong, 1], atol=1e-3)
+    dpsi = np.abs((r["params"][strong, 2] - p[strong, 2] + 90.0) % 180.0 - 90.0)
+    assert dpsi.max() < 1e-3
+
+
+def test_chi2_statistics_with_noise():
+    """Gaussian noise of the stated sigma: E[chi2(true)] = 24/15 and at the
+    fitted minimum E[chi2] = (24 - 9)/15 = 1 (Eq. 1 normalisation)."""
+    p, s, o, w = _obs(256, 23)
+    c_true = lm.chi2(o, s, w, 9)
+    assert abs(c_true.mean() - 24 / 15) < 0.12
+    r = lm.invert(o, w, T, X, LINE, init=p, max_iter=60, conv_rtol=1e-8)
+    ok = r["status"] == lm.CONVERGED
+    assert ok.mean() > 0.8
+    assert np.all(r["chi2"] <= c_true + 1e-12)
+    assert abs(r["chi2"][ok].mean() - 1.0) < 0.12
+
+
+def test_minimum_vs_grid_search():
+    """A brute-force scan over (B, gamma, psi) around the LM result finds no
+    lower chi2 (other parameters at the LM values)."""
+    p, s, o, w = _obs(4, 24)
+    p[:, 0] = np.maximum(p[:, 0], 800.0)
+    s = me.synth(p, T, X, LINE).reshape(4, -1)
+    o, w = W.observe(s, p, W.noise(4, 24, 24))
+    r = lm.invert(o, w, T, X, LINE, init=p, max_iter=100, conv_rtol=1e-10)
+    for i in range(4):
+        m = r["params"][i]
+        grid = []
+        for dB in np.linspace(-30, 30, 7):
+            for dg in np.linspace(-3, 3, 7):
+                for dp in np.linspace(-3, 3, 7):
+                    q = m.copy()
+                    q[0] += dB
+                    q[1] += dg
+                    q[2] += dp
+                    grid.append(q)
+        grid = np.array(grid)
+        c = lm.chi2(o[i:i + 1].repeat(len(grid), 0), me.synth(grid, T, X, LINE).reshape(len(grid), -1),
+                    w[i:i + 1].repeat(len(grid), 0), 9)
+        assert r["chi2"][i] <= c.min() + 1e-9
+
+
+def test_covariance_matches_noise_scatter():
+    p = W.quiet_and_active_params(1, 25)
+    p[0, 0], p[0, 1], p[0, 3] = 1500.0, 50.0, 8.0
+    s = me.synth(p, T, X, LINE).reshape(1, -1)
+    n = 300
+    P = np.repeat(p, n, 0)
+    S = np.repeat(s, n, 0)
+    o, w = W.observe(S, P, W.noise(n, 24, 26))
+    r = lm.invert(o, w, T, X, LINE, init=P, max_iter=60, conv_rtol=1e-9)
+    ok = r["status"] == lm.CONVERGED
+    assert ok.mean() > 0.9
+    for q in (0, 1, 6):
+        sd = r["params"][ok, q].std()
+        pred = np.sqrt(r["cov"][ok, q, q].mean())
+        assert 0.75 < sd / pred < 1.3, (q, sd, pred)
+
+
+def test_bad_input_status():
+    p, s, o, w = _obs(4, 27)
+    o[1, 3] = np.nan
+    w[2] = 0.0
+    r = lm.invert(o, w, T, X, LINE, max_iter=5)
+    assert r["status"][1] == lm.BAD_INPUT and r["status"][2] == lm.BAD_INPUT
+    assert r["status"][0] != lm.BAD_INPUT
+
+
+def test_bounds_equivalences():
+    """Negative B with gamma -> 180 - gamma and reflected gamma give the same
+    Stokes vector, so the bounds never change the model."""
+    p = W.quiet_and_active_params(6, 28)
+    q = p.copy()
+    q[:, 0] = -q[:, 0]
+    q[:, 1] = 180.0 - q[:, 1]
+    np.testing.assert_allclose(me.synth(lm.apply_bounds(q), T, X, LINE), me.synth(p, T, X, LINE), atol=1e-13)
+    q = p.copy()
+    q[:, 1] = -q[:, 1]
+    np.testing.assert_allclose(me.synth(q, T, X, LINE), me.synth(lm.apply_bounds(q), T, X, LINE), atol=1e-13)
