@@ -1,0 +1,150 @@
+/*
+ * vfisv.h -- C ABI of the GB300 Milne-Eddington Stokes inversion library
+ * (libvfisv.so).
+ *
+ * The library computes, for many independent pixels, the per-pixel hot path
+ * of the VFISV inversion (Borrero et al., "VFISV: Very Fast Inversion of the
+ * Stokes Vector for the Helioseismic and Magnetic Imager"):
+ *   - Milne-Eddington (Unno-Rachkovsky) synthesis of (I, Q, U, V) of a
+ *     normal Zeeman triplet (Sec. 3.1, Eq. 7) from the Voigt and
+ *     Faraday-Voigt functions (Sec. 3.2, Eqs. 8-9), convolved with the
+ *     instrument's filter transmission profiles;
+ *   - its analytic Jacobian (Sec. 4.4);
+ *   - Levenberg-Marquardt minimisation of chi-square (Sec. 2, Eqs. 1-6;
+ *     Sec. 4.2, Table 2; Sec. 4.4, Fig. 6);
+ *   - the learned initial guess (Sec. 5) as a 24-256-256-256-11 network.
+ *
+ * Conventions shared by every entry point
+ *   - Pointers may be device memory or host memory (pageable or pinned);
+ *     the library detects which.  Host buffers are staged through device
+ *     workspaces owned by the handle and the call returns after the results
+ *     are back in host memory.  With device buffers the call is
+ *     asynchronous on `stream`.
+ *   - All arrays are C-contiguous, caller-owned; the library never frees or
+ *     retains caller memory beyond the call.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).
+ *   - Return value: VFISV_OK (0) or a negative VFISV_E_* code.  Problems
+ *     of single pixels never fail a call; they are reported per pixel in
+ *     `status_out`.
+ *
+ * Parameter vector of one pixel, float32[10], in this order (Sec. 2 with
+ * the macroturbulence dropped):
+ *   0 B [G]   1 gamma [deg]   2 psi [deg]   3 eta0   4 dlambdaD [mA]
+ *   5 a       6 v_los [km/s, positive = redshift]    7 S0   8 S1
+ *   9 alpha (magnetic filling factor)
+ * Observables of one pixel, float32[4][nfilt]: Stokes I, Q, U, V at each
+ * filter position, in that order.
+ */
+#ifndef VFISV_H
+#define VFISV_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define VFISV_NPARAM 10
+
+enum {
+  VFISV_OK = 0,
+  VFISV_E_ARG = -1,         /* null pointer or invalid argument value */
+  VFISV_E_SIZE = -2,        /* a size is out of the supported range */
+  VFISV_E_UNSUPPORTED = -3, /* nfilt not compiled into this kernel */
+  VFISV_E_CUDA = -4,        /* a CUDA runtime call failed */
+  VFISV_E_DEVICE = -5,      /* a kernel reported an internal error */
+  VFISV_E_NOMEM = -6        /* a workspace allocation failed */
+};
+
+/* Per-pixel status codes written to status_out. */
+enum {
+  VFISV_PIX_CONVERGED = 0, /* chi2 stopped decreasing (see vfisv_config) */
+  VFISV_PIX_MAXITER = 1,   /* iteration cap reached first */
+  VFISV_PIX_STALLED = 2,   /* damping exceeded 1e12: no decrease possible */
+  VFISV_PIX_BAD_INPUT = 3, /* non-finite observable, weight or initial model,
+                              or all weights zero; outputs hold the guess */
+  VFISV_PIX_NAN_STATE = 4  /* synthesis at the initial model not finite */
+};
+
+/* A normal Zeeman triplet (Sec. 3.1).  The sigma components sit at
+ * +-dlambda_B = +-4.66685e-10 * geff * lambda0_A^2 * B  [mA]  (Eq. 7), the
+ * Doppler shift is lambda0 * v / c.  mu is the heliocentric angle cosine
+ * multiplying S1 in the Milne-Eddington solution. */
+typedef struct {
+  double lambda0_A;
+  double geff;
+  double mu;
+} vfisv_line;
+
+/* Levenberg-Marquardt controls (Sec. 4.2).
+ *   max_iter   cap on trial steps (solves) per pixel; the paper runs a fixed
+ *              count (30) -- here a pixel also stops when converged.
+ *   free_mask  bit p set = parameter p is free; bit 9 (alpha) must be clear
+ *              (the filling factor is held at 1 in the inversion).
+ *   conv_rtol  converged when a successful step lowers chi2 by less than
+ *              conv_rtol relative while the damping used was <= conv_eps.
+ *   eps0       initial damping.
+ * vfisv_config_default() fills: 50, 0x1FF, 1e-4, 1.0, 1.0. */
+typedef struct {
+  int32_t max_iter;
+  uint32_t free_mask;
+  double conv_rtol;
+  double conv_eps;
+  double eps0;
+} vfisv_config;
+
+typedef struct vfisv_handle vfisv_handle;
+
+/* Create a handle bound to CUDA device `device` (it becomes current on the
+ * calling thread for every call made with the handle).  Owns workspaces,
+ * the work-queue counter and the Weideman coefficients. */
+int vfisv_create(vfisv_handle** out, int device);
+void vfisv_destroy(vfisv_handle* h);
+void vfisv_config_default(vfisv_config* cfg);
+const char* vfisv_strerror(int code);
+
+/* Synchronise `stream` and report any error a kernel of this handle flagged
+ * on the device since the last check (VFISV_E_DEVICE) or a CUDA error. */
+int vfisv_check(vfisv_handle* h, void* stream);
+
+/* Milne-Eddington synthesis through the filters (Secs. 3.1-3.2).
+ *   params   float32[npix][10]   model (alpha in [0,1] honoured)
+ *   filters  float32[nfilt][nlam] transmission T_k(x_i)
+ *   wl_mA    float32[nlam]       x_i = lambda_i - lambda0 in mA
+ *   line     the triplet
+ *   stokes   float32[npix][4][nfilt] output: S_jk = sum_i T_k(x_i) S_j(x_i)
+ * 1 <= nfilt <= 8, 1 <= nlam <= 4096, npix >= 0 (0 is a no-op). */
+int vfisv_synth(vfisv_handle* h, const float* params, int64_t npix,
+                const float* filters, int32_t nfilt, const float* wl_mA,
+                int32_t nlam, const vfisv_line* line, float* stokes,
+                void* stream);
+
+/* Levenberg-Marquardt inversion of every pixel (Secs. 2 and 4).
+ *   obs        float32[npix][4][nfilt] observed Stokes vector
+ *   weights    w_ij^2 / sigma_ij^2 of Eq. 1: float32[npix][4][nfilt] if
+ *              weights_per_pixel, else float32[4][nfilt] for all pixels;
+ *              zero marks missing data (Sec. 4.3)
+ *   init       float32[npix][10] initial models, or NULL for the standard
+ *              guess B=500 G, gamma=60, psi=45, eta0=10, dlambdaD=35 mA,
+ *              a=0.25, v=0, S0=0.25 Ic, S1=0.75 Ic/mu (Ic = largest I sample)
+ *   params_out float32[npix][10] best model (alpha = 1)
+ *   chi2_out   float32[npix]     Eq. 1 at params_out (dof = 4 nfilt - F)
+ *   iters_out  int32[npix]       trial steps taken
+ *   status_out int32[npix]       VFISV_PIX_*
+ *   cov_out    float32[npix][10][10] (J^T W J)^+ at params_out in parameter
+ *              units (zero rows/columns for held parameters), or NULL
+ * Only nfilt == 6 is compiled; 1 <= nlam <= 4096. */
+int vfisv_invert(vfisv_handle* h, const float* obs, const float* weights,
+                 int32_t weights_per_pixel, const float* filters,
+                 int32_t nfilt, const float* wl_mA, int32_t nlam,
+                 const vfisv_line* line, const float* init,
+                 const vfisv_config* cfg, int64_t npix, float* params_out,
+                 float* chi2_out, int32_t* iters_out, int32_t* status_out,
+                 float* cov_out, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VFISV_H */

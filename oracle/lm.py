@@ -18,7 +18,10 @@ Readings of points the paper leaves open or prints garbled:
   zero (D_ii = 0) is held for that step.
 * Table 2's overlapping rows: on success eps > 1e4 -> /100,
   1e-4 <= eps <= 1e4 -> /10, eps < 1e-4 -> /2; on failure eps < 1e-4 -> x100,
-  1e-4 <= eps <= 1e4 -> x2, eps > 1e4 -> x10; eps is kept in [1e-12, 1e12].
+  1e-4 <= eps <= 1e4 -> x2, eps > 1e4 -> x10.  The paper gives no floor; eps
+  is kept >= 1e-9, so the Jacobi-scaled damped matrix (unit diagonal) has
+  every eigenvalue >= 1e-9 and the step never needs truncation; eps > 1e12
+  ends the iteration (no decrease is possible).
 * A trial is successful iff chi2_trial < chi2_best (strict); equality or a
   non-finite chi2 is a failure (Fig. 6: derivatives only after a success).
 * Stopping (the paper runs a fixed count): a pixel is converged when a
@@ -50,7 +53,7 @@ DEFAULT_FREE = 0x1FF  # B..S1 free, alpha held
 
 CONVERGED, MAXITER, STALLED, BAD_INPUT, NAN_STATE = 0, 1, 2, 3, 4
 
-EPS_MIN, EPS_MAX = 1e-12, 1e12
+EPS_MIN, EPS_MAX = 1e-9, 1e12
 SVD_RCOND = 1e-12
 
 STANDARD_GUESS = np.array([500.0, 60.0, 45.0, 10.0, 35.0, 0.25, 0.0, 0.25, 0.75, 1.0])

@@ -1,0 +1,231 @@
+"""Python binding of libvfisv.so, the GB300 Milne-Eddington Stokes inversion.
+
+Argument marshalling only: every step of synthesis and inversion runs in the
+library's CUDA kernels.  Functions carry the C-ABI names of ``include/vfisv.h``
+and accept numpy arrays (host memory, staged by the library) or torch tensors
+(device memory, used in place, asynchronous on the current torch stream).
+Importing this module does not load the library; the first call does, and
+raises if ``libvfisv.so`` has not been built (``python -m
+paper_0901_2702_gb300.build`` or ``__graft_entry__.build()``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+__all__ = [
+    "vfisv_create", "vfisv_destroy", "vfisv_synth", "vfisv_invert", "vfisv_check",
+    "vfisv_strerror", "vfisv_config_default", "VfisvError", "library_path", "load",
+]
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "_build", "libvfisv.so")
+_lib = None
+
+VFISV_OK = 0
+PIX_CONVERGED, PIX_MAXITER, PIX_STALLED, PIX_BAD_INPUT, PIX_NAN_STATE = range(5)
+
+
+class VfisvError(RuntimeError):
+    def __init__(self, code, where):
+        super().__init__(f"{where}: {vfisv_strerror(code)} ({code})")
+        self.code = code
+
+
+class vfisv_line(ctypes.Structure):
+    _fields_ = [("lambda0_A", ctypes.c_double), ("geff", ctypes.c_double), ("mu", ctypes.c_double)]
+
+
+class vfisv_config(ctypes.Structure):
+    _fields_ = [("max_iter", ctypes.c_int32), ("free_mask", ctypes.c_uint32),
+                ("conv_rtol", ctypes.c_double), ("conv_eps", ctypes.c_double),
+                ("eps0", ctypes.c_double)]
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def load():
+    """Load libvfisv.so (raises if it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_LIB_PATH):
+        raise RuntimeError(f"libvfisv.so not built: {_LIB_PATH} is missing; run "
+                           "__graft_entry__.build() or python -m paper_0901_2702_gb300.build")
+    lib = ctypes.CDLL(_LIB_PATH)
+    P, I32, I64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+    lib.vfisv_create.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int]
+    lib.vfisv_create.restype = ctypes.c_int
+    lib.vfisv_destroy.argtypes = [P]
+    lib.vfisv_destroy.restype = None
+    lib.vfisv_config_default.argtypes = [ctypes.POINTER(vfisv_config)]
+    lib.vfisv_config_default.restype = None
+    lib.vfisv_strerror.argtypes = [ctypes.c_int]
+    lib.vfisv_strerror.restype = ctypes.c_char_p
+    lib.vfisv_check.argtypes = [P, P]
+    lib.vfisv_check.restype = ctypes.c_int
+    lib.vfisv_synth.argtypes = [P, P, I64, P, I32, P, I32, ctypes.POINTER(vfisv_line), P, P]
+    lib.vfisv_synth.restype = ctypes.c_int
+    lib.vfisv_invert.argtypes = [P, P, P, I32, P, I32, P, I32, ctypes.POINTER(vfisv_line), P,
+                                 ctypes.POINTER(vfisv_config), I64, P, P, P, P, P, P]
+    lib.vfisv_invert.restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def vfisv_strerror(code: int) -> str:
+    try:
+        return load().vfisv_strerror(int(code)).decode()
+    except RuntimeError:
+        return f"error {code}"
+
+
+def _check(code, where):
+    if code != VFISV_OK:
+        raise VfisvError(code, where)
+
+
+class Handle:
+    """Owns a vfisv_handle (workspaces, work queue, constants) on one device."""
+
+    def __init__(self, device: int = 0):
+        self._lib = load()
+        h = ctypes.c_void_p()
+        _check(self._lib.vfisv_create(ctypes.byref(h), int(device)), "vfisv_create")
+        self.ptr = h
+        self.device = int(device)
+
+    def close(self):
+        if getattr(self, "ptr", None):
+            self._lib.vfisv_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def vfisv_create(device: int = 0) -> Handle:
+    return Handle(device)
+
+
+def vfisv_destroy(h: Handle) -> None:
+    h.close()
+
+
+def vfisv_config_default(**overrides) -> vfisv_config:
+    c = vfisv_config()
+    load().vfisv_config_default(ctypes.byref(c))
+    for k, v in overrides.items():
+        setattr(c, k, v)
+    return c
+
+
+def _line(line) -> vfisv_line:
+    if isinstance(line, vfisv_line):
+        return line
+    return vfisv_line(float(line["lambda0_A"]), float(line["geff"]), float(line.get("mu", 1.0)))
+
+
+def _is_torch(x):
+    return type(x).__module__.startswith("torch")
+
+
+def _ptr(x, dtype):
+    """(pointer, keep-alive object) of a C-contiguous array of `dtype`."""
+    if x is None:
+        return None, None
+    if _is_torch(x):
+        import torch
+        tdt = {np.float32: torch.float32, np.int32: torch.int32}[dtype]
+        if x.dtype != tdt or not x.is_contiguous():
+            x = x.to(tdt).contiguous()
+        return x.data_ptr(), x
+    a = np.ascontiguousarray(x, dtype=dtype)
+    return a.ctypes.data, a
+
+
+def _stream(ref, stream):
+    if stream is not None:
+        return int(getattr(stream, "cuda_stream", stream))
+    if _is_torch(ref) and ref.is_cuda:
+        import torch
+        return torch.cuda.current_stream(ref.device).cuda_stream
+    return 0
+
+
+def _empty(ref, shape, dtype):
+    if _is_torch(ref):
+        import torch
+        tdt = {np.float32: torch.float32, np.int32: torch.int32}[dtype]
+        return torch.empty(shape, dtype=tdt, device=ref.device)
+    return np.empty(shape, dtype=dtype)
+
+
+def vfisv_check(h: Handle, stream=None) -> None:
+    _check(load().vfisv_check(h.ptr, ctypes.c_void_p(_stream(None, stream))), "vfisv_check")
+
+
+def vfisv_synth(h: Handle, params, filters, wl_mA, line, stokes=None, stream=None):
+    """Filtered Stokes vector [npix, 4, nfilt] of models params [npix, 10]."""
+    npix = int(params.shape[0])
+    nfilt, nlam = int(filters.shape[0]), int(filters.shape[1])
+    if stokes is None:
+        stokes = _empty(params, (npix, 4, nfilt), np.float32)
+    pp, k1 = _ptr(params, np.float32)
+    fp, k2 = _ptr(filters, np.float32)
+    wp, k3 = _ptr(wl_mA, np.float32)
+    sp, k4 = _ptr(stokes, np.float32)
+    ln = _line(line)
+    rc = load().vfisv_synth(h.ptr, pp, npix, fp, nfilt, wp, nlam, ctypes.byref(ln), sp,
+                            ctypes.c_void_p(_stream(params, stream)))
+    _check(rc, "vfisv_synth")
+    if k4 is not stokes and not _is_torch(stokes):
+        stokes[...] = k4
+    return stokes
+
+
+def vfisv_invert(h: Handle, obs, weights, filters, wl_mA, line, init=None, config=None,
+                 want_cov=True, out=None, stream=None):
+    """Levenberg-Marquardt inversion of obs [npix, 4*nfilt] (or [npix, 4, nfilt]).
+
+    weights: [npix, 4*nfilt] per pixel or [4*nfilt] for all pixels (w^2/sigma^2).
+    Returns dict(params, chi2, iters, status, cov) in the memory kind of obs.
+    """
+    npix = int(obs.shape[0])
+    nfilt, nlam = int(filters.shape[0]), int(filters.shape[1])
+    per_pixel = 1 if (len(weights.shape) >= 2 and int(weights.shape[0]) == npix and
+                      int(np.prod(weights.shape)) == npix * 4 * nfilt) else 0
+    cfg = config if isinstance(config, vfisv_config) else vfisv_config_default(**(config or {}))
+    if out is None:
+        out = {"params": _empty(obs, (npix, 10), np.float32),
+               "chi2": _empty(obs, (npix,), np.float32),
+               "iters": _empty(obs, (npix,), np.int32),
+               "status": _empty(obs, (npix,), np.int32),
+               "cov": _empty(obs, (npix, 10, 10), np.float32) if want_cov else None}
+    op, k1 = _ptr(obs, np.float32)
+    wp, k2 = _ptr(weights, np.float32)
+    fp, k3 = _ptr(filters, np.float32)
+    lp, k4 = _ptr(wl_mA, np.float32)
+    ip, k5 = _ptr(init, np.float32)
+    pp, k6 = _ptr(out["params"], np.float32)
+    cp, k7 = _ptr(out["chi2"], np.float32)
+    tp, k8 = _ptr(out["iters"], np.int32)
+    sp, k9 = _ptr(out["status"], np.int32)
+    vp, k10 = _ptr(out.get("cov"), np.float32)
+    ln = _line(line)
+    rc = load().vfisv_invert(h.ptr, op, wp, per_pixel, fp, nfilt, lp, nlam, ctypes.byref(ln), ip,
+                             ctypes.byref(cfg), npix, pp, cp, tp, sp, vp,
+                             ctypes.c_void_p(_stream(obs, stream)))
+    _check(rc, "vfisv_invert")
+    for key, k in (("params", k6), ("chi2", k7), ("iters", k8), ("status", k9), ("cov", k10)):
+        dst = out.get(key)
+        if dst is not None and not _is_torch(dst) and k is not dst:
+            dst[...] = k
+    return out

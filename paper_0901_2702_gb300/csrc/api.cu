@@ -1,0 +1,371 @@
+// C ABI of libvfisv.so: argument checks, host/device pointer staging,
+// workspaces, and the Weideman coefficients.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <vector>
+
+#include "common.cuh"
+#include "vfisv.h"
+
+using namespace vfisv;
+
+struct vfisv_handle {
+  int device = 0;
+  Weideman W{};
+  void* ws = nullptr;      // device workspace: error word, queue, table, scratch
+  size_t ws_bytes = 0;
+  void* stage = nullptr;   // device staging for host buffers
+  size_t stage_bytes = 0;
+};
+
+namespace {
+
+constexpr size_t kAlign = 256;
+inline size_t up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
+
+// Weideman (1994): w(z) = 1/(sqrt(pi)(L - iz)) + 2/(L - iz)^2 sum_{n>=0} a_{n+1} Z^n,
+// Z = (L + iz)/(L - iz).  The a_n are the Fourier coefficients of
+// f(theta) = (L^2 + t^2) exp(-t^2), t = L tan(theta/2), obtained here by the
+// trapezoidal rule on a uniform theta grid (spectrally accurate for this
+// smooth periodic f), in double precision.
+Weideman weideman_coefficients() {
+  Weideman W{};
+  const int N = kWeidN;
+  const double L = sqrt(N / sqrt(2.0));
+  const int M = 64 * N;
+  const double pi = 3.14159265358979323846;
+  std::vector<double> th(M), f(M);
+  for (int j = 0; j < M; ++j) {
+    th[j] = -pi + 2.0 * pi * j / M;
+    if (j == 0) {
+      f[j] = 0.0;  // t = -infinity
+    } else {
+      const double t = L * tan(0.5 * th[j]);
+      f[j] = (L * L + t * t) * exp(-t * t);
+    }
+  }
+  W.L = (float)L;
+  W.a[0] = 0.0f;
+  for (int n = 1; n <= N; ++n) {
+    double s = 0.0;
+    for (int j = 0; j < M; ++j) s += f[j] * cos(n * th[j]);
+    W.a[n] = (float)(s / M);
+  }
+  return W;
+}
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+int grow(void** buf, size_t* have, size_t need) {
+  if (*have >= need) return VFISV_OK;
+  if (*buf) {
+    cudaDeviceSynchronize();
+    cudaFree(*buf);
+    *buf = nullptr;
+    *have = 0;
+  }
+  if (cudaMalloc(buf, need) != cudaSuccess) {
+    cudaGetLastError();
+    *buf = nullptr;
+    return VFISV_E_NOMEM;
+  }
+  *have = need;
+  return VFISV_OK;
+}
+
+LineK line_constants(const vfisv_line* l) {
+  LineK k;
+  // Eq. 7: dlambda_B [mA] = 4.66685e-10 g_eff lambda0[A]^2 B[G]
+  k.cB = (float)(4.66685e-10 * l->geff * l->lambda0_A * l->lambda0_A);
+  // Doppler: lambda0 v / c with lambda0 in mA and c in km/s
+  k.cv = (float)(l->lambda0_A * 1.0e3 / 299792.458);
+  k.mu = (float)l->mu;
+  return k;
+}
+
+bool line_ok(const vfisv_line* l) {
+  return l && isfinite(l->lambda0_A) && l->lambda0_A > 0 && isfinite(l->geff) &&
+         isfinite(l->mu) && l->mu > 0;
+}
+
+// A set of caller buffers, each either device memory (used in place) or
+// host memory (staged through the handle's staging area).
+struct Buf {
+  const void* user;
+  size_t bytes;
+  bool out;
+  bool host;
+  void* dev;
+};
+
+struct Staging {
+  std::vector<Buf> bufs;
+  void add(const void* p, size_t bytes, bool out) {
+    bufs.push_back(Buf{p, bytes, out, p && !is_device_ptr(p), nullptr});
+  }
+  int prepare(vfisv_handle* h, cudaStream_t s) {
+    size_t need = 0;
+    for (auto& b : bufs)
+      if (b.host && b.bytes) need += up(b.bytes);
+    int rc = grow(&h->stage, &h->stage_bytes, need > 0 ? need : 0);
+    if (rc) return rc;
+    size_t off = 0;
+    for (auto& b : bufs) {
+      if (!b.user) continue;
+      if (!b.host) {
+        b.dev = const_cast<void*>(b.user);
+        continue;
+      }
+      b.dev = (char*)h->stage + off;
+      off += up(b.bytes);
+      if (!b.out && b.bytes &&
+          cudaMemcpyAsync(b.dev, b.user, b.bytes, cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return VFISV_E_CUDA;
+    }
+    return VFISV_OK;
+  }
+  bool any_host() const {
+    for (auto& b : bufs)
+      if (b.host) return true;
+    return false;
+  }
+  int finish(cudaStream_t s) {
+    bool sync = false;
+    for (auto& b : bufs)
+      if (b.host && b.out && b.bytes) {
+        if (cudaMemcpyAsync(const_cast<void*>(b.user), b.dev, b.bytes, cudaMemcpyDeviceToHost,
+                            s) != cudaSuccess)
+          return VFISV_E_CUDA;
+        sync = true;
+      }
+    if (sync || any_host())
+      if (cudaStreamSynchronize(s) != cudaSuccess) return VFISV_E_CUDA;
+    return VFISV_OK;
+  }
+};
+
+// Workspace layout: [err int | queue u64 | pad] [table] [scratch]
+struct WsLayout {
+  size_t err = 0, queue = 64, table = 256, scratch = 0, total = 0;
+};
+
+WsLayout layout(int nf, int nlam, int64_t nslots) {
+  WsLayout L;
+  L.scratch = L.table + up((size_t)table_floats(nf, nlam) * sizeof(float));
+  L.total = L.scratch + up((size_t)kScratchPerSlot * (size_t)nslots * sizeof(float));
+  return L;
+}
+
+int set_device(vfisv_handle* h) {
+  return cudaSetDevice(h->device) == cudaSuccess ? VFISV_OK : VFISV_E_CUDA;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* vfisv_strerror(int code) {
+  switch (code) {
+    case VFISV_OK: return "ok";
+    case VFISV_E_ARG: return "invalid argument";
+    case VFISV_E_SIZE: return "size out of the supported range";
+    case VFISV_E_UNSUPPORTED: return "number of filters not compiled into this kernel";
+    case VFISV_E_CUDA: return "CUDA runtime error";
+    case VFISV_E_DEVICE: return "a kernel reported an internal error";
+    case VFISV_E_NOMEM: return "device workspace allocation failed";
+    default: return "unknown error";
+  }
+}
+
+void vfisv_config_default(vfisv_config* c) {
+  if (!c) return;
+  c->max_iter = 50;
+  c->free_mask = 0x1FFu;
+  c->conv_rtol = 1e-4;
+  c->conv_eps = 1.0;
+  c->eps0 = 1.0;
+}
+
+int vfisv_create(vfisv_handle** out, int device) {
+  if (!out) return VFISV_E_ARG;
+  *out = nullptr;
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess) {
+    cudaGetLastError();
+    return VFISV_E_CUDA;
+  }
+  if (device < 0 || device >= n) return VFISV_E_ARG;
+  vfisv_handle* h = new vfisv_handle();
+  h->device = device;
+  h->W = weideman_coefficients();
+  if (set_device(h) != VFISV_OK || invert_set_constants(h->W) != cudaSuccess) {
+    cudaGetLastError();
+    delete h;
+    return VFISV_E_CUDA;
+  }
+  *out = h;
+  return VFISV_OK;
+}
+
+void vfisv_destroy(vfisv_handle* h) {
+  if (!h) return;
+  cudaSetDevice(h->device);
+  cudaDeviceSynchronize();
+  if (h->ws) cudaFree(h->ws);
+  if (h->stage) cudaFree(h->stage);
+  delete h;
+}
+
+int vfisv_check(vfisv_handle* h, void* stream) {
+  if (!h) return VFISV_E_ARG;
+  if (set_device(h)) return VFISV_E_CUDA;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return VFISV_E_CUDA;
+  if (cudaGetLastError() != cudaSuccess) return VFISV_E_CUDA;
+  if (!h->ws) return VFISV_OK;
+  int e = 0;
+  if (cudaMemcpy(&e, h->ws, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return VFISV_E_CUDA;
+  if (e) {
+    cudaMemset(h->ws, 0, sizeof(int));
+    return VFISV_E_DEVICE;
+  }
+  return VFISV_OK;
+}
+
+int vfisv_synth(vfisv_handle* h, const float* params, int64_t npix, const float* filters,
+                int32_t nfilt, const float* wl_mA, int32_t nlam, const vfisv_line* line,
+                float* stokes, void* stream) {
+  if (!h || !params || !filters || !wl_mA || !stokes || !line_ok(line)) return VFISV_E_ARG;
+  if (npix < 0 || nfilt < 1 || nlam < 1 || nlam > 4096) return VFISV_E_SIZE;
+  if (nfilt > 8) return VFISV_E_UNSUPPORTED;
+  if (npix == 0) return VFISV_OK;
+  if (set_device(h)) return VFISV_E_CUDA;
+  cudaStream_t s = (cudaStream_t)stream;
+  WsLayout L = layout(nfilt, nlam, 0);
+  if (h->ws_bytes < L.total) {
+    int rc = grow(&h->ws, &h->ws_bytes, L.total);
+    if (rc) return rc;
+    if (cudaMemsetAsync(h->ws, 0, 64, s) != cudaSuccess) return VFISV_E_CUDA;
+  }
+  Staging st;
+  st.add(params, (size_t)npix * 10 * sizeof(float), false);
+  st.add(filters, (size_t)nfilt * nlam * sizeof(float), false);
+  st.add(wl_mA, (size_t)nlam * sizeof(float), false);
+  st.add(stokes, (size_t)npix * 4 * nfilt * sizeof(float), true);
+  int rc = st.prepare(h, s);
+  if (rc) return rc;
+  char* ws = (char*)h->ws;
+  float* table = (float*)(ws + L.table);
+  if (launch_pack_table((const float*)st.bufs[1].dev, nfilt, (const float*)st.bufs[2].dev,
+                        nlam, table, s) != cudaSuccess)
+    return VFISV_E_CUDA;
+  SynthArgs a;
+  a.params = (const float*)st.bufs[0].dev;
+  a.npix = npix;
+  a.table = table;
+  a.nlam = nlam;
+  a.stokes = (float*)st.bufs[3].dev;
+  a.err = (int*)(ws + L.err);
+  a.W = h->W;
+  a.lk = line_constants(line);
+  if (launch_synth(a, nfilt, s) != cudaSuccess) return VFISV_E_CUDA;
+  return st.finish(s);
+}
+
+int vfisv_invert(vfisv_handle* h, const float* obs, const float* weights,
+                 int32_t weights_per_pixel, const float* filters, int32_t nfilt,
+                 const float* wl_mA, int32_t nlam, const vfisv_line* line, const float* init,
+                 const vfisv_config* cfg, int64_t npix, float* params_out, float* chi2_out,
+                 int32_t* iters_out, int32_t* status_out, float* cov_out, void* stream) {
+  if (!h || !obs || !weights || !filters || !wl_mA || !cfg || !params_out || !chi2_out ||
+      !iters_out || !status_out || !line_ok(line))
+    return VFISV_E_ARG;
+  if (npix < 0 || nfilt < 1 || nlam < 1 || nlam > 4096) return VFISV_E_SIZE;
+  if (nfilt != 6) return VFISV_E_UNSUPPORTED;
+  if (cfg->max_iter < 0 || (cfg->free_mask & ~0x1FFu) || !(cfg->conv_rtol >= 0) ||
+      !(cfg->conv_eps >= 0) || !(cfg->eps0 > 0) || !isfinite(cfg->eps0))
+    return VFISV_E_ARG;
+  const int nfree = __builtin_popcount(cfg->free_mask);
+  if (4 * nfilt - nfree <= 0) return VFISV_E_ARG;
+  if (npix == 0) return VFISV_OK;
+  if (set_device(h)) return VFISV_E_CUDA;
+  cudaStream_t s = (cudaStream_t)stream;
+
+  int64_t nslots = 0;
+  int grid = 0, block = 0;
+  size_t smem = 0;
+  if (invert_slots(nfilt, nlam, npix, &nslots, &grid, &block, &smem) != cudaSuccess) {
+    cudaGetLastError();
+    return VFISV_E_CUDA;
+  }
+  WsLayout L = layout(nfilt, nlam, nslots);
+  if (h->ws_bytes < L.total) {
+    int rc = grow(&h->ws, &h->ws_bytes, L.total);
+    if (rc) return rc;
+    if (cudaMemsetAsync(h->ws, 0, 64, s) != cudaSuccess) return VFISV_E_CUDA;
+  }
+  const int nobs = 4 * nfilt;
+  Staging st;
+  st.add(obs, (size_t)npix * nobs * sizeof(float), false);
+  st.add(weights, (size_t)(weights_per_pixel ? npix : 1) * nobs * sizeof(float), false);
+  st.add(filters, (size_t)nfilt * nlam * sizeof(float), false);
+  st.add(wl_mA, (size_t)nlam * sizeof(float), false);
+  st.add(init, init ? (size_t)npix * 10 * sizeof(float) : 0, false);
+  st.add(params_out, (size_t)npix * 10 * sizeof(float), true);
+  st.add(chi2_out, (size_t)npix * sizeof(float), true);
+  st.add(iters_out, (size_t)npix * sizeof(int32_t), true);
+  st.add(status_out, (size_t)npix * sizeof(int32_t), true);
+  st.add(cov_out, cov_out ? (size_t)npix * 100 * sizeof(float) : 0, true);
+  int rc = st.prepare(h, s);
+  if (rc) return rc;
+  char* ws = (char*)h->ws;
+  float* table = (float*)(ws + L.table);
+  if (launch_pack_table((const float*)st.bufs[2].dev, nfilt, (const float*)st.bufs[3].dev,
+                        nlam, table, s) != cudaSuccess)
+    return VFISV_E_CUDA;
+  if (cudaMemsetAsync(ws + L.queue, 0, sizeof(unsigned long long), s) != cudaSuccess)
+    return VFISV_E_CUDA;
+  InvertArgs a;
+  a.obs = (const float*)st.bufs[0].dev;
+  a.w = (const float*)st.bufs[1].dev;
+  a.w_stride = weights_per_pixel ? nobs : 0;
+  a.init = (const float*)st.bufs[4].dev;
+  a.table = table;
+  a.nlam = nlam;
+  a.npix = npix;
+  a.params_out = (float*)st.bufs[5].dev;
+  a.chi2_out = (float*)st.bufs[6].dev;
+  a.iters_out = (int32_t*)st.bufs[7].dev;
+  a.status_out = (int32_t*)st.bufs[8].dev;
+  a.cov_out = (float*)st.bufs[9].dev;
+  a.scratch = (float*)(ws + L.scratch);
+  a.nslots = nslots;
+  a.queue = (unsigned long long*)(ws + L.queue);
+  a.err = (int*)(ws + L.err);
+  a.W = h->W;
+  a.lk = line_constants(line);
+  a.max_iter = cfg->max_iter;
+  a.free_mask = cfg->free_mask;
+  a.nfree = nfree;
+  a.conv_rtol = cfg->conv_rtol;
+  a.conv_eps = cfg->conv_eps;
+  a.eps0 = cfg->eps0;
+  if (launch_invert(a, nfilt, grid, block, smem, s) != cudaSuccess) return VFISV_E_CUDA;
+  if (a.cov_out &&
+      launch_covariance(a.cov_out, a.status_out, npix, cfg->free_mask, s) != cudaSuccess)
+    return VFISV_E_CUDA;
+  return st.finish(s);
+}
+
+}  // extern "C"

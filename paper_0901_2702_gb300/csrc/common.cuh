@@ -1,0 +1,155 @@
+// Shared device helpers: the filter/wavelength table staged into shared
+// memory by a TMA bulk copy, and kernel launch declarations.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "me_device.cuh"
+#include "vfisv.h"
+
+namespace vfisv {
+
+// Device error codes written to the handle's error word.
+enum : int { kDevErrNone = 0, kDevErrTableWait = 1 };
+
+// Filter table layout in global and shared memory: nlam rows of `stride`
+// floats {T_0(x_i), ..., T_{nf-1}(x_i), x_i, pad...}, then one row holding
+// tau_k = sum_i T_k(x_i).  stride = round_up(nf + 1, 4), so a row is a whole
+// number of 16-byte vectors.
+__host__ __device__ inline int table_stride(int nf) { return ((nf + 1) + 3) & ~3; }
+__host__ __device__ inline int table_floats(int nf, int nlam) {
+  return (nlam + 1) * table_stride(nf);
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// Copy `bytes` (multiple of 16, both addresses 16-byte aligned) from global
+// to this CTA's shared memory with one TMA bulk copy completing on an
+// mbarrier.  Every thread waits, with an iteration bound; returns false and
+// flags `err` if the copy did not complete in time.
+__device__ inline bool tma_load_table(float* sdst, const float* gsrc, uint32_t bytes,
+                                      uint64_t* mbar, int* err) {
+  const uint32_t bar = smem_u32(mbar);
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(1) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
+                 "r"(bytes)
+                 : "memory");
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, "
+        "[%3];" ::"r"(smem_u32(sdst)),
+        "l"(gsrc), "r"(bytes), "r"(bar)
+        : "memory");
+  }
+  uint32_t done = 0;
+  const long long t0 = clock64();
+  for (int it = 0; it < (1 << 22) && !done; ++it) {
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(0)
+        : "memory");
+    if (!done && clock64() - t0 > (1ll << 31)) break;  // ~1 s at 2 GHz
+  }
+  if (!done) {
+    atomicExch(err, kDevErrTableWait);
+    // give the copy in flight a last bounded chance to land before exit
+    for (int it = 0; it < (1 << 20) && !done; ++it) {
+      asm volatile(
+          "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+          " selp.u32 %0, 1, 0, p;\n}\n"
+          : "=r"(done)
+          : "r"(bar), "r"(0)
+          : "memory");
+    }
+    return false;
+  }
+  return true;
+}
+
+// Read one table row: the NF filter weights and the wavelength offset.
+template <int NF>
+__device__ __forceinline__ float load_row(const float* row, float (&T)[NF]) {
+  constexpr int S = ((NF + 1) + 3) & ~3;
+  float v[S];
+#pragma unroll
+  for (int j = 0; j < S; j += 4) {
+    const float4 q = *reinterpret_cast<const float4*>(row + j);
+    v[j] = q.x;
+    v[j + 1] = q.y;
+    v[j + 2] = q.z;
+    v[j + 3] = q.w;
+  }
+#pragma unroll
+  for (int k = 0; k < NF; ++k) T[k] = v[k];
+  return v[NF];
+}
+
+// ---------------------------------------------------------------------------
+// Host launchers (one translation unit each).
+
+struct SynthArgs {
+  const float* params;
+  int64_t npix;
+  const float* table;  // packed filter table in global memory
+  int nlam;
+  float* stokes;
+  int* err;
+  Weideman W;
+  LineK lk;
+};
+
+struct InvertArgs {
+  const float* obs;
+  const float* w;
+  int64_t w_stride;  // 4*nf when weights are per pixel, else 0
+  const float* init; // may be null: standard guess
+  const float* table;
+  int nlam;
+  int64_t npix;
+  float* params_out;
+  float* chi2_out;
+  int32_t* iters_out;
+  int32_t* status_out;
+  float* cov_out;    // may be null
+  float* scratch;    // [kScratchPerSlot][nslots]
+  int64_t nslots;
+  unsigned long long* queue;
+  int* err;
+  Weideman W;
+  LineK lk;
+  int max_iter;
+  uint32_t free_mask;
+  int nfree;
+  double conv_rtol;
+  double conv_eps;
+  double eps0;
+};
+
+constexpr int kScratchPerSlot = 45 + 9;  // packed J^T W J and J^T W r
+
+cudaError_t launch_pack_table(const float* filters, int nf, const float* wl, int nlam,
+                              float* table, cudaStream_t s);
+cudaError_t launch_synth(const SynthArgs& a, int nf, cudaStream_t s);
+// Persistent LM kernel: returns the number of resident slots it will use
+// for `npix` pixels (the scratch it needs) without launching when dry_run.
+cudaError_t invert_slots(int nf, int nlam, int64_t npix, int64_t* nslots, int* grid,
+                         int* block, size_t* smem);
+// Upload the Weideman coefficients to the LM kernel's constant bank on the
+// current device (once per device).
+cudaError_t invert_set_constants(const Weideman& W);
+cudaError_t launch_covariance(float* cov, const int32_t* status, int64_t npix,
+                              uint32_t free_mask, cudaStream_t s);
+cudaError_t launch_invert(const InvertArgs& a, int nf, int grid, int block, size_t smem,
+                          cudaStream_t s);
+
+}  // namespace vfisv

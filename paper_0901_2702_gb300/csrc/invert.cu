@@ -1,0 +1,600 @@
+// Persistent Levenberg-Marquardt kernel (Secs. 2 and 4): one pixel per
+// thread slot, pixels drawn from a global work queue so that converged
+// pixels retire and their slots refill.  Each iteration:
+//   1. FP64 damped solve of the Jacobi-scaled normal equations (Eqs. 3-5),
+//      Cholesky with a Jacobi-eigenvalue (SVD) fallback;
+//   2. one fused FP32 pass over the wavelength grid giving the filtered
+//      Stokes vector and the 6 per-wavelength Jacobian columns (Eqs. 8-9);
+//   3. FP64 chi-square (Eq. 1) and the acceptance test (Fig. 6);
+//   4. on success, J^T W J and J^T W r in compensated FP32 sums (Ogita-Rump-
+//      Oishi Dot2), stored per slot in global scratch; damping by Table 2.
+#include <math.h>
+
+#include "common.cuh"
+
+namespace vfisv {
+
+constexpr int kInvThreads = 128;
+constexpr int kNP = 9;    // parameters taking part in the solve (alpha held)
+constexpr int kNPk = 45;  // packed lower triangle of a 9x9 matrix
+
+__device__ __forceinline__ int tri(int i, int j) { return i * (i + 1) / 2 + j; }  // i >= j
+
+// Compensated accumulation of a product: s + c tracks sum(a*b) to about
+// twice the working precision (TwoProduct via FMA, TwoSum).
+struct Dot2 {
+  float s, c;
+  __device__ __forceinline__ void add(float a, float b) {
+    const float p = a * b;
+    const float ep = fmaf(a, b, -p);
+    const float t = s + p;
+    const float bp = t - s;
+    const float es = (s - (t - bp)) + (p - bp);
+    s = t;
+    c += es + ep;
+  }
+  __device__ __forceinline__ float value() const { return s + c; }
+};
+
+// Bounds applied after every step (the oracle's reading).
+__device__ __forceinline__ void apply_bounds(float (&m)[10]) {
+  if (m[0] < 0.0f) {
+    m[0] = -m[0];
+    m[1] = 180.0f - m[1];
+  }
+  float g = fmodf(m[1], 360.0f);
+  if (g < 0.0f) g += 360.0f;
+  m[1] = (g > 180.0f) ? 360.0f - g : g;
+  float ps = fmodf(m[2], 180.0f);
+  if (ps < 0.0f) ps += 180.0f;
+  if (ps >= 180.0f) ps = 0.0f;
+  m[2] = ps;
+  m[0] = fminf(m[0], 6000.0f);
+  m[3] = fminf(fmaxf(m[3], 0.01f), 500.0f);
+  m[4] = fminf(fmaxf(m[4], 5.0f), 150.0f);
+  m[5] = fminf(fmaxf(m[5], 0.0f), 5.0f);
+  m[6] = fminf(fmaxf(m[6], -20.0f), 20.0f);
+  m[7] = fminf(fmaxf(m[7], 0.0f), 2.0f);
+  m[8] = fminf(fmaxf(m[8], 0.0f), 2.0f);
+}
+
+// Table 2 (with the oracle's reading of its overlapping rows).
+__device__ __forceinline__ double eps_update(double e, bool success) {
+  double n;
+  if (success)
+    n = (e > 1e4) ? e / 100.0 : (e >= 1e-4 ? e / 10.0 : e / 2.0);
+  else
+    n = (e < 1e-4) ? e * 100.0 : (e <= 1e4 ? e * 2.0 : e * 10.0);
+  return fmax(n, 1e-9);  // floor: the scaled damped matrix keeps eigenvalues >= 1e-9
+}
+
+// Symmetric eigen-decomposition by cyclic Jacobi rotations, FP64; the
+// fallback when the Cholesky pivots show a (numerically) singular matrix.
+// Solves M y = b with eigenvalues below 1e-12 * max zeroed (truncated SVD
+// of a symmetric matrix), or, with b == nullptr, writes the truncated
+// pseudo-inverse into Minv.
+__device__ __noinline__ void jacobi_pinv(const double* Mp /*packed*/, const double* b,
+                                         double* y, double* Minv) {
+  double a[kNP][kNP], v[kNP][kNP];
+  for (int i = 0; i < kNP; ++i)
+    for (int j = 0; j < kNP; ++j) {
+      a[i][j] = (i >= j) ? Mp[tri(i, j)] : Mp[tri(j, i)];
+      v[i][j] = (i == j) ? 1.0 : 0.0;
+    }
+  for (int sweep = 0; sweep < 30; ++sweep) {
+    double off = 0.0, dia = 0.0;
+    for (int i = 0; i < kNP; ++i) {
+      dia += a[i][i] * a[i][i];
+      for (int j = i + 1; j < kNP; ++j) off += a[i][j] * a[i][j];
+    }
+    if (!(off > 1e-32 * dia)) break;
+    for (int p = 0; p < kNP - 1; ++p)
+      for (int q = p + 1; q < kNP; ++q) {
+        const double apq = a[p][q];
+        if (apq == 0.0) continue;
+        const double th = (a[q][q] - a[p][p]) / (2.0 * apq);
+        const double t = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
+        const double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
+        for (int k = 0; k < kNP; ++k) {
+          const double akp = a[k][p], akq = a[k][q];
+          a[k][p] = c * akp - s * akq;
+          a[k][q] = s * akp + c * akq;
+        }
+        for (int k = 0; k < kNP; ++k) {
+          const double apk = a[p][k], aqk = a[q][k];
+          a[p][k] = c * apk - s * aqk;
+          a[q][k] = s * apk + c * aqk;
+        }
+        for (int k = 0; k < kNP; ++k) {
+          const double vkp = v[k][p], vkq = v[k][q];
+          v[k][p] = c * vkp - s * vkq;
+          v[k][q] = s * vkp + c * vkq;
+        }
+      }
+  }
+  double lmax = 0.0;
+  for (int i = 0; i < kNP; ++i) lmax = fmax(lmax, fabs(a[i][i]));
+  double linv[kNP];
+  for (int i = 0; i < kNP; ++i) {
+    const double l = fabs(a[i][i]);
+    linv[i] = (l > 1e-12 * lmax && l > 0.0) ? 1.0 / a[i][i] : 0.0;
+  }
+  if (b) {
+    double t[kNP];
+    for (int i = 0; i < kNP; ++i) {
+      double s = 0.0;
+      for (int k = 0; k < kNP; ++k) s += v[k][i] * b[k];
+      t[i] = s * linv[i];
+    }
+    for (int k = 0; k < kNP; ++k) {
+      double s = 0.0;
+      for (int i = 0; i < kNP; ++i) s += v[k][i] * t[i];
+      y[k] = s;
+    }
+  } else {
+    for (int i = 0; i < kNP; ++i)
+      for (int j = 0; j <= i; ++j) {
+        double s = 0.0;
+        for (int k = 0; k < kNP; ++k) s += v[i][k] * linv[k] * v[j][k];
+        Minv[tri(i, j)] = s;
+      }
+  }
+}
+
+// In-place Cholesky of a packed 9x9 matrix; false if a pivot is not
+// comfortably positive (the matrix has unit-scale diagonal here).
+__device__ __forceinline__ bool cholesky9(double (&L)[kNPk], double (&ri)[kNP]) {
+#pragma unroll
+  for (int j = 0; j < kNP; ++j) {
+    double d = L[tri(j, j)];
+#pragma unroll
+    for (int k = 0; k < j; ++k) d = fma(-L[tri(j, k)], L[tri(j, k)], d);
+    if (!(d > 1e-10)) return false;
+    const double r = rsqrt(d);
+    ri[j] = r;
+    L[tri(j, j)] = d * r;
+#pragma unroll
+    for (int i = j + 1; i < kNP; ++i) {
+      double s = L[tri(i, j)];
+#pragma unroll
+      for (int k = 0; k < j; ++k) s = fma(-L[tri(i, k)], L[tri(j, k)], s);
+      L[tri(i, j)] = s * r;
+    }
+  }
+  return true;
+}
+
+// Forward and back substitution with the factor and its reciprocal pivots.
+__device__ __forceinline__ void chol_solve9(const double (&L)[kNPk], const double (&ri)[kNP],
+                                            double (&x)[kNP]) {
+#pragma unroll
+  for (int i = 0; i < kNP; ++i) {
+    double s = x[i];
+#pragma unroll
+    for (int k = 0; k < i; ++k) s = fma(-L[tri(i, k)], x[k], s);
+    x[i] = s * ri[i];
+  }
+#pragma unroll
+  for (int i = kNP - 1; i >= 0; --i) {
+    double s = x[i];
+#pragma unroll
+    for (int k = i + 1; k < kNP; ++k) s = fma(-L[tri(k, i)], x[k], s);
+    x[i] = s * ri[i];
+  }
+}
+
+// Jacobi-scaled matrix of the stored normal equations: returns the scale
+// s_i = diag^-1/2 (0 for held parameters) and fills Mx = D^-1/2 A D^-1/2 +
+// eps I on free parameters, identity rows/columns on held ones.
+__device__ __forceinline__ void scaled_system(const float* scr, int64_t ns, uint32_t free_mask,
+                                              double eps, double (&Mx)[kNPk],
+                                              double (&sc)[kNP], bool (&held)[kNP]) {
+#pragma unroll
+  for (int i = 0; i < kNP; ++i) {
+    const double d = (double)scr[(int64_t)tri(i, i) * ns];
+    held[i] = !((free_mask >> i) & 1u) || !(d > 0.0) || !isfinite(d);
+    sc[i] = held[i] ? 0.0 : rsqrt(d);
+  }
+#pragma unroll
+  for (int i = 0; i < kNP; ++i)
+#pragma unroll
+    for (int j = 0; j <= i; ++j) {
+      double m;
+      if (i == j)
+        m = held[i] ? 1.0 : 1.0 + eps;
+      else
+        m = (held[i] || held[j]) ? 0.0 : (double)scr[(int64_t)tri(i, j) * ns] * sc[i] * sc[j];
+      Mx[tri(i, j)] = m;
+    }
+}
+
+// Eq. 5 with the Marquardt diagonal (Eq. 4): delta = (A + eps diag A)^-1 g.
+__device__ __noinline__ void damped_step(const float* scr, int64_t ns, uint32_t free_mask, double eps,
+                            double (&delta)[kNP]) {
+  double L[kNPk], sc[kNP];
+  bool held[kNP];
+  scaled_system(scr, ns, free_mask, eps, L, sc, held);
+  double y[kNP];
+#pragma unroll
+  for (int i = 0; i < kNP; ++i)
+    y[i] = held[i] ? 0.0 : (double)scr[(int64_t)(kNPk + i) * ns] * sc[i];
+  double ri[kNP];
+  if (cholesky9(L, ri)) {
+    chol_solve9(L, ri, y);
+  } else {
+    // rebuild the scaled matrix (the factorisation overwrote it)
+    scaled_system(scr, ns, free_mask, eps, L, sc, held);
+    double b[kNP];
+#pragma unroll
+    for (int i = 0; i < kNP; ++i) b[i] = y[i];
+    jacobi_pinv(L, b, y, nullptr);
+  }
+#pragma unroll
+  for (int i = 0; i < kNP; ++i) delta[i] = held[i] ? 0.0 : sc[i] * y[i];
+}
+
+// Covariance (J^T W J)^+ at the final model, in parameter units, from the
+// packed J^T W J at scr[e * ns].  Reads everything before writing `out`, so
+// `out` may hold the packed matrix itself.
+__device__ __noinline__ void covariance(const float* scr, int64_t ns, uint32_t free_mask, float* out) {
+  double L[kNPk], sc[kNP];
+  bool held[kNP];
+  scaled_system(scr, ns, free_mask, 0.0, L, sc, held);
+  double P[kNPk], ri[kNP];
+  if (cholesky9(L, ri)) {
+    for (int j = 0; j < kNP; ++j) {
+      double x[kNP];
+#pragma unroll
+      for (int i = 0; i < kNP; ++i) x[i] = (i == j) ? 1.0 : 0.0;
+      chol_solve9(L, ri, x);
+      for (int i = j; i < kNP; ++i) P[tri(i, j)] = x[i];
+    }
+  } else {
+    scaled_system(scr, ns, free_mask, 0.0, L, sc, held);
+    jacobi_pinv(L, nullptr, nullptr, P);
+  }
+  for (int i = 0; i < 10; ++i)
+    for (int j = 0; j < 10; ++j) {
+      float v = 0.0f;
+      if (i < kNP && j < kNP && !held[i] && !held[j])
+        v = (float)(sc[i] * sc[j] * ((i >= j) ? P[tri(i, j)] : P[tri(j, i)]));
+      out[i * 10 + j] = v;
+    }
+}
+
+// Weideman coefficients of this translation unit (set by invert_set_constants).
+__constant__ Weideman c_W;
+
+// The fused pass over the wavelength grid, kept out of line so that its
+// 168 accumulators get the whole register file; results go to the
+// thread's column of `dump`.
+template <int NF>
+__device__ __noinline__ void fused_pass(const PixK P, const float* __restrict__ tab, int nlam,
+                                        float* __restrict__ dump, int nt) {
+  constexpr int S = ((NF + 1) + 3) & ~3;
+  float acc[kRows][4][NF];
+#pragma unroll
+  for (int r = 0; r < kRows; ++r)
+#pragma unroll
+    for (int s = 0; s < 4; ++s)
+#pragma unroll
+      for (int k = 0; k < NF; ++k) acc[r][s][k] = 0.0f;
+#pragma unroll 1
+  for (int i = 0; i < nlam; ++i) {
+    float T[NF];
+    const float x = load_row<NF>(tab + (size_t)i * S, T);
+    lambda_step<NF, true>(c_W, P, x, T, acc);
+  }
+#pragma unroll
+  for (int r = 0; r < kRows; ++r)
+#pragma unroll
+    for (int s = 0; s < 4; ++s)
+#pragma unroll
+      for (int k = 0; k < NF; ++k) dump[((r * 4 + s) * NF + k) * nt] = acc[r][s][k];
+}
+
+// Per-slot LM state kept in shared memory (structure of arrays, one column
+// per thread) so that the registers of the wavelength loop hold only its
+// accumulators.
+constexpr int kStateWords = 10 + 10 + 2 + 2 + 2 + 1;  // M, Mt, chi2b, eps, pix, it
+__host__ __device__ constexpr size_t invert_smem_bytes(int tabf, int nacc, int nt) {
+  return (size_t)tabf * 4 + (size_t)nacc * nt * 4 + (size_t)kStateWords * nt * 4 + 16;
+}
+
+template <int NF>
+__global__ void __launch_bounds__(kInvThreads, 1) invert_kernel(InvertArgs A) {
+  constexpr int NOBS = 4 * NF;
+  constexpr int NACC = kRows * 4 * NF;
+  extern __shared__ __align__(16) float smem[];
+  const int S = table_stride(NF);
+  const int tabf = table_floats(NF, A.nlam);
+  const int tid = threadIdx.x, nt = blockDim.x;
+  float* tab = smem;
+  float* dump = smem + tabf;                      // [NACC][nt]
+  float* sM = dump + NACC * nt;                   // [10][nt] best model
+  float* sMt = sM + 10 * nt;                      // [10][nt] trial model
+  double* sChi = reinterpret_cast<double*>(sMt + 10 * nt);  // [nt]
+  double* sEps = sChi + nt;                       // [nt]
+  long long* sPix = reinterpret_cast<long long*>(sEps + nt);  // [nt]
+  int* sIt = reinterpret_cast<int*>(sPix + nt);   // [nt]
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + (invert_smem_bytes(tabf, NACC, nt) - 16) / 4);
+  if (!tma_load_table(tab, A.table, (uint32_t)(tabf * sizeof(float)), mbar, A.err)) return;
+  const float* tau = tab + (size_t)A.nlam * S;
+  const int64_t slot = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t ns = A.nslots;
+  float* scr = A.scratch + slot;
+  const int dof = NOBS - A.nfree;
+#define ST(arr, j) arr[(j) * nt + tid]
+
+  sPix[tid] = -1;
+  while (true) {
+    bool fresh = false;
+    {
+      long long pix = sPix[tid];
+      if (pix < 0) {
+        pix = (long long)atomicAdd(A.queue, 1ull);
+        if (pix >= A.npix) break;
+        fresh = true;
+        sPix[tid] = pix;
+        const float* o = A.obs + pix * NOBS;
+        const float* wv = A.w + pix * A.w_stride;
+        bool bad = false;
+        float wsum = 0.0f, ic = -INFINITY;
+#pragma unroll
+        for (int j = 0; j < NOBS; ++j) {
+          const float ov = o[j], ww = wv[j];
+          bad |= !isfinite(ov) || !isfinite(ww);
+          wsum += isfinite(ww) ? ww : 0.0f;
+          if (j < NF) ic = fmaxf(ic, isfinite(ov) ? ov : 0.0f);
+        }
+        bad |= !(wsum > 0.0f);
+        float Mt[10];
+        if (A.init) {
+          const float guess[10] = {500.f, 60.f, 45.f, 10.f, 35.f, 0.25f, 0.f, 0.25f, 0.75f, 1.f};
+#pragma unroll
+          for (int j = 0; j < 10; ++j) {
+            const float v = A.init[pix * 10 + j];
+            bad |= !isfinite(v);
+            Mt[j] = isfinite(v) ? v : guess[j];
+          }
+        } else {
+          Mt[0] = 500.f; Mt[1] = 60.f; Mt[2] = 45.f; Mt[3] = 10.f; Mt[4] = 35.f;
+          Mt[5] = 0.25f; Mt[6] = 0.f;
+          Mt[7] = 0.25f * ic;
+          Mt[8] = 0.75f * ic / A.lk.mu;
+        }
+        Mt[9] = 1.0f;
+        apply_bounds(Mt);
+        if (bad) {
+          for (int j = 0; j < 10; ++j) A.params_out[pix * 10 + j] = Mt[j];
+          A.chi2_out[pix] = 0.0f;
+          A.iters_out[pix] = 0;
+          A.status_out[pix] = VFISV_PIX_BAD_INPUT;
+          if (A.cov_out)
+            for (int j = 0; j < 100; ++j) A.cov_out[pix * 100 + j] = 0.0f;
+          sPix[tid] = -1;
+          continue;
+        }
+#pragma unroll
+        for (int j = 0; j < 10; ++j) ST(sMt, j) = Mt[j];
+        sIt[tid] = 0;
+        sEps[tid] = A.eps0;
+      } else {
+        double d[kNP];
+        damped_step(scr, ns, A.free_mask, sEps[tid], d);
+        float Mt[10];
+#pragma unroll
+        for (int j = 0; j < kNP; ++j) Mt[j] = (float)((double)ST(sM, j) + d[j]);
+        Mt[9] = 1.0f;
+        apply_bounds(Mt);
+#pragma unroll
+        for (int j = 0; j < 10; ++j) ST(sMt, j) = Mt[j];
+      }
+    }
+
+    // ---- fused synthesis + Jacobian at the trial model (Secs. 3 and 4.4) ----
+    fused_pass<NF>(make_pixk(A.lk, ST(sMt, 0), ST(sMt, 1), ST(sMt, 3), ST(sMt, 4),
+                             ST(sMt, 5), ST(sMt, 6)),
+                   tab, A.nlam, dump + tid, nt);
+    auto D = [&](int r, int s, int k) { return dump[((r * 4 + s) * NF + k) * nt + tid]; };
+
+    const long long pix = sPix[tid];
+    const float* o = A.obs + pix * NOBS;
+    const float* wv = A.w + pix * A.w_stride;
+
+    // ---- model, residual and chi-square (Eq. 1, FP64) ----
+    float c2p, s2p;
+    sincosf(2.0f * ST(sMt, 2) * kDeg, &s2p, &c2p);
+    const float mus1 = A.lk.mu * ST(sMt, 8);
+    const float s0 = ST(sMt, 7);
+    float syn[NOBS];
+#pragma unroll
+    for (int k = 0; k < NF; ++k) {
+      const float q0 = D(0, 1, k), u0 = D(0, 2, k);
+      syn[k] = fmaf(s0, tau[k], mus1 * D(0, 0, k));
+      syn[NF + k] = mus1 * fmaf(c2p, q0, -s2p * u0);
+      syn[2 * NF + k] = mus1 * fmaf(s2p, q0, c2p * u0);
+      syn[3 * NF + k] = mus1 * D(0, 3, k);
+    }
+    double c2 = 0.0;
+#pragma unroll
+    for (int j = 0; j < NOBS; ++j) {
+      const double r = (double)(o[j] - syn[j]);
+      c2 = fma((double)wv[j] * r, r, c2);
+    }
+    c2 /= (double)dof;
+
+    bool accept, retire = false;
+    int status = VFISV_PIX_MAXITER;
+    int it = sIt[tid];
+    if (fresh) {
+      accept = isfinite(c2);
+      if (!accept) {
+        retire = true;
+        status = VFISV_PIX_NAN_STATE;
+      }
+    } else {
+      ++it;
+      const double chi2b = sChi[tid];
+      accept = isfinite(c2) && c2 < chi2b;
+      const double eps_used = sEps[tid];
+      const double eps = eps_update(eps_used, accept);
+      sEps[tid] = eps;
+      if (accept) {
+        const double rel = (chi2b - c2) / chi2b;
+        if (rel < A.conv_rtol && eps_used <= A.conv_eps) {
+          retire = true;
+          status = VFISV_PIX_CONVERGED;
+        }
+      } else if (eps >= 1e12) {
+        retire = true;
+        status = VFISV_PIX_STALLED;
+      }
+    }
+    sIt[tid] = it;
+
+    if (accept) {
+      // ---- J^T W J and J^T W r at the new best model (compensated FP32) ----
+#pragma unroll
+      for (int j = 0; j < 10; ++j) ST(sM, j) = ST(sMt, j);
+      sChi[tid] = c2;
+      Dot2 a[kNPk], g[kNP];
+#pragma unroll
+      for (int i = 0; i < kNPk; ++i) a[i] = Dot2{0.0f, 0.0f};
+#pragma unroll
+      for (int i = 0; i < kNP; ++i) g[i] = Dot2{0.0f, 0.0f};
+      constexpr int rowOf[kNP] = {kRowB, kRowG, -1, kRowE, kRowD, kRowA, kRowV, -1, -1};
+      const float mu = A.lk.mu;
+      // Runtime loops over (filter, Stokes) keep this block small: it runs
+      // on accepted steps only and must not evict the wavelength loop from
+      // the instruction cache.  Observable (s, k) of row r is
+      // fmaf(cA, D(r, sa, k), cB * D(r, sb, k)), the psi rotation of Q0/U0.
+#pragma unroll 1
+      for (int k = 0; k < NF; ++k) {
+        const float q0 = D(0, 1, k), u0 = D(0, 2, k);
+        const float Qk = mus1 * fmaf(c2p, q0, -s2p * u0);
+        const float Uk = mus1 * fmaf(s2p, q0, c2p * u0);
+#pragma unroll 1
+        for (int s = 0; s < 4; ++s) {
+          const int sa = (s == 0) ? 0 : (s == 3 ? 3 : 1);
+          const int sb = (s == 0) ? 0 : (s == 3 ? 3 : 2);
+          const float cA = (s == 1) ? c2p : (s == 2 ? s2p : 1.0f);
+          const float cB = (s == 1) ? -s2p : (s == 2 ? c2p : 0.0f);
+          float J[kNP];
+#pragma unroll
+          for (int p = 0; p < kNP; ++p)
+            if (rowOf[p] >= 0)
+              J[p] = mus1 * fmaf(cA, D(rowOf[p], sa, k), cB * D(rowOf[p], sb, k));
+          J[2] = (s == 1) ? -2.0f * kDeg * Uk : (s == 2 ? 2.0f * kDeg * Qk : 0.0f);
+          J[7] = (s == 0) ? tau[k] : 0.0f;
+          const float lin = fmaf(cA, D(0, sa, k), cB * D(0, sb, k));
+          J[8] = mu * lin;
+          const float sv = (s == 0) ? fmaf(s0, tau[k], mus1 * lin) : mus1 * lin;
+          const int ob = s * NF + k;
+          const float ww = wv[ob];
+          const float rr = o[ob] - sv;
+#pragma unroll
+          for (int p = 0; p < kNP; ++p) {
+            const float wj = ww * J[p];
+            g[p].add(wj, rr);
+#pragma unroll
+            for (int q = 0; q <= p; ++q) a[tri(p, q)].add(wj, J[q]);
+          }
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < kNPk; ++i) scr[(int64_t)i * ns] = a[i].value();
+#pragma unroll
+      for (int i = 0; i < kNP; ++i) scr[(int64_t)(kNPk + i) * ns] = g[i].value();
+    }
+    if (!retire && it >= A.max_iter) retire = true;  // status stays MAXITER
+
+    if (retire) {
+      double chi2b = sChi[tid];
+      if (status == VFISV_PIX_NAN_STATE) {
+#pragma unroll
+        for (int j = 0; j < 10; ++j) ST(sM, j) = ST(sMt, j);
+        chi2b = c2;
+      }
+      for (int j = 0; j < 10; ++j) A.params_out[pix * 10 + j] = ST(sM, j);
+      A.chi2_out[pix] = (float)chi2b;
+      A.iters_out[pix] = it;
+      A.status_out[pix] = status;
+      if (A.cov_out) {
+        // the covariance itself is computed by covariance_kernel for all
+        // pixels at once (full warps); here the pixel's J^T W J is parked in
+        // its own output row
+        float* cv = A.cov_out + pix * 100;
+        if (status == VFISV_PIX_NAN_STATE) {
+          for (int j = 0; j < 100; ++j) cv[j] = 0.0f;
+        } else {
+          for (int j = 0; j < kNPk; ++j) cv[j] = scr[(int64_t)j * ns];
+        }
+      }
+      sPix[tid] = -1;
+    }
+  }
+#undef ST
+}
+
+// Covariance of every pixel that finished with a model: one pixel per
+// thread; reads the packed J^T W J parked in the pixel's output row.
+__global__ void __launch_bounds__(128) covariance_kernel(float* cov, const int32_t* status,
+                                                         int64_t npix, uint32_t free_mask) {
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < npix;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    const int st = status[p];
+    if (st == VFISV_PIX_CONVERGED || st == VFISV_PIX_MAXITER || st == VFISV_PIX_STALLED)
+      covariance(cov + p * 100, 1, free_mask, cov + p * 100);
+  }
+}
+
+cudaError_t launch_covariance(float* cov, const int32_t* status, int64_t npix,
+                              uint32_t free_mask, cudaStream_t s) {
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  int64_t grid = (npix + 127) / 128;
+  if (grid > (int64_t)nsm * 16) grid = (int64_t)nsm * 16;
+  if (grid < 1) grid = 1;
+  covariance_kernel<<<(int)grid, 128, 0, s>>>(cov, status, npix, free_mask);
+  return cudaGetLastError();
+}
+
+cudaError_t invert_slots(int nf, int nlam, int64_t npix, int64_t* nslots, int* grid,
+                         int* block, size_t* smem) {
+  if (nf != 6) return cudaErrorInvalidValue;
+  auto kern = invert_kernel<6>;
+  const int bs = kInvThreads;
+  const size_t sm = invert_smem_bytes(table_floats(6, nlam), kRows * 4 * 6, bs);
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  int dev = 0, nsm = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, bs, sm);
+  if (e != cudaSuccess) return e;
+  if (per < 1) return cudaErrorLaunchOutOfResources;
+  int64_t g = (int64_t)nsm * per;
+  const int64_t need = (npix + bs - 1) / bs;
+  if (need < g) g = need;
+  if (g < 1) g = 1;
+  *grid = (int)g;
+  *block = bs;
+  *smem = sm;
+  *nslots = g * bs;
+  return cudaSuccess;
+}
+
+cudaError_t invert_set_constants(const Weideman& W) {
+  return cudaMemcpyToSymbol(c_W, &W, sizeof(W));
+}
+
+cudaError_t launch_invert(const InvertArgs& a, int nf, int grid, int block, size_t smem,
+                          cudaStream_t s) {
+  if (nf != 6) return cudaErrorInvalidValue;
+  invert_kernel<6><<<grid, block, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace vfisv
