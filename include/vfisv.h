@@ -47,6 +47,22 @@ extern "C" {
 
 #define VFISV_NPARAM 10
 
+/* Initial-guess network: 24 inputs (the observables divided by the largest
+ * Stokes I sample, standardised), three GELU hidden layers of 256, 11
+ * outputs (B, cos gamma, sin 2psi, cos 2psi, ln eta0, dlambdaD, a, v_los,
+ * S0/Ic, S1/Ic standardised, and a confidence = predicted log mean squared
+ * error of the other ten).  Its float32 parameter blob holds, in order:
+ *   W0[24][256] b0[256] W1[256][256] b1[256] W2[256][256] b2[256]
+ *   W3[256][11] b3[11]  (weights [fan_in][fan_out]: y = x W + b)
+ *   in_mean[24] in_std[24] out_mean[10] out_std[10]  (standardisation)
+ * The first VFISV_NN_NTRAIN floats are trained; the rest are statistics of
+ * the training set. */
+#define VFISV_NN_NIN 24
+#define VFISV_NN_NHID 256
+#define VFISV_NN_NOUT 11
+#define VFISV_NN_NTRAIN 140811
+#define VFISV_NN_NBLOB 140879
+
 enum {
   VFISV_OK = 0,
   VFISV_E_ARG = -1,         /* null pointer or invalid argument value */
@@ -142,6 +158,56 @@ int vfisv_invert(vfisv_handle* h, const float* obs, const float* weights,
                  const vfisv_config* cfg, int64_t npix, float* params_out,
                  float* chi2_out, int32_t* iters_out, int32_t* status_out,
                  float* cov_out, void* stream);
+
+/* Initialise a network blob for training (Sec. 5): weights uniform in
+ * +-sqrt(6/fan_in) from a counter-based hash of (seed, index), biases zero,
+ * and the standardisation statistics (mean, standard deviation; FP64
+ * accumulation) of the n training pairs.
+ *   blob    float32[VFISV_NN_NBLOB] output
+ *   obs     float32[n][24] observables of the training profiles
+ *   params  float32[n][10] their generating models */
+int vfisv_nn_init(vfisv_handle* h, float* blob, const float* obs, const float* params,
+                  int64_t n, uint64_t seed, void* stream);
+
+/* Train in place: Adam (beta1 0.9, beta2 0.999, eps 1e-8) with cosine
+ * learning-rate decay from lr0 to 0 over epochs * floor(n / batch) steps,
+ * minibatches drawn by a per-epoch affine permutation of the training set.
+ * Loss = mean squared error of the 10 standardised targets + squared error
+ * of the confidence output against log(mean squared error + 1e-4).
+ * batch must be a positive multiple of 512; n < 2^31.
+ *   loss_hist  float32[epochs * floor(n / batch)] per-step loss, or NULL */
+int vfisv_nn_train(vfisv_handle* h, float* blob, const float* obs, const float* params,
+                   int64_t n, int32_t batch, int32_t epochs, float lr0, uint64_t seed,
+                   float* loss_hist, void* stream);
+
+/* Loss and gradient for one batch of n pairs (the training kernels' forward
+ * and backward passes, BF16 operands, FP32 accumulation).
+ *   grad_out  float32[VFISV_NN_NTRAIN] dL/d(weights, biases), blob layout
+ *   loss_out  float32[1]
+ * 1 <= n <= 2^20. */
+int vfisv_nn_grad(vfisv_handle* h, const float* blob, const float* obs, const float* params,
+                  int64_t n, float* grad_out, float* loss_out, void* stream);
+
+/* Network initial guesses for npix pixels.
+ *   init_out  float32[npix][10] models decoded from the outputs (alpha = 1)
+ *   conf_out  float32[npix] confidence output, or NULL
+ *   raw_out   float32[npix][11] raw (standardised) outputs, or NULL */
+int vfisv_nn_infer(vfisv_handle* h, const float* blob, const float* obs, int64_t npix,
+                   const vfisv_line* line, float* init_out, float* conf_out, float* raw_out,
+                   void* stream);
+
+/* Mixed inversion: network guess, LM with cfg_nn, then every pixel that did
+ * not converge or ends with chi2 > chi2_flag is inverted again from the
+ * standard guess with cfg_plain and keeps the lower-chi2 result.  Arguments
+ * as vfisv_invert; iters_out counts the steps of both runs; flagged_out
+ * (int32[npix], or NULL) marks the re-inverted pixels. */
+int vfisv_invert_nn(vfisv_handle* h, const float* blob, const float* obs, const float* weights,
+                    int32_t weights_per_pixel, const float* filters, int32_t nfilt,
+                    const float* wl_mA, int32_t nlam, const vfisv_line* line,
+                    const vfisv_config* cfg_nn, const vfisv_config* cfg_plain,
+                    double chi2_flag, int64_t npix, float* params_out, float* chi2_out,
+                    int32_t* iters_out, int32_t* status_out, float* cov_out,
+                    int32_t* flagged_out, void* stream);
 
 #ifdef __cplusplus
 }

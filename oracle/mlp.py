@@ -98,3 +98,110 @@ def adam_step(param, grad, m, v, step, lr, b1=0.9, b2=0.999, eps=1e-8):
     mhat = m / (1 - b1 ** step)
     vhat = v / (1 - b2 ** step)
     return param - lr * mhat / (np.sqrt(vhat) + eps), m, v
+
+
+# --- the network's view of a pixel (features, targets, decoding) ----------
+# Features: f_j = (obs_j / Ic - in_mean_j) / in_std_j with Ic the largest
+# Stokes I sample.  Targets (then standardised by out_mean/out_std):
+# [B, cos gamma, sin 2psi, cos 2psi, ln eta0, dlambdaD, a, v, S0/Ic, S1/Ic].
+
+NIN = 24
+NTARGET = 10
+NFILT = 6
+
+
+def blob_layout():
+    """Offsets of the float32 parameter blob: name -> (offset, shape)."""
+    shapes = [("W0", (24, 256)), ("b0", (256,)), ("W1", (256, 256)), ("b1", (256,)),
+              ("W2", (256, 256)), ("b2", (256,)), ("W3", (256, 11)), ("b3", (11,)),
+              ("in_mean", (24,)), ("in_std", (24,)), ("out_mean", (10,)), ("out_std", (10,))]
+    out, off = {}, 0
+    for name, shp in shapes:
+        out[name] = (off, shp)
+        off += int(np.prod(shp))
+    out["_total"] = (off, ())
+    return out
+
+
+def unpack(blob):
+    """Blob -> (weights [(W, b) x 4], stats dict), FP64 copies."""
+    lay = blob_layout()
+    b = np.asarray(blob, dtype=np.float64)
+    get = lambda k: b[lay[k][0]:lay[k][0] + int(np.prod(lay[k][1]))].reshape(lay[k][1])  # noqa: E731
+    weights = [(get(f"W{l}"), get(f"b{l}")) for l in range(4)]
+    stats = {k: get(k) for k in ("in_mean", "in_std", "out_mean", "out_std")}
+    return weights, stats
+
+
+def pack(weights, stats):
+    lay = blob_layout()
+    blob = np.zeros(lay["_total"][0], dtype=np.float64)
+    for l, (W, b) in enumerate(weights):
+        for k, v in ((f"W{l}", W), (f"b{l}", b)):
+            o, shp = lay[k]
+            blob[o:o + int(np.prod(shp))] = np.asarray(v).ravel()
+    for k, v in stats.items():
+        o, shp = lay[k]
+        blob[o:o + int(np.prod(shp))] = v
+    return blob
+
+
+def continuum_estimate(obs):
+    return np.maximum(obs[:, :NFILT].max(axis=1), 1e-30)
+
+
+def raw_features(obs):
+    return obs / continuum_estimate(obs)[:, None]
+
+
+def raw_targets(params, ic):
+    p = np.asarray(params, dtype=np.float64)
+    g = np.radians(p[:, 1])
+    ps = np.radians(2.0 * p[:, 2])
+    return np.stack([p[:, 0], np.cos(g), np.sin(ps), np.cos(ps), np.log(p[:, 3]), p[:, 4],
+                     p[:, 5], p[:, 6], p[:, 7] / ic, p[:, 8] / ic], axis=1)
+
+
+def statistics(obs, params):
+    """Standardisation statistics of a training set (mean, population std)."""
+    f = raw_features(obs)
+    t = raw_targets(params, continuum_estimate(obs))
+    sd = lambda a: np.maximum(a.std(axis=0), 1e-6)  # noqa: E731
+    return {"in_mean": f.mean(axis=0), "in_std": sd(f), "out_mean": t.mean(axis=0),
+            "out_std": sd(t)}
+
+
+def features(obs, stats):
+    return (raw_features(obs) - stats["in_mean"]) / stats["in_std"]
+
+
+def targets(params, obs, stats):
+    return (raw_targets(params, continuum_estimate(obs)) - stats["out_mean"]) / stats["out_std"]
+
+
+def decode(y, obs, stats, mu=1.0):
+    """Network outputs [N, 11] -> initial models [N, 10] (inverse of targets)."""
+    ic = continuum_estimate(obs)
+    t = y[:, :NTARGET] * stats["out_std"] + stats["out_mean"]
+    m = np.empty((len(y), 10))
+    m[:, 0] = np.maximum(t[:, 0], 0.0)
+    m[:, 1] = np.degrees(np.arccos(np.clip(t[:, 1], -1.0, 1.0)))
+    m[:, 2] = np.mod(0.5 * np.degrees(np.arctan2(t[:, 2], t[:, 3])), 180.0)
+    m[:, 3] = np.exp(t[:, 4])
+    m[:, 4] = t[:, 5]
+    m[:, 5] = t[:, 6]
+    m[:, 6] = t[:, 7]
+    m[:, 7] = t[:, 8] * ic
+    m[:, 8] = t[:, 9] * ic / mu
+    m[:, 9] = 1.0
+    return m
+
+
+def loss_and_grad(blob, obs, params):
+    """FP64 loss and gradient (blob layout, trained part) of one batch."""
+    weights, stats = unpack(blob)
+    y, cache = forward(weights, features(obs, stats))
+    L, dy = loss_and_grad_output(y, targets(params, obs, stats))
+    grads = backward(weights, cache, dy)
+    g = pack([(gw, gb) for gw, gb in grads], {k: np.zeros_like(v) for k, v in stats.items()})
+    return L, g[:blob_layout()["in_mean"][0]], y

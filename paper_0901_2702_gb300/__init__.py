@@ -17,8 +17,13 @@ import numpy as np
 
 __all__ = [
     "vfisv_create", "vfisv_destroy", "vfisv_synth", "vfisv_invert", "vfisv_check",
-    "vfisv_strerror", "vfisv_config_default", "VfisvError", "library_path", "load",
+    "vfisv_strerror", "vfisv_config_default", "vfisv_nn_init", "vfisv_nn_train",
+    "vfisv_nn_grad", "vfisv_nn_infer", "vfisv_invert_nn", "VfisvError", "library_path", "load",
+    "NN_NBLOB", "NN_NTRAIN",
 ]
+
+NN_NIN, NN_NHID, NN_NOUT = 24, 256, 11
+NN_NTRAIN, NN_NBLOB = 140811, 140879
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_HERE, "_build", "libvfisv.so")
@@ -73,6 +78,19 @@ def load():
     lib.vfisv_invert.argtypes = [P, P, P, I32, P, I32, P, I32, ctypes.POINTER(vfisv_line), P,
                                  ctypes.POINTER(vfisv_config), I64, P, P, P, P, P, P]
     lib.vfisv_invert.restype = ctypes.c_int
+    U64 = ctypes.c_uint64
+    lib.vfisv_nn_init.argtypes = [P, P, P, P, I64, U64, P]
+    lib.vfisv_nn_init.restype = ctypes.c_int
+    lib.vfisv_nn_train.argtypes = [P, P, P, P, I64, I32, I32, ctypes.c_float, U64, P, P]
+    lib.vfisv_nn_train.restype = ctypes.c_int
+    lib.vfisv_nn_grad.argtypes = [P, P, P, P, I64, P, P, P]
+    lib.vfisv_nn_grad.restype = ctypes.c_int
+    lib.vfisv_nn_infer.argtypes = [P, P, P, I64, ctypes.POINTER(vfisv_line), P, P, P, P]
+    lib.vfisv_nn_infer.restype = ctypes.c_int
+    lib.vfisv_invert_nn.argtypes = [P, P, P, P, I32, P, I32, P, I32, ctypes.POINTER(vfisv_line),
+                                    ctypes.POINTER(vfisv_config), ctypes.POINTER(vfisv_config),
+                                    ctypes.c_double, I64, P, P, P, P, P, P, P]
+    lib.vfisv_invert_nn.restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -225,6 +243,112 @@ def vfisv_invert(h: Handle, obs, weights, filters, wl_mA, line, init=None, confi
                              ctypes.c_void_p(_stream(obs, stream)))
     _check(rc, "vfisv_invert")
     for key, k in (("params", k6), ("chi2", k7), ("iters", k8), ("status", k9), ("cov", k10)):
+        dst = out.get(key)
+        if dst is not None and not _is_torch(dst) and k is not dst:
+            dst[...] = k
+    return out
+
+
+def _out(ref, given, shape, dtype):
+    return given if given is not None else _empty(ref, shape, dtype)
+
+
+def vfisv_nn_init(h: Handle, obs, params, seed: int = 0, blob=None, stream=None):
+    """Fresh network blob: random weights and the training set's statistics."""
+    n = int(obs.shape[0])
+    blob = _out(obs, blob, (NN_NBLOB,), np.float32)
+    bp, kb = _ptr(blob, np.float32)
+    op, k1 = _ptr(obs, np.float32)
+    pp, k2 = _ptr(params, np.float32)
+    _check(load().vfisv_nn_init(h.ptr, bp, op, pp, n, int(seed),
+                                ctypes.c_void_p(_stream(obs, stream))), "vfisv_nn_init")
+    if not _is_torch(blob) and kb is not blob:
+        blob[...] = kb
+    return blob
+
+
+def vfisv_nn_train(h: Handle, blob, obs, params, batch: int = 8192, epochs: int = 1,
+                   lr0: float = 1e-3, seed: int = 0, want_loss: bool = True, stream=None):
+    """Train the blob in place (Adam, cosine decay); returns the per-step loss."""
+    n = int(obs.shape[0])
+    steps = (n // batch) * epochs
+    loss = _empty(obs, (max(steps, 1),), np.float32) if want_loss else None
+    bp, kb = _ptr(blob, np.float32)
+    op, k1 = _ptr(obs, np.float32)
+    pp, k2 = _ptr(params, np.float32)
+    lp, kl = _ptr(loss, np.float32)
+    _check(load().vfisv_nn_train(h.ptr, bp, op, pp, n, int(batch), int(epochs), float(lr0),
+                                 int(seed), lp, ctypes.c_void_p(_stream(obs, stream))),
+           "vfisv_nn_train")
+    if not _is_torch(blob) and kb is not blob:
+        blob[...] = kb
+    if loss is not None and not _is_torch(loss) and kl is not loss:
+        loss[...] = kl
+    return loss[:steps] if loss is not None else None
+
+
+def vfisv_nn_grad(h: Handle, blob, obs, params, stream=None):
+    """(loss, gradient[NN_NTRAIN]) of one batch."""
+    n = int(obs.shape[0])
+    grad = _empty(obs, (NN_NTRAIN,), np.float32)
+    loss = _empty(obs, (1,), np.float32)
+    bp, kb = _ptr(blob, np.float32)
+    op, k1 = _ptr(obs, np.float32)
+    pp, k2 = _ptr(params, np.float32)
+    gp, kg = _ptr(grad, np.float32)
+    lp, kl = _ptr(loss, np.float32)
+    _check(load().vfisv_nn_grad(h.ptr, bp, op, pp, n, gp, lp,
+                                ctypes.c_void_p(_stream(obs, stream))), "vfisv_nn_grad")
+    return loss, grad
+
+
+def vfisv_nn_infer(h: Handle, blob, obs, line, want_conf=True, want_raw=False, stream=None):
+    """Initial models [npix, 10] (and confidence / raw outputs) from the network."""
+    n = int(obs.shape[0])
+    init = _empty(obs, (n, 10), np.float32)
+    conf = _empty(obs, (n,), np.float32) if want_conf else None
+    raw = _empty(obs, (n, NN_NOUT), np.float32) if want_raw else None
+    bp, kb = _ptr(blob, np.float32)
+    op, k1 = _ptr(obs, np.float32)
+    ip, ki = _ptr(init, np.float32)
+    cp, kc = _ptr(conf, np.float32)
+    rp, kr = _ptr(raw, np.float32)
+    ln = _line(line)
+    _check(load().vfisv_nn_infer(h.ptr, bp, op, n, ctypes.byref(ln), ip, cp, rp,
+                                 ctypes.c_void_p(_stream(obs, stream))), "vfisv_nn_infer")
+    return {"init": init, "conf": conf, "raw": raw}
+
+
+def vfisv_invert_nn(h: Handle, blob, obs, weights, filters, wl_mA, line, config_nn=None,
+                    config_plain=None, chi2_flag: float = 3.0, want_cov=True, out=None,
+                    stream=None):
+    """Mixed inversion: network guess + LM, plain LM re-inversion of flagged pixels."""
+    npix = int(obs.shape[0])
+    nfilt, nlam = int(filters.shape[0]), int(filters.shape[1])
+    per_pixel = 1 if (len(weights.shape) >= 2 and int(weights.shape[0]) == npix and
+                      int(np.prod(weights.shape)) == npix * 4 * nfilt) else 0
+    cn = config_nn if isinstance(config_nn, vfisv_config) else \
+        vfisv_config_default(**({"max_iter": 20} | (config_nn or {})))
+    cp_ = config_plain if isinstance(config_plain, vfisv_config) else \
+        vfisv_config_default(**(config_plain or {}))
+    if out is None:
+        out = {"params": _empty(obs, (npix, 10), np.float32),
+               "chi2": _empty(obs, (npix,), np.float32),
+               "iters": _empty(obs, (npix,), np.int32),
+               "status": _empty(obs, (npix,), np.int32),
+               "cov": _empty(obs, (npix, 10, 10), np.float32) if want_cov else None,
+               "flagged": _empty(obs, (npix,), np.int32)}
+    ptrs = [_ptr(x, np.float32) for x in (blob, obs, weights, filters, wl_mA)]
+    outs = [(k, _ptr(out.get(k), np.int32 if k in ("iters", "status", "flagged") else np.float32))
+            for k in ("params", "chi2", "iters", "status", "cov", "flagged")]
+    ln = _line(line)
+    rc = load().vfisv_invert_nn(h.ptr, ptrs[0][0], ptrs[1][0], ptrs[2][0], per_pixel, ptrs[3][0],
+                                nfilt, ptrs[4][0], nlam, ctypes.byref(ln), ctypes.byref(cn),
+                                ctypes.byref(cp_), float(chi2_flag), npix,
+                                *[p for _, (p, _k) in outs],
+                                ctypes.c_void_p(_stream(obs, stream)))
+    _check(rc, "vfisv_invert_nn")
+    for key, (_, k) in outs:
         dst = out.get(key)
         if dst is not None and not _is_torch(dst) and k is not dst:
             dst[...] = k

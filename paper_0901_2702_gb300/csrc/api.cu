@@ -7,6 +7,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "nn.cuh"
 #include "vfisv.h"
 
 using namespace vfisv;
@@ -18,6 +19,10 @@ struct vfisv_handle {
   size_t ws_bytes = 0;
   void* stage = nullptr;   // device staging for host buffers
   size_t stage_bytes = 0;
+  void* nnws = nullptr;    // network activations, gradients, optimiser state
+  size_t nnws_bytes = 0;
+  void* mixws = nullptr;   // mixed inversion: guesses, gathered pixels, 2nd run
+  size_t mixws_bytes = 0;
 };
 
 namespace {
@@ -170,6 +175,94 @@ int set_device(vfisv_handle* h) {
   return cudaSetDevice(h->device) == cudaSuccess ? VFISV_OK : VFISV_E_CUDA;
 }
 
+
+int check_config(const vfisv_config* cfg, int nfilt) {
+  if (!cfg) return VFISV_E_ARG;
+  if (cfg->max_iter < 0 || (cfg->free_mask & ~0x1FFu) || !(cfg->conv_rtol >= 0) ||
+      !(cfg->conv_eps >= 0) || !(cfg->eps0 > 0) || !isfinite(cfg->eps0))
+    return VFISV_E_ARG;
+  if (4 * nfilt - __builtin_popcount(cfg->free_mask) <= 0) return VFISV_E_ARG;
+  return VFISV_OK;
+}
+
+int check_invert_args(vfisv_handle* h, const float* obs, const float* weights,
+                      const float* filters, int32_t nfilt, const float* wl_mA, int32_t nlam,
+                      const vfisv_line* line, const vfisv_config* cfg, int64_t npix,
+                      const float* params_out, const float* chi2_out, const int32_t* iters_out,
+                      const int32_t* status_out) {
+  if (!h || !obs || !weights || !filters || !wl_mA || !cfg || !params_out || !chi2_out ||
+      !iters_out || !status_out || !line_ok(line))
+    return VFISV_E_ARG;
+  if (npix < 0 || nfilt < 1 || nlam < 1 || nlam > 4096) return VFISV_E_SIZE;
+  if (nfilt != 6) return VFISV_E_UNSUPPORTED;
+  return check_config(cfg, nfilt);
+}
+
+// Device buffers of one inversion.
+struct DevInvert {
+  const float *obs = nullptr, *w = nullptr, *filters = nullptr, *wl = nullptr, *init = nullptr;
+  int64_t w_stride = 0;
+  float *params = nullptr, *chi2 = nullptr, *cov = nullptr;
+  int32_t *iters = nullptr, *status = nullptr;
+};
+
+// Pack the filter table, zero the work queue, run the persistent LM kernel
+// and the batched covariance, all on stream s.
+int invert_device(vfisv_handle* h, const DevInvert& d, int nfilt, int nlam,
+                  const vfisv_line* line, const vfisv_config* cfg, int64_t npix,
+                  const int64_t* npix_dev, cudaStream_t s) {
+  int64_t nslots = 0;
+  int grid = 0, block = 0;
+  size_t smem = 0;
+  if (invert_slots(nfilt, nlam, npix, &nslots, &grid, &block, &smem) != cudaSuccess) {
+    cudaGetLastError();
+    return VFISV_E_CUDA;
+  }
+  WsLayout L = layout(nfilt, nlam, nslots);
+  if (h->ws_bytes < L.total) {
+    int rc = grow(&h->ws, &h->ws_bytes, L.total);
+    if (rc) return rc;
+    if (cudaMemsetAsync(h->ws, 0, 64, s) != cudaSuccess) return VFISV_E_CUDA;
+  }
+  char* ws = (char*)h->ws;
+  float* table = (float*)(ws + L.table);
+  if (launch_pack_table(d.filters, nfilt, d.wl, nlam, table, s) != cudaSuccess)
+    return VFISV_E_CUDA;
+  if (cudaMemsetAsync(ws + L.queue, 0, sizeof(unsigned long long), s) != cudaSuccess)
+    return VFISV_E_CUDA;
+  InvertArgs a;
+  a.obs = d.obs;
+  a.w = d.w;
+  a.w_stride = d.w_stride;
+  a.init = d.init;
+  a.table = table;
+  a.nlam = nlam;
+  a.npix = npix;
+  a.npix_dev = npix_dev;
+  a.params_out = d.params;
+  a.chi2_out = d.chi2;
+  a.iters_out = d.iters;
+  a.status_out = d.status;
+  a.cov_out = d.cov;
+  a.scratch = (float*)(ws + L.scratch);
+  a.nslots = nslots;
+  a.queue = (unsigned long long*)(ws + L.queue);
+  a.err = (int*)(ws + L.err);
+  a.W = h->W;
+  a.lk = line_constants(line);
+  a.max_iter = cfg->max_iter;
+  a.free_mask = cfg->free_mask;
+  a.nfree = __builtin_popcount(cfg->free_mask);
+  a.conv_rtol = cfg->conv_rtol;
+  a.conv_eps = cfg->conv_eps;
+  a.eps0 = cfg->eps0;
+  if (launch_invert(a, nfilt, grid, block, smem, s) != cudaSuccess) return VFISV_E_CUDA;
+  if (d.cov && launch_covariance(d.cov, d.status, npix, npix_dev, cfg->free_mask, s) !=
+                   cudaSuccess)
+    return VFISV_E_CUDA;
+  return VFISV_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -223,6 +316,8 @@ void vfisv_destroy(vfisv_handle* h) {
   cudaDeviceSynchronize();
   if (h->ws) cudaFree(h->ws);
   if (h->stage) cudaFree(h->stage);
+  if (h->nnws) cudaFree(h->nnws);
+  if (h->mixws) cudaFree(h->mixws);
   delete h;
 }
 
@@ -288,33 +383,11 @@ int vfisv_invert(vfisv_handle* h, const float* obs, const float* weights,
                  const float* wl_mA, int32_t nlam, const vfisv_line* line, const float* init,
                  const vfisv_config* cfg, int64_t npix, float* params_out, float* chi2_out,
                  int32_t* iters_out, int32_t* status_out, float* cov_out, void* stream) {
-  if (!h || !obs || !weights || !filters || !wl_mA || !cfg || !params_out || !chi2_out ||
-      !iters_out || !status_out || !line_ok(line))
-    return VFISV_E_ARG;
-  if (npix < 0 || nfilt < 1 || nlam < 1 || nlam > 4096) return VFISV_E_SIZE;
-  if (nfilt != 6) return VFISV_E_UNSUPPORTED;
-  if (cfg->max_iter < 0 || (cfg->free_mask & ~0x1FFu) || !(cfg->conv_rtol >= 0) ||
-      !(cfg->conv_eps >= 0) || !(cfg->eps0 > 0) || !isfinite(cfg->eps0))
-    return VFISV_E_ARG;
-  const int nfree = __builtin_popcount(cfg->free_mask);
-  if (4 * nfilt - nfree <= 0) return VFISV_E_ARG;
-  if (npix == 0) return VFISV_OK;
+  int rc = check_invert_args(h, obs, weights, filters, nfilt, wl_mA, nlam, line, cfg, npix,
+                             params_out, chi2_out, iters_out, status_out);
+  if (rc || npix == 0) return rc;
   if (set_device(h)) return VFISV_E_CUDA;
   cudaStream_t s = (cudaStream_t)stream;
-
-  int64_t nslots = 0;
-  int grid = 0, block = 0;
-  size_t smem = 0;
-  if (invert_slots(nfilt, nlam, npix, &nslots, &grid, &block, &smem) != cudaSuccess) {
-    cudaGetLastError();
-    return VFISV_E_CUDA;
-  }
-  WsLayout L = layout(nfilt, nlam, nslots);
-  if (h->ws_bytes < L.total) {
-    int rc = grow(&h->ws, &h->ws_bytes, L.total);
-    if (rc) return rc;
-    if (cudaMemsetAsync(h->ws, 0, 64, s) != cudaSuccess) return VFISV_E_CUDA;
-  }
   const int nobs = 4 * nfilt;
   Staging st;
   st.add(obs, (size_t)npix * nobs * sizeof(float), false);
@@ -327,43 +400,205 @@ int vfisv_invert(vfisv_handle* h, const float* obs, const float* weights,
   st.add(iters_out, (size_t)npix * sizeof(int32_t), true);
   st.add(status_out, (size_t)npix * sizeof(int32_t), true);
   st.add(cov_out, cov_out ? (size_t)npix * 100 * sizeof(float) : 0, true);
+  if ((rc = st.prepare(h, s))) return rc;
+  DevInvert d;
+  d.obs = (const float*)st.bufs[0].dev;
+  d.w = (const float*)st.bufs[1].dev;
+  d.w_stride = weights_per_pixel ? nobs : 0;
+  d.filters = (const float*)st.bufs[2].dev;
+  d.wl = (const float*)st.bufs[3].dev;
+  d.init = (const float*)st.bufs[4].dev;
+  d.params = (float*)st.bufs[5].dev;
+  d.chi2 = (float*)st.bufs[6].dev;
+  d.iters = (int32_t*)st.bufs[7].dev;
+  d.status = (int32_t*)st.bufs[8].dev;
+  d.cov = (float*)st.bufs[9].dev;
+  if ((rc = invert_device(h, d, nfilt, nlam, line, cfg, npix, nullptr, s))) return rc;
+  return st.finish(s);
+}
+
+int vfisv_nn_init(vfisv_handle* h, float* blob, const float* obs, const float* params,
+                  int64_t n, uint64_t seed, void* stream) {
+  if (!h || !blob || !obs || !params) return VFISV_E_ARG;
+  if (n < 1) return VFISV_E_SIZE;
+  if (set_device(h)) return VFISV_E_CUDA;
+  cudaStream_t s = (cudaStream_t)stream;
+  Staging st;
+  st.add(blob, nn::NBLOB * sizeof(float), true);
+  st.add(obs, (size_t)n * nn::IN * sizeof(float), false);
+  st.add(params, (size_t)n * 10 * sizeof(float), false);
   int rc = st.prepare(h, s);
   if (rc) return rc;
-  char* ws = (char*)h->ws;
-  float* table = (float*)(ws + L.table);
-  if (launch_pack_table((const float*)st.bufs[2].dev, nfilt, (const float*)st.bufs[3].dev,
-                        nlam, table, s) != cudaSuccess)
+  if ((rc = grow(&h->nnws, &h->nnws_bytes, nn::workspace_bytes(512)))) return rc;
+  if (nn::nn_init(h->nnws, (float*)st.bufs[0].dev, (const float*)st.bufs[1].dev,
+                  (const float*)st.bufs[2].dev, n, seed, s) != cudaSuccess)
     return VFISV_E_CUDA;
-  if (cudaMemsetAsync(ws + L.queue, 0, sizeof(unsigned long long), s) != cudaSuccess)
+  return st.finish(s);
+}
+
+int vfisv_nn_train(vfisv_handle* h, float* blob, const float* obs, const float* params,
+                   int64_t n, int32_t batch, int32_t epochs, float lr0, uint64_t seed,
+                   float* loss_hist, void* stream) {
+  if (!h || !blob || !obs || !params || !(lr0 > 0) || epochs < 0) return VFISV_E_ARG;
+  if (batch < 512 || batch % 512 != 0 || n < batch || n >= (1ll << 31)) return VFISV_E_SIZE;
+  if (set_device(h)) return VFISV_E_CUDA;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t steps = (n / batch) * epochs;
+  Staging st;
+  st.add(blob, nn::NBLOB * sizeof(float), false);
+  st.add(obs, (size_t)n * nn::IN * sizeof(float), false);
+  st.add(params, (size_t)n * 10 * sizeof(float), false);
+  st.add(loss_hist, loss_hist ? (size_t)steps * sizeof(float) : 0, true);
+  int rc = st.prepare(h, s);
+  if (rc) return rc;
+  // the blob is updated in place: a host blob is copied back after training
+  st.bufs[0].out = true;
+  if ((rc = grow(&h->nnws, &h->nnws_bytes, nn::workspace_bytes(batch)))) return rc;
+  if (nn::nn_train(h->nnws, (float*)st.bufs[0].dev, (const float*)st.bufs[1].dev,
+                   (const float*)st.bufs[2].dev, n, batch, epochs, lr0, seed,
+                   (float*)st.bufs[3].dev, s) != cudaSuccess)
     return VFISV_E_CUDA;
-  InvertArgs a;
-  a.obs = (const float*)st.bufs[0].dev;
-  a.w = (const float*)st.bufs[1].dev;
-  a.w_stride = weights_per_pixel ? nobs : 0;
-  a.init = (const float*)st.bufs[4].dev;
-  a.table = table;
-  a.nlam = nlam;
-  a.npix = npix;
-  a.params_out = (float*)st.bufs[5].dev;
-  a.chi2_out = (float*)st.bufs[6].dev;
-  a.iters_out = (int32_t*)st.bufs[7].dev;
-  a.status_out = (int32_t*)st.bufs[8].dev;
-  a.cov_out = (float*)st.bufs[9].dev;
-  a.scratch = (float*)(ws + L.scratch);
-  a.nslots = nslots;
-  a.queue = (unsigned long long*)(ws + L.queue);
-  a.err = (int*)(ws + L.err);
-  a.W = h->W;
-  a.lk = line_constants(line);
-  a.max_iter = cfg->max_iter;
-  a.free_mask = cfg->free_mask;
-  a.nfree = nfree;
-  a.conv_rtol = cfg->conv_rtol;
-  a.conv_eps = cfg->conv_eps;
-  a.eps0 = cfg->eps0;
-  if (launch_invert(a, nfilt, grid, block, smem, s) != cudaSuccess) return VFISV_E_CUDA;
-  if (a.cov_out &&
-      launch_covariance(a.cov_out, a.status_out, npix, cfg->free_mask, s) != cudaSuccess)
+  return st.finish(s);
+}
+
+int vfisv_nn_grad(vfisv_handle* h, const float* blob, const float* obs, const float* params,
+                  int64_t n, float* grad_out, float* loss_out, void* stream) {
+  if (!h || !blob || !obs || !params || !grad_out || !loss_out) return VFISV_E_ARG;
+  if (n < 1 || n > (1ll << 20)) return VFISV_E_SIZE;
+  if (set_device(h)) return VFISV_E_CUDA;
+  cudaStream_t s = (cudaStream_t)stream;
+  Staging st;
+  st.add(blob, nn::NBLOB * sizeof(float), false);
+  st.add(obs, (size_t)n * nn::IN * sizeof(float), false);
+  st.add(params, (size_t)n * 10 * sizeof(float), false);
+  st.add(grad_out, nn::NTRAIN * sizeof(float), true);
+  st.add(loss_out, sizeof(float), true);
+  int rc = st.prepare(h, s);
+  if (rc) return rc;
+  if ((rc = grow(&h->nnws, &h->nnws_bytes, nn::workspace_bytes(nn::padded_rows(n))))) return rc;
+  if (nn::nn_grad(h->nnws, (const float*)st.bufs[0].dev, (const float*)st.bufs[1].dev,
+                  (const float*)st.bufs[2].dev, n, (float*)st.bufs[3].dev,
+                  (float*)st.bufs[4].dev, s) != cudaSuccess)
+    return VFISV_E_CUDA;
+  return st.finish(s);
+}
+
+static constexpr int64_t kInferChunk = 65536;
+
+int vfisv_nn_infer(vfisv_handle* h, const float* blob, const float* obs, int64_t npix,
+                   const vfisv_line* line, float* init_out, float* conf_out, float* raw_out,
+                   void* stream) {
+  if (!h || !blob || !obs || !init_out || !line_ok(line)) return VFISV_E_ARG;
+  if (npix < 0) return VFISV_E_SIZE;
+  if (npix == 0) return VFISV_OK;
+  if (set_device(h)) return VFISV_E_CUDA;
+  cudaStream_t s = (cudaStream_t)stream;
+  Staging st;
+  st.add(blob, nn::NBLOB * sizeof(float), false);
+  st.add(obs, (size_t)npix * nn::IN * sizeof(float), false);
+  st.add(init_out, (size_t)npix * 10 * sizeof(float), true);
+  st.add(conf_out, conf_out ? (size_t)npix * sizeof(float) : 0, true);
+  st.add(raw_out, raw_out ? (size_t)npix * nn::OUT * sizeof(float) : 0, true);
+  int rc = st.prepare(h, s);
+  if (rc) return rc;
+  if ((rc = grow(&h->nnws, &h->nnws_bytes, nn::workspace_bytes(kInferChunk)))) return rc;
+  if (nn::nn_infer(h->nnws, kInferChunk, (const float*)st.bufs[0].dev,
+                   (const float*)st.bufs[1].dev, npix, (float)line->mu,
+                   (float*)st.bufs[2].dev, (float*)st.bufs[3].dev, (float*)st.bufs[4].dev,
+                   s) != cudaSuccess)
+    return VFISV_E_CUDA;
+  return st.finish(s);
+}
+
+int vfisv_invert_nn(vfisv_handle* h, const float* blob, const float* obs, const float* weights,
+                    int32_t weights_per_pixel, const float* filters, int32_t nfilt,
+                    const float* wl_mA, int32_t nlam, const vfisv_line* line,
+                    const vfisv_config* cfg_nn, const vfisv_config* cfg_plain,
+                    double chi2_flag, int64_t npix, float* params_out, float* chi2_out,
+                    int32_t* iters_out, int32_t* status_out, float* cov_out,
+                    int32_t* flagged_out, void* stream) {
+  if (!blob || !cfg_plain) return VFISV_E_ARG;
+  int rc = check_invert_args(h, obs, weights, filters, nfilt, wl_mA, nlam, line, cfg_nn, npix,
+                             params_out, chi2_out, iters_out, status_out);
+  if (rc) return rc;
+  if ((rc = check_config(cfg_plain, nfilt))) return rc;
+  if (nfilt != nn::IN / 4) return VFISV_E_UNSUPPORTED;
+  if (npix == 0) return VFISV_OK;
+  if (set_device(h)) return VFISV_E_CUDA;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int nobs = 4 * nfilt;
+  Staging st;
+  st.add(obs, (size_t)npix * nobs * sizeof(float), false);
+  st.add(weights, (size_t)(weights_per_pixel ? npix : 1) * nobs * sizeof(float), false);
+  st.add(filters, (size_t)nfilt * nlam * sizeof(float), false);
+  st.add(wl_mA, (size_t)nlam * sizeof(float), false);
+  st.add(blob, nn::NBLOB * sizeof(float), false);
+  st.add(params_out, (size_t)npix * 10 * sizeof(float), true);
+  st.add(chi2_out, (size_t)npix * sizeof(float), true);
+  st.add(iters_out, (size_t)npix * sizeof(int32_t), true);
+  st.add(status_out, (size_t)npix * sizeof(int32_t), true);
+  st.add(cov_out, cov_out ? (size_t)npix * 100 * sizeof(float) : 0, true);
+  st.add(flagged_out, flagged_out ? (size_t)npix * sizeof(int32_t) : 0, true);
+  if ((rc = st.prepare(h, s))) return rc;
+  const float* o = (const float*)st.bufs[0].dev;
+  const float* w = (const float*)st.bufs[1].dev;
+  const int64_t wstride = weights_per_pixel ? nobs : 0;
+  // workspace: guesses, index, count, gathered obs/weights, second-run outputs
+  const bool cov = cov_out != nullptr;
+  size_t off = 0;
+  auto place = [&](size_t bytes) {
+    const size_t at = off;
+    off += up(bytes);
+    return at;
+  };
+  const size_t o_init = place((size_t)npix * 10 * 4), o_cnt = place(8),
+               o_idx = place((size_t)npix * 8), o_obs = place((size_t)npix * nobs * 4),
+               o_w = weights_per_pixel ? place((size_t)npix * nobs * 4) : 0,
+               o_p = place((size_t)npix * 10 * 4), o_c = place((size_t)npix * 4),
+               o_i = place((size_t)npix * 4), o_s = place((size_t)npix * 4),
+               o_v = cov ? place((size_t)npix * 100 * 4) : 0;
+  if ((rc = grow(&h->mixws, &h->mixws_bytes, off))) return rc;
+  if ((rc = grow(&h->nnws, &h->nnws_bytes, nn::workspace_bytes(kInferChunk)))) return rc;
+  char* mw = (char*)h->mixws;
+  float* init = (float*)(mw + o_init);
+  if (nn::nn_infer(h->nnws, kInferChunk, (const float*)st.bufs[4].dev, o, npix, (float)line->mu,
+                   init, nullptr, nullptr, s) != cudaSuccess)
+    return VFISV_E_CUDA;
+  DevInvert d;
+  d.obs = o;
+  d.w = w;
+  d.w_stride = wstride;
+  d.filters = (const float*)st.bufs[2].dev;
+  d.wl = (const float*)st.bufs[3].dev;
+  d.init = init;
+  d.params = (float*)st.bufs[5].dev;
+  d.chi2 = (float*)st.bufs[6].dev;
+  d.iters = (int32_t*)st.bufs[7].dev;
+  d.status = (int32_t*)st.bufs[8].dev;
+  d.cov = (float*)st.bufs[9].dev;
+  if ((rc = invert_device(h, d, nfilt, nlam, line, cfg_nn, npix, nullptr, s))) return rc;
+  int64_t* cnt = (int64_t*)(mw + o_cnt);
+  int64_t* idx = (int64_t*)(mw + o_idx);
+  float* og = (float*)(mw + o_obs);
+  float* wg = weights_per_pixel ? (float*)(mw + o_w) : nullptr;
+  if (nn::flag_and_gather(d.status, d.chi2, npix, (float)chi2_flag, o, w, wstride, nobs, cnt,
+                          idx, og, wg, (int32_t*)st.bufs[10].dev, s) != cudaSuccess)
+    return VFISV_E_CUDA;
+  DevInvert d2;
+  d2.obs = og;
+  d2.w = weights_per_pixel ? wg : w;
+  d2.w_stride = wstride;
+  d2.filters = d.filters;
+  d2.wl = d.wl;
+  d2.init = nullptr;
+  d2.params = (float*)(mw + o_p);
+  d2.chi2 = (float*)(mw + o_c);
+  d2.iters = (int32_t*)(mw + o_i);
+  d2.status = (int32_t*)(mw + o_s);
+  d2.cov = cov ? (float*)(mw + o_v) : nullptr;
+  if ((rc = invert_device(h, d2, nfilt, nlam, line, cfg_plain, npix, cnt, s))) return rc;
+  if (nn::merge_plain(cnt, idx, npix, d2.params, d2.chi2, d2.iters, d2.status, d2.cov, d.params,
+                      d.chi2, d.iters, d.status, d.cov, s) != cudaSuccess)
     return VFISV_E_CUDA;
   return st.finish(s);
 }

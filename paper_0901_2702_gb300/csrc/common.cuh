@@ -115,7 +115,8 @@ struct InvertArgs {
   const float* init; // may be null: standard guess
   const float* table;
   int nlam;
-  int64_t npix;
+  int64_t npix;              // pixel count (upper bound when npix_dev is set)
+  const int64_t* npix_dev;   // optional device-side count (<= npix)
   float* params_out;
   float* chi2_out;
   int32_t* iters_out;
@@ -148,7 +149,7 @@ cudaError_t invert_slots(int nf, int nlam, int64_t npix, int64_t* nslots, int* g
 // current device (once per device).
 cudaError_t invert_set_constants(const Weideman& W);
 cudaError_t launch_covariance(float* cov, const int32_t* status, int64_t npix,
-                              uint32_t free_mask, cudaStream_t s);
+                              const int64_t* npix_dev, uint32_t free_mask, cudaStream_t s);
 cudaError_t launch_invert(const InvertArgs& a, int nf, int grid, int block, size_t smem,
                           cudaStream_t s);
 

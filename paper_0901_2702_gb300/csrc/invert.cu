@@ -324,6 +324,7 @@ __global__ void __launch_bounds__(kInvThreads, 1) invert_kernel(InvertArgs A) {
   const int64_t ns = A.nslots;
   float* scr = A.scratch + slot;
   const int dof = NOBS - A.nfree;
+  const int64_t npix = A.npix_dev ? *A.npix_dev : A.npix;
 #define ST(arr, j) arr[(j) * nt + tid]
 
   sPix[tid] = -1;
@@ -333,7 +334,7 @@ __global__ void __launch_bounds__(kInvThreads, 1) invert_kernel(InvertArgs A) {
       long long pix = sPix[tid];
       if (pix < 0) {
         pix = (long long)atomicAdd(A.queue, 1ull);
-        if (pix >= A.npix) break;
+        if (pix >= npix) break;
         fresh = true;
         sPix[tid] = pix;
         const float* o = A.obs + pix * NOBS;
@@ -540,7 +541,10 @@ __global__ void __launch_bounds__(kInvThreads, 1) invert_kernel(InvertArgs A) {
 // Covariance of every pixel that finished with a model: one pixel per
 // thread; reads the packed J^T W J parked in the pixel's output row.
 __global__ void __launch_bounds__(128) covariance_kernel(float* cov, const int32_t* status,
-                                                         int64_t npix, uint32_t free_mask) {
+                                                         int64_t npix_max,
+                                                         const int64_t* npix_dev,
+                                                         uint32_t free_mask) {
+  const int64_t npix = npix_dev ? *npix_dev : npix_max;
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < npix;
        p += (int64_t)gridDim.x * blockDim.x) {
     const int st = status[p];
@@ -550,14 +554,14 @@ __global__ void __launch_bounds__(128) covariance_kernel(float* cov, const int32
 }
 
 cudaError_t launch_covariance(float* cov, const int32_t* status, int64_t npix,
-                              uint32_t free_mask, cudaStream_t s) {
+                              const int64_t* npix_dev, uint32_t free_mask, cudaStream_t s) {
   int dev = 0, nsm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   int64_t grid = (npix + 127) / 128;
   if (grid > (int64_t)nsm * 16) grid = (int64_t)nsm * 16;
   if (grid < 1) grid = 1;
-  covariance_kernel<<<(int)grid, 128, 0, s>>>(cov, status, npix, free_mask);
+  covariance_kernel<<<(int)grid, 128, 0, s>>>(cov, status, npix, npix_dev, free_mask);
   return cudaGetLastError();
 }
 

@@ -1,0 +1,77 @@
+// Mixed NN-initialised inversion: after the LM run from the network's guess,
+// pixels that did not converge or whose chi2 exceeds a threshold are flagged,
+// gathered and inverted again from the standard guess; the better of the two
+// results (lower chi2) is kept.  The flagged count stays on the device.
+#include "common.cuh"
+#include "nn.cuh"
+
+namespace vfisv {
+namespace nn {
+
+__global__ void flag_gather_kernel(const int32_t* __restrict__ status,
+                                   const float* __restrict__ chi2, int64_t npix,
+                                   float chi2_flag, const float* __restrict__ obs,
+                                   const float* __restrict__ w, int64_t w_stride, int nobs,
+                                   unsigned long long* __restrict__ count,
+                                   int64_t* __restrict__ index, float* __restrict__ obs_g,
+                                   float* __restrict__ w_g, int32_t* __restrict__ flagged) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= npix) return;
+  const int st = status[p];
+  const bool conv = (st == VFISV_PIX_CONVERGED || st == VFISV_PIX_STALLED);
+  const bool f = (st != VFISV_PIX_BAD_INPUT) && (!conv || !(chi2[p] <= chi2_flag));
+  if (flagged) flagged[p] = f ? 1 : 0;
+  if (!f) return;
+  const int64_t j = (int64_t)atomicAdd(count, 1ull);
+  index[j] = p;
+  for (int o = 0; o < nobs; ++o) obs_g[j * nobs + o] = obs[p * nobs + o];
+  if (w_g)
+    for (int o = 0; o < nobs; ++o) w_g[j * nobs + o] = w[p * w_stride + o];
+}
+
+cudaError_t flag_and_gather(const int32_t* status, const float* chi2, int64_t npix,
+                            float chi2_flag, const float* obs, const float* w,
+                            int64_t w_stride, int nobs, int64_t* count, int64_t* index,
+                            float* obs_g, float* w_g, int32_t* flagged, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(count, 0, sizeof(int64_t), s);
+  if (e != cudaSuccess) return e;
+  const unsigned nb = (unsigned)((npix + 255) / 256);
+  flag_gather_kernel<<<nb, 256, 0, s>>>(status, chi2, npix, chi2_flag, obs, w, w_stride, nobs,
+                                        (unsigned long long*)count, index, obs_g, w_g, flagged);
+  return cudaGetLastError();
+}
+
+__global__ void merge_kernel(const int64_t* __restrict__ count, const int64_t* __restrict__ index,
+                             const float* __restrict__ p2, const float* __restrict__ c2,
+                             const int32_t* __restrict__ i2, const int32_t* __restrict__ s2,
+                             const float* __restrict__ cov2, float* __restrict__ params,
+                             float* __restrict__ chi2, int32_t* __restrict__ iters,
+                             int32_t* __restrict__ status, float* __restrict__ cov) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= *count) return;
+  const int64_t p = index[j];
+  iters[p] += i2[j];
+  const int sp = s2[j];
+  const bool plain_ok = (sp != VFISV_PIX_NAN_STATE) && isfinite(c2[j]);
+  const bool nn_ok = (status[p] != VFISV_PIX_NAN_STATE) && isfinite(chi2[p]);
+  if (plain_ok && (!nn_ok || c2[j] < chi2[p])) {
+    for (int q = 0; q < 10; ++q) params[p * 10 + q] = p2[j * 10 + q];
+    chi2[p] = c2[j];
+    status[p] = sp;
+    if (cov && cov2)
+      for (int q = 0; q < 100; ++q) cov[p * 100 + q] = cov2[j * 100 + q];
+  }
+}
+
+cudaError_t merge_plain(const int64_t* count, const int64_t* index, int64_t npix_max,
+                        const float* p2, const float* c2, const int32_t* i2, const int32_t* s2,
+                        const float* cov2, float* params, float* chi2, int32_t* iters,
+                        int32_t* status, float* cov, cudaStream_t s) {
+  const unsigned nb = (unsigned)((npix_max + 255) / 256);
+  merge_kernel<<<nb, 256, 0, s>>>(count, index, p2, c2, i2, s2, cov2, params, chi2, iters, status,
+                                  cov);
+  return cudaGetLastError();
+}
+
+}  // namespace nn
+}  // namespace vfisv

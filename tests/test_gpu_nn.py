@@ -1,0 +1,163 @@
+"""The initial-guess network on the GPU vs the FP64 oracle, its training, and
+what it gains over plain Levenberg-Marquardt.
+
+Tolerances for the BF16 tensor-core kernels (8-bit mantissa operands, FP32
+accumulation) against FP64: raw outputs within 0.05 (standardised units),
+loss within 2 %, every layer's gradient within 5 % relative L2 error.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import lm, me, mlp
+from gpu_common import LINE, T, X, f32, vf  # noqa: F401
+
+pytestmark = pytest.mark.gpu
+
+
+def _oracle_set(n, seed):
+    p = f32(W.training_params(n, seed))
+    s = me.synth(p, f32(T), f32(X), LINE).reshape(n, -1)
+    obs, w = W.observe(s, p, W.noise(n, 24, seed))
+    return p, f32(obs), f32(w)
+
+
+def _random_blob(seed, obs, params):
+    rng = np.random.default_rng(seed)
+    weights = [(rng.uniform(-1, 1, (a, b)) * np.sqrt(6.0 / a), rng.normal(0, 0.05, b))
+               for a, b in zip(mlp.LAYERS[:-1], mlp.LAYERS[1:])]
+    return f32(mlp.pack(weights, mlp.statistics(obs, params)))
+
+
+def test_init_statistics_match_oracle(vf):
+    v, h, torch = vf
+    p, obs, w = _oracle_set(4096, 40)
+    blob = v.vfisv_nn_init(h, obs.astype(np.float32), p.astype(np.float32), seed=7)
+    _, st = mlp.unpack(blob)
+    ref = mlp.statistics(obs, p)
+    for k in ref:
+        np.testing.assert_allclose(st[k], ref[k], rtol=2e-4, atol=1e-6)
+    lay = mlp.blob_layout()
+    W0 = blob[lay["W0"][0]:lay["W0"][0] + 24 * 256]
+    assert np.abs(W0).max() <= np.sqrt(6 / 24) and abs(W0.mean()) < 0.02
+    assert np.all(blob[lay["b0"][0]:lay["b0"][0] + 256] == 0)
+
+
+def test_forward_and_gradient_vs_oracle(vf):
+    v, h, torch = vf
+    p, obs, w = _oracle_set(1000, 41)
+    blob = _random_blob(1, obs, p)
+    L_ref, g_ref, y_ref = mlp.loss_and_grad(blob, obs, p)
+    r = v.vfisv_nn_infer(h, blob.astype(np.float32), obs.astype(np.float32), LINE, want_raw=True)
+    assert np.abs(r["raw"] - y_ref).max() < 0.05
+    loss, g = v.vfisv_nn_grad(h, blob.astype(np.float32), obs.astype(np.float32),
+                              p.astype(np.float32))
+    assert abs(loss[0] / L_ref - 1) < 2e-2
+    lay = mlp.blob_layout()
+    for name in ("W0", "b0", "W1", "b1", "W2", "b2", "W3", "b3"):
+        o, shp = lay[name]
+        n = int(np.prod(shp))
+        a, b = g[o:o + n].astype(np.float64), g_ref[o:o + n]
+        rel = np.linalg.norm(a - b) / np.linalg.norm(b)
+        assert rel < 5e-2, (name, rel)
+
+
+def test_decoded_guesses_vs_oracle(vf):
+    v, h, torch = vf
+    p, obs, w = _oracle_set(512, 42)
+    blob = _random_blob(2, obs, p)
+    r = v.vfisv_nn_infer(h, blob.astype(np.float32), obs.astype(np.float32), LINE, want_raw=True)
+    _, st = mlp.unpack(blob)
+    # decode the GPU's own raw outputs in FP64: checks the decoding kernel alone
+    m = mlp.decode(r["raw"].astype(np.float64), obs, st)
+    ok = np.abs(np.cos(np.radians(m[:, 1]))) < 0.999  # away from the arccos poles
+    np.testing.assert_allclose(r["init"][:, [0, 3, 4, 5, 6, 7, 8]], m[:, [0, 3, 4, 5, 6, 7, 8]],
+                               rtol=2e-5, atol=2e-3)
+    np.testing.assert_allclose(r["init"][ok, 1], m[ok, 1], atol=2e-3)
+    dpsi = np.abs(np.mod(r["init"][:, 2] - m[:, 2] + 90, 180) - 90)
+    assert dpsi.max() < 2e-3
+
+
+def _gpu_training_set(v, h, torch, n, seed):
+    dev = torch.device("cuda:0")
+    p = W.training_params(n, seed).astype(np.float32)
+    tp = torch.tensor(p, device=dev)
+    tf = torch.tensor(T, dtype=torch.float32, device=dev)
+    tx = torch.tensor(X, dtype=torch.float32, device=dev)
+    s = v.vfisv_synth(h, tp, tf, tx, LINE).reshape(n, 24)
+    g = torch.Generator(device=dev)
+    g.manual_seed(seed)
+    sig = 1e-3 * (tp[:, 7] + tp[:, 8])[:, None]
+    obs = s + sig * torch.randn(n, 24, device=dev, generator=g)
+    return tp, obs.contiguous(), tf, tx
+
+
+def test_training_reduces_loss(vf):
+    v, h, torch = vf
+    tp, obs, tf, tx = _gpu_training_set(v, h, torch, 65536, 43)
+    blob = v.vfisv_nn_init(h, obs, tp, seed=3)
+    loss = v.vfisv_nn_train(h, blob, obs, tp, batch=4096, epochs=6, lr0=1e-3, seed=5)
+    v.vfisv_check(h)
+    l = loss.cpu().numpy()
+    assert np.all(np.isfinite(l))
+    assert l[-8:].mean() < 0.5 * l[:4].mean(), (l[:4], l[-8:])
+
+
+def test_network_gain_over_plain_lm(vf):
+    """Trained on 1M GPU-synthesised profiles, the network's guesses make the
+    inversion of a held-out map converge in fewer iterations, and the mixed
+    result (NN + LM, flagged pixels re-inverted plainly) matches or beats
+    plain LM's chi2 for nearly every pixel."""
+    v, h, torch = vf
+    tp, obs, tf, tx = _gpu_training_set(v, h, torch, 1 << 20, W.SEEDS["nn_train"])
+    blob = v.vfisv_nn_init(h, obs, tp, seed=11)
+    v.vfisv_nn_train(h, blob, obs, tp, batch=8192, epochs=4, lr0=1e-3, seed=12)
+    del obs
+    n = 16384
+    hp, hobs, _, _ = _gpu_training_set(v, h, torch, n, W.SEEDS["nn_heldout"])
+    sig = 1e-3 * (hp[:, 7] + hp[:, 8])[:, None]
+    wts = (1.0 / (sig * sig)).expand(n, 24).contiguous()
+    plain = v.vfisv_invert(h, hobs, wts, tf, tx, LINE)
+    mixed = v.vfisv_invert_nn(h, blob, hobs, wts, tf, tx, LINE, chi2_flag=3.0)
+    nn_only = v.vfisv_invert(h, hobs, wts, tf, tx, LINE,
+                             init=v.vfisv_nn_infer(h, blob, hobs, LINE)["init"],
+                             config={"max_iter": 20})
+    v.vfisv_check(h)
+    c = lambda st: ((st == 0) | (st == 2)).float().mean().item()  # noqa: E731
+    it_plain = plain["iters"].float().mean().item()
+    it_nn = nn_only["iters"].float().mean().item()
+    better = (mixed["chi2"] <= plain["chi2"] * (1 + 1e-3)).float().mean().item()
+    print(f"plain: conv {c(plain['status']):.3f} iters {it_plain:.1f}; NN-init: conv "
+          f"{c(nn_only['status']):.3f} iters {it_nn:.1f}; mixed conv {c(mixed['status']):.3f} "
+          f"flagged {mixed['flagged'].float().mean().item():.3f}; chi2 <= plain: {better:.3f}")
+    assert it_nn < 0.7 * it_plain
+    assert c(mixed["status"]) >= c(plain["status"])
+    assert better >= 0.9
+
+
+def test_mixed_first_stage_vs_oracle(vf):
+    """LM from the network's guess vs the oracle's LM from its own FP64
+    evaluation of the same network."""
+    v, h, torch = vf
+    p, obs, w = _oracle_set(2048, 44)
+    tp, gobs, tf, tx = _gpu_training_set(v, h, torch, 131072, 45)
+    blob = v.vfisv_nn_init(h, gobs, tp, seed=1)
+    v.vfisv_nn_train(h, blob, gobs, tp, batch=4096, epochs=4, lr0=1e-3, seed=2)
+    blob = blob.cpu().numpy()
+    n = 600
+    o, ww = obs[:n], w[:n]
+    weights, st = mlp.unpack(blob)
+    y, _ = mlp.forward(weights, mlp.features(o, st))
+    init_ref = mlp.decode(y, o, st)
+    r = v.vfisv_nn_infer(h, blob, o.astype(np.float32), LINE)
+    # the GPU's BF16 guess and the oracle's FP64 guess agree closely ...
+    assert np.median(np.abs(r["init"][:, 0] - init_ref[:, 0])) < 30.0
+    # ... and LM from the oracle's guess on both sides converges to the same chi2
+    init = f32(init_ref)
+    g = v.vfisv_invert(h, o.astype(np.float32), ww.astype(np.float32), T.astype(np.float32),
+                       X.astype(np.float32), LINE, init=init.astype(np.float32),
+                       config={"max_iter": 20})
+    ref = lm.invert(o, ww, f32(T), f32(X), LINE, init=init, max_iter=20)
+    both = np.isin(g["status"], (0, 2)) & np.isin(ref["status"], (0, 2))
+    rel = np.abs(g["chi2"][both] / ref["chi2"][both] - 1)
+    assert both.mean() > 0.5 and np.mean(rel <= 1e-3) >= 0.98

@@ -63,3 +63,55 @@ def test_adam_first_step_and_cosine():
     assert abs(mlp.cosine_lr(1e-3, 50, 100) - 5e-4) < 1e-15
     assert mlp.cosine_lr(1e-3, 100, 100) == 0.0
     assert math.isclose(mlp.cosine_lr(1e-3, 25, 100), 1e-3 * 0.5 * (1 + math.cos(math.pi / 4)))
+
+
+def test_blob_layout_matches_header():
+    import re, os
+    hdr = open(os.path.join(os.path.dirname(__file__), "..", "include", "vfisv.h")).read()
+    ntrain = int(re.search(r"VFISV_NN_NTRAIN (\d+)", hdr).group(1))
+    nblob = int(re.search(r"VFISV_NN_NBLOB (\d+)", hdr).group(1))
+    lay = mlp.blob_layout()
+    assert lay["_total"][0] == nblob and lay["in_mean"][0] == ntrain
+
+
+def test_decode_inverts_targets():
+    """decode(standardised targets) recovers the model (psi mod 180)."""
+    import workloads as W
+    from oracle import me
+    p = W.quiet_and_active_params(200, 31)
+    x = W.wavelength_grid()
+    obs = me.synth(p, W.hmi_filters(x), x, W.FE6173).reshape(200, -1)
+    st = mlp.statistics(obs, p)
+    t = mlp.targets(p, obs, st)
+    y = np.concatenate([t, np.zeros((200, 1))], axis=1)
+    m = mlp.decode(y, obs, st)
+    np.testing.assert_allclose(m[:, [0, 1, 3, 4, 5, 6, 7, 8]], p[:, [0, 1, 3, 4, 5, 6, 7, 8]],
+                               rtol=1e-9, atol=1e-9)
+    np.testing.assert_allclose(np.mod(m[:, 2] - p[:, 2] + 90, 180) - 90, 0, atol=1e-9)
+    f = mlp.features(obs, st)
+    np.testing.assert_allclose(f.mean(0), 0, atol=1e-9)
+    np.testing.assert_allclose(f.std(0), 1, rtol=1e-9)
+
+
+def test_blob_gradient_vs_finite_differences():
+    rng = np.random.default_rng(5)
+    import workloads as W
+    p = W.quiet_and_active_params(16, 32)
+    obs = rng.normal(0.5, 0.1, (16, 24))
+    obs[:, :6] = np.abs(obs[:, :6]) + 0.5
+    st = mlp.statistics(obs, p)
+    weights = [(rng.normal(0, 0.1, (a, b)), rng.normal(0, 0.05, b))
+               for a, b in zip(mlp.LAYERS[:-1], mlp.LAYERS[1:])]
+    blob = mlp.pack(weights, st)
+    L, g, y = mlp.loss_and_grad(blob, obs, p)
+    lay = mlp.blob_layout()
+    c0 = mlp.confidence_target(y, mlp.targets(p, obs, st))
+    for name, idx in (("W0", 5), ("b1", 3), ("W2", 777), ("W3", 40), ("b3", 10)):
+        o = lay[name][0] + idx
+        bp, bm = blob.copy(), blob.copy()
+        bp[o] += 1e-6
+        bm[o] -= 1e-6
+        f = lambda b: mlp.loss_and_grad_output(mlp.forward(mlp.unpack(b)[0], mlp.features(obs, st))[0],  # noqa: E731
+                                               mlp.targets(p, obs, st), c0)[0]
+        fd = (f(bp) - f(bm)) / 2e-6
+        assert abs(fd - g[o]) < 1e-6 * max(1.0, abs(fd)), (name, fd, g[o])
