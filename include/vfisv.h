@@ -209,6 +209,40 @@ int vfisv_invert_nn(vfisv_handle* h, const float* blob, const float* obs, const 
                     int32_t* iters_out, int32_t* status_out, float* cov_out,
                     int32_t* flagged_out, void* stream);
 
+/* Allocation-free variant of vfisv_invert.  The paper has no counterpart:
+ * this entry point exists for callers that cannot call cudaMalloc -- code
+ * that runs inside a host framework owning all device memory through its
+ * own pool (a cudaMalloc would bypass the pool's accounting and its hard
+ * cap), and real-time pipelines that allocate everything up front because a
+ * cudaMalloc or cudaFree can synchronise the device and stall their other
+ * streams.  It takes no handle and allocates nothing: the kernel's scratch
+ * (pixel-slot normal equations, work-queue counter, error word, packed
+ * filter table) is a fixed array of VFISV_NOALLOC_SCRATCH_BYTES (about
+ * 8.1 MiB) compiled into the library; every GPU that loads the library
+ * holds it until the process exits.
+ *   - All pointers must be device memory; arguments and outputs are those
+ *     of vfisv_invert, on the current CUDA device, asynchronous on `stream`.
+ *   - nlam <= VFISV_NOALLOC_MAX_NLAM (4096) and nfilt == 6, else
+ *     VFISV_E_SIZE / VFISV_E_UNSUPPORTED.  Any npix works: at most
+ *     VFISV_NOALLOC_MAX_SLOTS pixels are resident at once and the others
+ *     queue behind them.
+ *   - The first call on a device looks up the array's device address and
+ *     uploads the kernel's constants (blocking calls): make that first call
+ *     before any stream capture.
+ *   - Every call, from any thread or stream, shares the one array: calls
+ *     whose kernels overlap on the GPU race and corrupt each other's
+ *     results; serialise them (one stream, or events).  Each call resets the
+ *     work-queue counter itself; the rest of the array is overwritten before
+ *     it is read. */
+#define VFISV_NOALLOC_MAX_NLAM 4096
+#define VFISV_NOALLOC_MAX_SLOTS 38912
+#define VFISV_NOALLOC_SCRATCH_BYTES 8536576
+int vfisv_invert_noalloc(const float* obs, const float* weights, int32_t weights_per_pixel,
+                         const float* filters, int32_t nfilt, const float* wl_mA, int32_t nlam,
+                         const vfisv_line* line, const float* init, const vfisv_config* cfg,
+                         int64_t npix, float* params_out, float* chi2_out, int32_t* iters_out,
+                         int32_t* status_out, float* cov_out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif
