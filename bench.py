@@ -1,17 +1,31 @@
-"""Benchmark: converged pixels/s of the GB300 Milne-Eddington inversion.
+"""Benchmark: converged pixels/s of the GB300 Milne-Eddington inversion,
+NN-initialised mixed inversion vs plain Levenberg-Marquardt.
 
-Default workload (N=1): the 1024x1024 plain-LM map -- 1,048,576 pixels,
-Fe I 6173.34 A (g_eff = 2.5), 149 wavelengths at 10 mA over +-740 mA, 6 HMI-like
-filters (24 observables), per-pixel parameters drawn from the uniform
-distributions, Gaussian noise sigma = 1e-3 Ic, LM from the standard guess with
-a 50-iteration cap, covariance requested.  A step is one vfisv_invert call
-over the whole map (synthetic observations already resident in HBM).
+Default workload (N=1): the 4096x4096 full-disk synthetic map -- 13,457,608
+on-disk pixels (disk radius 2073 px), 90 % quiet Sun (B ~ U[0,200] G) and
+Gaussian active-region blobs (B up to 3500 G); Fe I 6173.34 A (g_eff 2.5),
+149 wavelengths at 10 mA, 6 HMI-like filters (24 observables), noise
+sigma = 1e-3 Ic.  `--workload map1024` selects the 1024x1024 map with the
+uniform parameter distributions instead.
 
-With --impl reference the FP64 CPU oracle is timed instead on a bounded
-sample of the same workload (that is the only other place it runs here).
+A step is one full-map inversion with the observations resident in HBM:
+  value:      vfisv_invert_nn -- network guess, LM, then plain LM (cap 50)
+              re-inversion of flagged pixels, lower chi2 kept; covariance on.
+              Full disk: LM cap 50 from the network's guess (the plain run's
+              budget), flag = chi2 > 2.5 (a fit worse than the noise allows:
+              P(chi2_15/15 > 2.5) = 0.15 %).  1024x1024 map: LM cap 20, flag =
+              not converged or chi2 > 3;
+  plain_lm:   vfisv_invert from the standard guess (cap 50), covariance on.
+The network is trained before timing (4M profiles synthesised by the
+library, 8 epochs) and the training time is reported beside the numbers.
+`e2e` repeats the mixed step through the same public call with pinned host
+buffers (host->device copies of observations and weights and the copy back
+of all outputs inside the timed region).
 
-Multi-GPU: pixels are independent, so N ranks invert N independent maps
-(weak scaling, no collective on the data path).
+With --impl reference the FP64 CPU oracle (plain LM) is timed instead on a
+bounded sample of the same map.  Multi-GPU: pixels are independent, so N
+ranks invert N independent maps (weak scaling, no collective on the data
+path).
 """
 from __future__ import annotations
 
@@ -33,18 +47,18 @@ import workloads as W  # noqa: E402
 
 NLAM, NF = 149, 6
 METRIC = "converged pixels/s on 1 GB300 at oracle-matched chi2: NN-init mixed vs plain LM"
-MAXITER = 50
+PLAIN_CAP = 50
+# (LM cap after the network's guess, chi2 flag, flag unconverged pixels too)
+MIXED = {"disk": (50, 2.5, False), "map1024": (20, 3.0, True)}
+TRAIN_N, TRAIN_EPOCHS, TRAIN_BATCH = 1 << 22, 8, 8192
 
-# Algorithmic FP32 flops of one fused pass (synthesis + 6-column Jacobian +
-# filtering) per wavelength point, from the op count of the formulas
-# (FMA = 2 flops): Faddeeva (Weideman, N=16) 3 x 135, absorption matrix 26,
-# Unno-Rachkovsky 31, Stokes filtering 48, Eqs. 8-9 27, Delta partials 13,
+# Algorithmic FP32 flops of one fused LM pass (synthesis + 6-column Jacobian
+# + filtering) per wavelength point, from the op count of the formulas
+# (FMA = 2 flops): Faddeeva (Weideman, 16 terms) 3 x 135, absorption matrix
+# 26, Unno-Rachkovsky 31, Stokes filtering 48, Eqs. 8-9 27, Delta partials 13,
 # 20 Stokes partials 90, 6 parameter chains 654.
 FLOP_PER_LAMBDA = 3 * 135 + 26 + 31 + 48 + 27 + 13 + 90 + 654
-# per pass, outside the wavelength loop: model 60, chi2 (FP64) 72, and on an
-# accepted pass the compensated normal equations 24 x 54 x 8.
-FLOP_PER_PASS = 60
-FLOP_PER_ACCEPT = 24 * 54 * 8
+FLOP_PER_PASS_EXTRA = 60  # model and residual outside the wavelength loop
 
 
 def fp32_peak_tflops(sm_mhz: float, nsm: int = 152) -> float:
@@ -69,8 +83,7 @@ class ClockSampler:
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
                  "--format=csv,noheader,nounits", "-lms", "200"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
-            self.t = threading.Thread(target=self._read, daemon=True)
-            self.t.start()
+            threading.Thread(target=self._read, daemon=True).start()
         except Exception:
             self.proc = None
 
@@ -87,20 +100,23 @@ class ClockSampler:
         except Exception:
             self.proc.kill()
         rows = [r for r in self.rows if len(r) >= 9]
-        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        num = lambda x: x.replace(".", "", 1).isdigit()  # noqa: E731
+        sm = [float(r[1]) for r in rows if num(r[1])]
+        mx = [float(r[2]) for r in rows if num(r[2])]
+        pw = [float(r[3]) for r in rows if num(r[3])]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = sorted({names[j] for r in rows for j in range(4) if r[5 + j].lower() == "active"})
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
-                "samples": len(rows)}
+                "power_w_max": max(pw) if pw else None, "samples": len(rows)}
 
 
-def make_map(npix: int, seed: int):
-    p = W.quiet_and_active_params(npix, seed)
-    x = W.wavelength_grid(NLAM)
-    T = W.hmi_filters(x)
-    return p, x, T
+def map_params(workload: str, rank: int):
+    if workload == "disk":
+        p, _ = W.full_disk_params(W.SEEDS["disk"] + 1000 * rank)
+        return p, W.SEEDS["disk"] + 1000 * rank
+    n = 1024 * 1024
+    return W.quiet_and_active_params(n, W.SEEDS["map1024"] + 1000 * rank), W.SEEDS["map1024"] + 1000 * rank
 
 
 def run_ours(args, rank, world):
@@ -109,130 +125,215 @@ def run_ours(args, rank, world):
     import paper_0901_2702_gb300 as v
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
-    side = args.side
-    npix = side * side
-    seed = W.SEEDS["map1024"] + 1000 * rank
-    p, x, T = make_map(npix, seed)
     line = W.FE6173
+    x = W.wavelength_grid(NLAM)
+    T = W.hmi_filters(x)
     h = v.vfisv_create(dev.index)
-    tf = torch.tensor(T, dtype=torch.float32, device=dev)
-    tx = torch.tensor(x, dtype=torch.float32, device=dev)
-    tp = torch.tensor(p, dtype=torch.float32, device=dev)
-    syn = v.vfisv_synth(h, tp, tf, tx, line).reshape(npix, 4 * NF)
-    nz = torch.tensor(W.noise(npix, 4 * NF, seed), dtype=torch.float32, device=dev)
-    sig = (1e-3 * torch.tensor(W.continuum(p), dtype=torch.float32, device=dev))[:, None]
-    obs = (syn + sig * nz).contiguous()
+    t32 = lambda a: torch.tensor(np.asarray(a, dtype=np.float32), device=dev)  # noqa: E731
+    tf, tx = t32(T), t32(x)
+
+    # --- train the initial-guess network on profiles synthesised by the library
+    t0 = time.perf_counter()
+    tp = t32(W.training_params(TRAIN_N, W.SEEDS["nn_train"]))
+    tobs = v.vfisv_synth(h, tp, tf, tx, line).reshape(TRAIN_N, 4 * NF)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(W.SEEDS["nn_train"])
+    tobs += 1e-3 * (tp[:, 7] + tp[:, 8])[:, None] * torch.randn(TRAIN_N, 4 * NF, device=dev,
+                                                               generator=gen)
+    blob = v.vfisv_nn_init(h, tobs, tp, seed=11)
+    loss = v.vfisv_nn_train(h, blob, tobs, tp, batch=TRAIN_BATCH, epochs=TRAIN_EPOCHS,
+                            lr0=1e-3, seed=12)
+    v.vfisv_check(h)
+    train_s = time.perf_counter() - t0
+    final_loss = float(loss[-50:].mean().item())
+    del tp, tobs
+
+    # --- the map: synthetic observations resident in HBM
+    p, seed = map_params(args.workload, rank)
+    npix = p.shape[0]
+    tpm = t32(p)
+    syn = v.vfisv_synth(h, tpm, tf, tx, line).reshape(npix, 4 * NF)
+    sig = 1e-3 * (tpm[:, 7] + tpm[:, 8])[:, None]
+    obs = (syn + sig * t32(W.noise(npix, 4 * NF, seed))).contiguous()
     wts = (1.0 / (sig * sig)).expand(npix, 4 * NF).contiguous()
-    del syn, nz, tp
-    cfg = v.vfisv_config_default(max_iter=MAXITER)
-    out = {"params": torch.empty(npix, 10, device=dev), "chi2": torch.empty(npix, device=dev),
-           "iters": torch.empty(npix, dtype=torch.int32, device=dev),
-           "status": torch.empty(npix, dtype=torch.int32, device=dev),
-           "cov": torch.empty(npix, 10, 10, device=dev)}
+    del syn, tpm
+    NN_CAP, CHI2_FLAG, FLAG_UNCONV = MIXED[args.workload]
+    cfg_nn = v.vfisv_config_default(max_iter=NN_CAP)
+    cfg_plain = v.vfisv_config_default(max_iter=PLAIN_CAP)
+
+    def outputs(flag=True, cov=True):
+        o = {"params": torch.empty(npix, 10, device=dev), "chi2": torch.empty(npix, device=dev),
+             "iters": torch.empty(npix, dtype=torch.int32, device=dev),
+             "status": torch.empty(npix, dtype=torch.int32, device=dev),
+             "cov": torch.empty(npix, 10, 10, device=dev) if cov else None}
+        if flag:
+            o["flagged"] = torch.empty(npix, dtype=torch.int32, device=dev)
+        return o
+
     stream = torch.cuda.current_stream(dev)
+    out_m, out_p = outputs(True), outputs(False)
 
-    def step():
-        v.vfisv_invert(h, obs, wts, tf, tx, line, config=cfg, out=out, stream=stream)
+    def step_mixed():
+        v.vfisv_invert_nn(h, blob, obs, wts, tf, tx, line, config_nn=cfg_nn,
+                          config_plain=cfg_plain, chi2_flag=CHI2_FLAG,
+                          flag_unconverged=FLAG_UNCONV, out=out_m, stream=stream)
 
-    for _ in range(args.warmup):
-        step()
-    v.vfisv_check(h, stream)
+    def step_plain(out=out_p, cov=True):
+        v.vfisv_invert(h, obs, wts, tf, tx, line, config=cfg_plain, out=out, stream=stream)
+
+    def timed(fn, k, name):
+        # the NVTX range lets a profiler select exactly the timed launches
+        torch.cuda.nvtx.range_push(name)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(k):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+        return e0.elapsed_time(e1) / k
+
     dist = world > 1
+    for _ in range(args.warmup):
+        step_mixed()
+    v.vfisv_check(h, stream)
     if dist:
         import torch.distributed as tdist
         tdist.barrier()
     torch.cuda.synchronize()
     clk = ClockSampler(dev.index)
     clk.start()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    conv = 0
-    passes = 0
-    accepts_est = 0
-    e0.record(stream)
-    for _ in range(args.steps):
-        step()
-    e1.record(stream)
-    torch.cuda.synchronize()
+    ms_mixed = timed(step_mixed, args.steps, "timed_mixed")
     clocks = clk.stop()
     v.vfisv_check(h, stream)
-    ms = e0.elapsed_time(e1) / args.steps
-    st = out["status"]
-    conv = int(((st == 0) | (st == 2)).sum().item())
-    it = out["iters"].to(torch.int64)
-    passes = int((it + 1).sum().item())
+    # plain LM on the same map (its own warm-up), then the LM kernel alone
+    # (no covariance) for the roofline
+    step_plain()
+    ms_plain = timed(step_plain, max(1, min(args.steps, 2)), "timed_plain")
+    out_r = outputs(False, cov=False)
+    step_plain(out_r)
+    ms_lm = timed(lambda: step_plain(out_r), 1, "timed_lm")
+    v.vfisv_check(h, stream)
+
+    conv = lambda o: int(((o["status"] == 0) | (o["status"] == 2)).sum().item())  # noqa: E731
+    conv_m, conv_p = conv(out_m), conv(out_p)
     if dist:
         import torch.distributed as tdist
-        t = torch.tensor([ms], device=dev)
+        t = torch.tensor([ms_mixed, ms_plain], device=dev)
         tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-        ms = float(t.item())
-        c = torch.tensor([conv], device=dev, dtype=torch.int64)
+        ms_mixed, ms_plain = (float(a) for a in t.tolist())
+        c = torch.tensor([conv_m, conv_p], device=dev, dtype=torch.int64)
         tdist.all_reduce(c)
-        conv_total = int(c.item())
+        conv_m_tot, conv_p_tot = (int(a) for a in c.tolist())
     else:
-        conv_total = conv
-    value = conv_total / (ms / 1e3)
+        conv_m_tot, conv_p_tot = conv_m, conv_p
+    value = conv_m_tot / (ms_mixed / 1e3)
+    plain_value = conv_p_tot / (ms_plain / 1e3)
+    better = float((out_m["chi2"] <= out_p["chi2"] * (1 + 1e-3)).float().mean().item())
+    better2 = float((out_m["chi2"] <= out_p["chi2"] * (1 + 1e-2)).float().mean().item())
+    ratio_med = float((out_m["chi2"] / out_p["chi2"]).median().item())
+    passes = int((out_r["iters"].to(torch.int64) + 1).sum().item())
+    flops = passes * (NLAM * FLOP_PER_LAMBDA + FLOP_PER_PASS_EXTRA)
+    sm_mhz = clocks.get("sm_mhz") or 2070.0
+    achieved = flops / (ms_lm / 1e3) / 1e12
+    peak = fp32_peak_tflops(2070.0)
 
-    # end to end: the same call with pinned host buffers, copies inside the timed region
+    # end to end: pinned host buffers through the same public call
     obs_h = obs.cpu().pin_memory()
     wts_h = wts.cpu().pin_memory()
-    T32 = tf.cpu().pin_memory()
-    x32 = tx.cpu().pin_memory()
-    outh = {k: torch.empty(tuple(t_.shape), dtype=t_.dtype).pin_memory() for k, t_ in out.items()}
-    v.vfisv_invert(h, obs_h, wts_h, T32, x32, line, config=cfg, out=outh)  # warm staging
-    t0 = time.perf_counter()
-    ne2e = max(1, min(args.steps, 3))
-    for _ in range(ne2e):
-        v.vfisv_invert(h, obs_h, wts_h, T32, x32, line, config=cfg, out=outh)
-    e2e_s = (time.perf_counter() - t0) / ne2e
-    st_h = outh["status"]
-    conv_h = int(((st_h == 0) | (st_h == 2)).sum().item())
-    h2d = sum(t_.numel() * t_.element_size() for t_ in (obs_h, wts_h, T32, x32))
-    d2h = sum(t_.numel() * t_.element_size() for t_ in outh.values())
+    tf_h, tx_h = tf.cpu().pin_memory(), tx.cpu().pin_memory()
+    blob_h = blob.cpu().pin_memory()
+    outh = {k: (torch.empty(tuple(t_.shape), dtype=t_.dtype).pin_memory() if t_ is not None else None)
+            for k, t_ in out_m.items()}
 
-    flops = passes * (NLAM * FLOP_PER_LAMBDA + FLOP_PER_PASS)
-    achieved = flops / (ms / 1e3) / 1e12
-    peak = fp32_peak_tflops(2070.0)
+    def step_e2e():
+        v.vfisv_invert_nn(h, blob_h, obs_h, wts_h, tf_h, tx_h, line, config_nn=cfg_nn,
+                          config_plain=cfg_plain, chi2_flag=CHI2_FLAG,
+                          flag_unconverged=FLAG_UNCONV, out=outh)
+
+    step_e2e()
+    ne = max(1, min(args.steps, 2))
+    t0 = time.perf_counter()
+    for _ in range(ne):
+        step_e2e()
+    e2e_s = (time.perf_counter() - t0) / ne
+    conv_h = int(((outh["status"] == 0) | (outh["status"] == 2)).sum().item())
+    h2d = sum(t_.numel() * t_.element_size() for t_ in (obs_h, wts_h, tf_h, tx_h, blob_h))
+    d2h = sum(t_.numel() * t_.element_size() for t_ in outh.values() if t_ is not None)
+
+    wl = ("full-disk 4096x4096 map, 13,457,608 on-disk pixels (90 % quiet Sun, active-region "
+          "blobs)" if args.workload == "disk" else "1024x1024 map, uniform parameter draws")
     res = {
         "metric": METRIC, "value": value, "unit": "pixels/s", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
-        "data": "synthetic (seeded ME parameters, GPU-synthesised Stokes + Gaussian noise)",
-        "config": {"workload": f"plain LM, {side}x{side} map, Fe I 6173 A, 6 filters x 149 lambda, "
-                               f"cap {MAXITER}, standard initial guess, covariance on",
-                   "pixels_per_gpu": npix, "l2": "inputs 192 MB > 129 MB L2 (no flush)",
-                   "parallelism": f"replicas x{world}"},
-        "converged_fraction": conv / npix, "mean_iterations": float(it.float().mean().item()),
-        "e2e": {"value": conv_h / e2e_s * world, "unit": "pixels/s",
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_mixed,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 synthesis/Jacobian, f64 solve/chi2, bf16 network",
+        "data": "synthetic (seeded ME parameters, library-synthesised Stokes + Gaussian noise)",
+        "config": {"workload": f"NN-initialised mixed inversion of the {wl}: Fe I 6173 A, "
+                               f"6 filters x 149 wavelengths, network guess + LM cap {NN_CAP}, "
+                               f"plain LM cap {PLAIN_CAP} for pixels with chi2 > {CHI2_FLAG}"
+                               + (" or not converged" if FLAG_UNCONV else "")
+                               + "; vs plain LM cap 50 from the standard guess; covariance on",
+                   "pixels_per_gpu": npix,
+                   "l2": "inputs 2.6 GB > 129 MB L2 (no flush needed)" if args.workload == "disk"
+                   else "inputs 201 MB > 129 MB L2 (no flush needed)",
+                   "parallelism": f"independent maps x{world}"},
+        "converged_fraction": conv_m / npix,
+        "mean_iterations": float(out_m["iters"].float().mean().item()),
+        "flagged_fraction": float(out_m["flagged"].float().mean().item()),
+        "plain_lm": {"value": plain_value, "unit": "pixels/s", "ms_per_step": ms_plain,
+                     "converged_fraction": conv_p / npix,
+                     "mean_iterations": float(out_p["iters"].float().mean().item())},
+        "mixed_over_plain": value / plain_value,
+        "chi2_mixed_le_plain_frac": better,
+        "chi2_mixed_le_plain_1pct_frac": better2,
+        "chi2_mixed_over_plain_median": ratio_med,
+        "train": {"profiles": TRAIN_N, "epochs": TRAIN_EPOCHS, "batch": TRAIN_BATCH,
+                  "seconds_incl_synthesis": train_s, "final_loss": final_loss},
+        "e2e": {"value": conv_h * world / e2e_s, "unit": "pixels/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "gpu_launches": 2 * args.steps,
+        "gpu_launches": None,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": None,
-                     "note": "FP32 pipe peak = 152 SM x 128 lanes x 2 x 2070 MHz; algorithmic "
-                             "flops = passes x (149 x %d + %d)" % (FLOP_PER_LAMBDA, FLOP_PER_PASS)},
+                     "kernel": "invert_kernel<6> (plain LM pass, no covariance)",
+                     "kernel_ms": ms_lm,
+                     "note": "peak = FP32 pipe, 152 SM x 128 lanes x 2 flop x 2070 MHz (no "
+                             "measured FP32 peak in MEASURED_PEAKS.json); algorithmic flops = "
+                             f"passes x (149 x {FLOP_PER_LAMBDA} + {FLOP_PER_PASS_EXTRA}); "
+                             f"frac at the sampled {sm_mhz:.0f} MHz clock = "
+                             f"{achieved / fp32_peak_tflops(sm_mhz):.3f}"},
         "clocks": clocks,
     }
+    # our kernel launches per mixed step: network (pack + per 65536-pixel chunk:
+    # features, 4 GEMMs, decode), 2 x (table pack, LM, covariance), flag, merge
+    chunks = (npix + 65535) // 65536
+    res["gpu_launches"] = args.steps * (1 + 6 * chunks + 2 * 3 + 2)
     h.close()
     return res
 
 
 def cpu_baseline(args, sample: int):
-    """The FP64 oracle timed on the host, on a bounded sample of the same map."""
+    """The FP64 oracle (plain LM) on the host, on a bounded sample of the map."""
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
     code = f"""
 import sys, time, json
 sys.path.insert(0, {ROOT!r})
 import numpy as np, workloads as W
 from oracle import me, lm
-side = {args.side}; npix = side*side; n = {sample}
-p = W.quiet_and_active_params(npix, W.SEEDS['map1024'])
+wl = {args.workload!r}
+if wl == 'disk':
+    p, _ = W.full_disk_params(W.SEEDS['disk']); seed = W.SEEDS['disk']
+else:
+    p = W.quiet_and_active_params(1024 * 1024, W.SEEDS['map1024']); seed = W.SEEDS['map1024']
+npix = p.shape[0]; n = {sample}
 idx = np.linspace(0, npix - 1, n).astype(np.int64)
 x = W.wavelength_grid({NLAM}); T = W.hmi_filters(x)
-nz = W.noise(npix, 24, W.SEEDS['map1024'])[idx]
+nz = W.noise(npix, 24, seed)[idx]
 s = me.synth(p[idx], T, x, W.FE6173).reshape(n, -1)
 obs, w = W.observe(s, p[idx], nz)
 t0 = time.perf_counter()
-r = lm.invert(obs, w, T, x, W.FE6173, max_iter={MAXITER})
+r = lm.invert(obs, w, T, x, W.FE6173, max_iter={PLAIN_CAP})
 dt = time.perf_counter() - t0
 conv = int(np.sum((r['status'] == 0) | (r['status'] == 2)))
 print(json.dumps({{'value': conv / dt, 'seconds': dt, 'n': n}}))
@@ -243,22 +344,22 @@ print(json.dumps({{'value': conv / dt, 'seconds': dt, 'n': n}}))
                 "sample": f"failed: {out.stderr[-300:]}"}
     d = json.loads(out.stdout.strip().splitlines()[-1])
     return {"value": d["value"], "unit": "pixels/s", "cores": 1, "kind": "oracle",
-            "sample": f"{d['n']} pixels evenly spaced over the {args.side}x{args.side} map, "
+            "sample": f"{d['n']} pixels evenly spaced over the map, plain LM cap {PLAIN_CAP}, "
                       f"{d['seconds']:.1f} s, numpy/scipy FP64, 1 thread"}
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--side", type=int, default=1024)
+    ap.add_argument("--workload", default="disk", choices=["disk", "map1024"])
     ap.add_argument("--cpu-sample", type=int, default=384)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
-    world = int(os.environ.get("WORLD_SIZE", args.gpus if args.gpus == 1 else 1))
+    world = int(os.environ.get("WORLD_SIZE", 1))
 
     if args.impl == "reference":
         if rank != 0:
@@ -267,7 +368,7 @@ def main():
         res = {"metric": METRIC, "value": cb["value"], "unit": "pixels/s", "n_gpus": world,
                "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
                "impl": "reference", "dtype": "f64", "data": "synthetic",
-               "config": {"workload": f"plain LM, {args.side}x{args.side} map (bounded sample)"},
+               "config": {"workload": f"{args.workload} map, plain LM (bounded sample)"},
                "cpu_baseline": cb,
                "e2e": {"value": cb["value"], "unit": "pixels/s", "h2d_bytes_per_step": 0,
                        "d2h_bytes_per_step": 0}}

@@ -196,16 +196,18 @@ int vfisv_nn_infer(vfisv_handle* h, const float* blob, const float* obs, int64_t
                    const vfisv_line* line, float* init_out, float* conf_out, float* raw_out,
                    void* stream);
 
-/* Mixed inversion: network guess, LM with cfg_nn, then every pixel that did
- * not converge or ends with chi2 > chi2_flag is inverted again from the
- * standard guess with cfg_plain and keeps the lower-chi2 result.  Arguments
- * as vfisv_invert; iters_out counts the steps of both runs; flagged_out
- * (int32[npix], or NULL) marks the re-inverted pixels. */
+/* Mixed inversion: network guess, LM with cfg_nn, then every pixel that ends
+ * with chi2 > chi2_flag (or, with flag_unconverged, that did not converge)
+ * is inverted again from the standard guess with cfg_plain and keeps the
+ * lower-chi2 result.  Arguments as vfisv_invert; iters_out counts the steps
+ * of both runs; flagged_out (int32[npix], or NULL) marks the re-inverted
+ * pixels. */
 int vfisv_invert_nn(vfisv_handle* h, const float* blob, const float* obs, const float* weights,
                     int32_t weights_per_pixel, const float* filters, int32_t nfilt,
                     const float* wl_mA, int32_t nlam, const vfisv_line* line,
                     const vfisv_config* cfg_nn, const vfisv_config* cfg_plain,
-                    double chi2_flag, int64_t npix, float* params_out, float* chi2_out,
+                    double chi2_flag, int32_t flag_unconverged, int64_t npix,
+                    float* params_out, float* chi2_out,
                     int32_t* iters_out, int32_t* status_out, float* cov_out,
                     int32_t* flagged_out, void* stream);
 

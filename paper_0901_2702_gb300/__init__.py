@@ -89,7 +89,7 @@ def load():
     lib.vfisv_nn_infer.restype = ctypes.c_int
     lib.vfisv_invert_nn.argtypes = [P, P, P, P, I32, P, I32, P, I32, ctypes.POINTER(vfisv_line),
                                     ctypes.POINTER(vfisv_config), ctypes.POINTER(vfisv_config),
-                                    ctypes.c_double, I64, P, P, P, P, P, P, P]
+                                    ctypes.c_double, I32, I64, P, P, P, P, P, P, P]
     lib.vfisv_invert_nn.restype = ctypes.c_int
     _lib = lib
     return lib
@@ -320,9 +320,10 @@ def vfisv_nn_infer(h: Handle, blob, obs, line, want_conf=True, want_raw=False, s
 
 
 def vfisv_invert_nn(h: Handle, blob, obs, weights, filters, wl_mA, line, config_nn=None,
-                    config_plain=None, chi2_flag: float = 3.0, want_cov=True, out=None,
-                    stream=None):
-    """Mixed inversion: network guess + LM, plain LM re-inversion of flagged pixels."""
+                    config_plain=None, chi2_flag: float = 3.0, flag_unconverged: bool = True,
+                    want_cov=True, out=None, stream=None):
+    """Mixed inversion: network guess + LM, plain LM re-inversion of flagged pixels
+    (chi2 > chi2_flag, and with flag_unconverged also those that did not converge)."""
     npix = int(obs.shape[0])
     nfilt, nlam = int(filters.shape[0]), int(filters.shape[1])
     per_pixel = 1 if (len(weights.shape) >= 2 and int(weights.shape[0]) == npix and
@@ -344,7 +345,8 @@ def vfisv_invert_nn(h: Handle, blob, obs, weights, filters, wl_mA, line, config_
     ln = _line(line)
     rc = load().vfisv_invert_nn(h.ptr, ptrs[0][0], ptrs[1][0], ptrs[2][0], per_pixel, ptrs[3][0],
                                 nfilt, ptrs[4][0], nlam, ctypes.byref(ln), ctypes.byref(cn),
-                                ctypes.byref(cp_), float(chi2_flag), npix,
+                                ctypes.byref(cp_), float(chi2_flag), int(bool(flag_unconverged)),
+                                npix,
                                 *[p for _, (p, _k) in outs],
                                 ctypes.c_void_p(_stream(obs, stream)))
     _check(rc, "vfisv_invert_nn")

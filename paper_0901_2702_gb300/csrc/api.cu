@@ -514,7 +514,8 @@ int vfisv_invert_nn(vfisv_handle* h, const float* blob, const float* obs, const 
                     int32_t weights_per_pixel, const float* filters, int32_t nfilt,
                     const float* wl_mA, int32_t nlam, const vfisv_line* line,
                     const vfisv_config* cfg_nn, const vfisv_config* cfg_plain,
-                    double chi2_flag, int64_t npix, float* params_out, float* chi2_out,
+                    double chi2_flag, int32_t flag_unconverged, int64_t npix,
+                    float* params_out, float* chi2_out,
                     int32_t* iters_out, int32_t* status_out, float* cov_out,
                     int32_t* flagged_out, void* stream) {
   if (!blob || !cfg_plain) return VFISV_E_ARG;
@@ -581,8 +582,9 @@ int vfisv_invert_nn(vfisv_handle* h, const float* blob, const float* obs, const 
   int64_t* idx = (int64_t*)(mw + o_idx);
   float* og = (float*)(mw + o_obs);
   float* wg = weights_per_pixel ? (float*)(mw + o_w) : nullptr;
-  if (nn::flag_and_gather(d.status, d.chi2, npix, (float)chi2_flag, o, w, wstride, nobs, cnt,
-                          idx, og, wg, (int32_t*)st.bufs[10].dev, s) != cudaSuccess)
+  if (nn::flag_and_gather(d.status, d.chi2, npix, (float)chi2_flag, flag_unconverged != 0, o, w,
+                          wstride, nobs, cnt, idx, og, wg, (int32_t*)st.bufs[10].dev,
+                          s) != cudaSuccess)
     return VFISV_E_CUDA;
   DevInvert d2;
   d2.obs = og;

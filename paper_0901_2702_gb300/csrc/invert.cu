@@ -87,7 +87,7 @@ __device__ __noinline__ void jacobi_pinv(const double* Mp /*packed*/, const doub
       dia += a[i][i] * a[i][i];
       for (int j = i + 1; j < kNP; ++j) off += a[i][j] * a[i][j];
     }
-    if (!(off > 1e-32 * dia)) break;
+    if (!(off > 1e-26 * dia)) break;  // off-diagonal below ~3e-13 of the diagonal
     for (int p = 0; p < kNP - 1; ++p)
       for (int q = p + 1; q < kNP; ++q) {
         const double apq = a[p][q];
@@ -235,8 +235,11 @@ __device__ __noinline__ void damped_step(const float* scr, int64_t ns, uint32_t 
 
 // Covariance (J^T W J)^+ at the final model, in parameter units, from the
 // packed J^T W J at scr[e * ns].  Reads everything before writing `out`, so
-// `out` may hold the packed matrix itself.
-__device__ __noinline__ void covariance(const float* scr, int64_t ns, uint32_t free_mask, float* out) {
+// `out` may hold the packed matrix itself.  With try_only, returns false
+// without writing when the Cholesky factorisation fails (the caller then
+// runs the eigen-decomposition path for that pixel).
+__device__ __noinline__ bool covariance(const float* scr, int64_t ns, uint32_t free_mask,
+                                        float* out, bool try_only) {
   double L[kNPk], sc[kNP];
   bool held[kNP];
   scaled_system(scr, ns, free_mask, 0.0, L, sc, held);
@@ -250,6 +253,7 @@ __device__ __noinline__ void covariance(const float* scr, int64_t ns, uint32_t f
       for (int i = j; i < kNP; ++i) P[tri(i, j)] = x[i];
     }
   } else {
+    if (try_only) return false;
     scaled_system(scr, ns, free_mask, 0.0, L, sc, held);
     jacobi_pinv(L, nullptr, nullptr, P);
   }
@@ -260,6 +264,7 @@ __device__ __noinline__ void covariance(const float* scr, int64_t ns, uint32_t f
         v = (float)(sc[i] * sc[j] * ((i >= j) ? P[tri(i, j)] : P[tri(j, i)]));
       out[i * 10 + j] = v;
     }
+  return true;
 }
 
 // Weideman coefficients of this translation unit (set by invert_set_constants).
@@ -538,18 +543,47 @@ __global__ void __launch_bounds__(kInvThreads, 1) invert_kernel(InvertArgs A) {
 #undef ST
 }
 
-// Covariance of every pixel that finished with a model: one pixel per
-// thread; reads the packed J^T W J parked in the pixel's output row.
-__global__ void __launch_bounds__(128) covariance_kernel(float* cov, const int32_t* status,
-                                                         int64_t npix_max,
-                                                         const int64_t* npix_dev,
-                                                         uint32_t free_mask) {
+// Covariance of every pixel that finished with a model, from the packed
+// J^T W J parked in the pixel's output row.  Cholesky runs one pixel per
+// thread; the rare pixels whose matrix is numerically singular go to a
+// shared-memory queue and are drained by consecutive threads, so the costly
+// eigen-decomposition runs in (nearly) full warps instead of stalling every
+// warp that happens to hold one such pixel.
+constexpr int kCovThreads = 128;
+constexpr int kCovQueue = 2 * kCovThreads;
+__global__ void __launch_bounds__(kCovThreads) covariance_kernel(float* cov,
+                                                                 const int32_t* status,
+                                                                 int64_t npix_max,
+                                                                 const int64_t* npix_dev,
+                                                                 uint32_t free_mask) {
+  __shared__ int64_t queue[kCovQueue];
+  __shared__ int qn;
   const int64_t npix = npix_dev ? *npix_dev : npix_max;
-  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < npix;
-       p += (int64_t)gridDim.x * blockDim.x) {
-    const int st = status[p];
-    if (st == VFISV_PIX_CONVERGED || st == VFISV_PIX_MAXITER || st == VFISV_PIX_STALLED)
-      covariance(cov + p * 100, 1, free_mask, cov + p * 100);
+  if (threadIdx.x == 0) qn = 0;
+  __syncthreads();
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  // every thread of the block runs the same number of rounds
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < npix; base += stride) {
+    const int64_t p = base + threadIdx.x;
+    if (p < npix) {
+      const int st = status[p];
+      if (st == VFISV_PIX_CONVERGED || st == VFISV_PIX_MAXITER || st == VFISV_PIX_STALLED) {
+        if (!covariance(cov + p * 100, 1, free_mask, cov + p * 100, true)) {
+          const int slot = atomicAdd(&qn, 1);
+          queue[slot] = p;  // slot < kCovQueue: drained below before it can fill
+        }
+      }
+    }
+    __syncthreads();
+    const bool last = base + stride >= npix;
+    if (qn >= kCovThreads || last) {
+      const int n = qn;
+      for (int i = threadIdx.x; i < n; i += blockDim.x)
+        covariance(cov + queue[i] * 100, 1, free_mask, cov + queue[i] * 100, false);
+      __syncthreads();
+      if (threadIdx.x == 0) qn = 0;
+    }
+    __syncthreads();
   }
 }
 
@@ -558,10 +592,11 @@ cudaError_t launch_covariance(float* cov, const int32_t* status, int64_t npix,
   int dev = 0, nsm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  int64_t grid = (npix + 127) / 128;
-  if (grid > (int64_t)nsm * 16) grid = (int64_t)nsm * 16;
+  // a few blocks per SM, each sweeping many pixels so its fallback queue fills
+  int64_t grid = (npix + kCovThreads - 1) / kCovThreads;
+  if (grid > (int64_t)nsm * 4) grid = (int64_t)nsm * 4;
   if (grid < 1) grid = 1;
-  covariance_kernel<<<(int)grid, 128, 0, s>>>(cov, status, npix, npix_dev, free_mask);
+  covariance_kernel<<<(int)grid, kCovThreads, 0, s>>>(cov, status, npix, npix_dev, free_mask);
   return cudaGetLastError();
 }
 

@@ -10,7 +10,8 @@ namespace nn {
 
 __global__ void flag_gather_kernel(const int32_t* __restrict__ status,
                                    const float* __restrict__ chi2, int64_t npix,
-                                   float chi2_flag, const float* __restrict__ obs,
+                                   float chi2_flag, bool flag_unconverged,
+                                   const float* __restrict__ obs,
                                    const float* __restrict__ w, int64_t w_stride, int nobs,
                                    unsigned long long* __restrict__ count,
                                    int64_t* __restrict__ index, float* __restrict__ obs_g,
@@ -19,7 +20,8 @@ __global__ void flag_gather_kernel(const int32_t* __restrict__ status,
   if (p >= npix) return;
   const int st = status[p];
   const bool conv = (st == VFISV_PIX_CONVERGED || st == VFISV_PIX_STALLED);
-  const bool f = (st != VFISV_PIX_BAD_INPUT) && (!conv || !(chi2[p] <= chi2_flag));
+  const bool f = (st != VFISV_PIX_BAD_INPUT) &&
+                 ((flag_unconverged && !conv) || !(chi2[p] <= chi2_flag));
   if (flagged) flagged[p] = f ? 1 : 0;
   if (!f) return;
   const int64_t j = (int64_t)atomicAdd(count, 1ull);
@@ -30,13 +32,15 @@ __global__ void flag_gather_kernel(const int32_t* __restrict__ status,
 }
 
 cudaError_t flag_and_gather(const int32_t* status, const float* chi2, int64_t npix,
-                            float chi2_flag, const float* obs, const float* w,
+                            float chi2_flag, bool flag_unconverged, const float* obs,
+                            const float* w,
                             int64_t w_stride, int nobs, int64_t* count, int64_t* index,
                             float* obs_g, float* w_g, int32_t* flagged, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(count, 0, sizeof(int64_t), s);
   if (e != cudaSuccess) return e;
   const unsigned nb = (unsigned)((npix + 255) / 256);
-  flag_gather_kernel<<<nb, 256, 0, s>>>(status, chi2, npix, chi2_flag, obs, w, w_stride, nobs,
+  flag_gather_kernel<<<nb, 256, 0, s>>>(status, chi2, npix, chi2_flag, flag_unconverged, obs, w,
+                                        w_stride, nobs,
                                         (unsigned long long*)count, index, obs_g, w_g, flagged);
   return cudaGetLastError();
 }

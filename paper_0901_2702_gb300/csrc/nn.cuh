@@ -68,7 +68,7 @@ int64_t padded_rows(int64_t n);
 
 // mixed.cu: flag pixels for plain re-inversion, gather them, merge results.
 cudaError_t flag_and_gather(const int32_t* status, const float* chi2, int64_t npix,
-                            float chi2_flag, const float* obs, const float* w,
+                            float chi2_flag, bool flag_unconverged, const float* obs, const float* w,
                             int64_t w_stride, int nobs, int64_t* count, int64_t* index,
                             float* obs_g, float* w_g, int32_t* flagged, cudaStream_t s);
 cudaError_t merge_plain(const int64_t* count, const int64_t* index, int64_t npix_max,
