@@ -53,11 +53,13 @@ MIXED = {"disk": (50, 2.5, False), "map1024": (20, 3.0, True)}
 TRAIN_N, TRAIN_EPOCHS, TRAIN_BATCH = 1 << 22, 8, 8192
 
 # Algorithmic FP32 flops of one fused LM pass (synthesis + 6-column Jacobian
-# + filtering) per wavelength point, from the op count of the formulas
-# (FMA = 2 flops): Faddeeva (Weideman, 16 terms) 3 x 135, absorption matrix
-# 26, Unno-Rachkovsky 31, Stokes filtering 48, Eqs. 8-9 27, Delta partials 13,
-# 20 Stokes partials 90, 6 parameter chains 654.
-FLOP_PER_LAMBDA = 3 * 135 + 26 + 31 + 48 + 27 + 13 + 90 + 654
+# + filtering) per wavelength point, from the op count of the formulas in
+# the kernel (FMA = 2 flops): profile coordinates 4, Faddeeva (Weideman, 16
+# terms) 3 x 135, absorption-matrix elements 16, Unno-Rachkovsky 32, Stokes
+# filtering 48, Eqs. 8-9 28, Delta partials 14, inclination factors 4,
+# filter weights x 1/Delta 6, 20 Stokes partials 63, chain rule and six
+# filtered derivative rows 4 x 132.
+FLOP_PER_LAMBDA = 4 + 3 * 135 + 16 + 32 + 48 + 28 + 14 + 4 + 6 + 63 + 4 * 132
 FLOP_PER_PASS_EXTRA = 60  # model and residual outside the wavelength loop
 
 

@@ -471,6 +471,7 @@ __global__ void __launch_bounds__(kInvThreads, 1) invert_kernel(InvertArgs A) {
       for (int i = 0; i < kNP; ++i) g[i] = Dot2{0.0f, 0.0f};
       constexpr int rowOf[kNP] = {kRowB, kRowG, -1, kRowE, kRowD, kRowA, kRowV, -1, -1};
       const float mu = A.lk.mu;
+      const RowScale R = row_scale(A.lk, ST(sMt, 3), ST(sMt, 4));
       // Runtime loops over (filter, Stokes) keep this block small: it runs
       // on accepted steps only and must not evict the wavelength loop from
       // the instruction cache.  Observable (s, k) of row r is
@@ -490,7 +491,8 @@ __global__ void __launch_bounds__(kInvThreads, 1) invert_kernel(InvertArgs A) {
 #pragma unroll
           for (int p = 0; p < kNP; ++p)
             if (rowOf[p] >= 0)
-              J[p] = mus1 * fmaf(cA, D(rowOf[p], sa, k), cB * D(rowOf[p], sb, k));
+              J[p] = (mus1 * R.s[rowOf[p]]) *
+                     fmaf(cA, D(rowOf[p], sa, k), cB * D(rowOf[p], sb, k));
           J[2] = (s == 1) ? -2.0f * kDeg * Uk : (s == 2 ? 2.0f * kDeg * Qk : 0.0f);
           J[7] = (s == 0) ? tau[k] : 0.0f;
           const float lin = fmaf(cA, D(0, sa, k), cB * D(0, sb, k));

@@ -13,6 +13,17 @@ namespace vfisv {
 // terms the truncation error is below 1.3e-7 for Im z >= 0, about the size
 // of the FP32 rounding error of the evaluation itself.
 constexpr int kWeidN = 16;
+// Unroll factor of the Horner loop (15 = fully unrolled); a smaller factor
+// shrinks the wavelength loop's code at the cost of loop overhead.
+#ifndef VFISV_HORNER_UNROLL
+#define VFISV_HORNER_UNROLL 15
+#endif
+constexpr int kHornerUnroll = VFISV_HORNER_UNROLL;
+// 1: multiply the filter weights by 1/Delta once per wavelength (6 products,
+// 6 live registers); 0: scale the six derivative row values instead.
+#ifndef VFISV_FOLD_ID_IN_WEIGHTS
+#define VFISV_FOLD_ID_IN_WEIGHTS 1
+#endif
 constexpr float kInvSqrtPi = 0.56418958354775628695f;
 constexpr float kTwoInvSqrtPi = 1.1283791670955125739f;
 constexpr float kDeg = 0.017453292519943295769f;
@@ -51,7 +62,7 @@ __device__ __forceinline__ void faddeeva(const Weideman& W, float u, float a,
   const float zr = fmaf(L - a, lp, -u * u) * rd;
   const float zi = (2.0f * L * u) * rd;
   float pr = W.a[kWeidN], pi = 0.0f;
-#pragma unroll
+#pragma unroll kHornerUnroll
   for (int n = kWeidN - 1; n >= 1; --n) {
     const float t = fmaf(pr, zr, fmaf(-pi, zi, W.a[n]));
     pi = fmaf(pr, zi, pi * zr);
@@ -69,15 +80,17 @@ struct PixK {
   float uv;     // Doppler shift / dlambdaD
   float uB;     // Zeeman shift / dlambdaD
   float a;      // damping
-  float eta0;
-  float s2;     // sin^2 gamma
-  float c2p1;   // 1 + cos^2 gamma
-  float cg;     // cos gamma
-  // derivative helpers
-  float kB;     // d u_blue / dB = cB / dlambdaD
-  float kv;     // d u / dv = -cv / dlambdaD
-  float ds2;    // d sin^2 gamma / d gamma[deg]
-  float dcg;    // d cos gamma / d gamma[deg]
+  // absorption-matrix coefficients (psi = 0 frame): with Hsum = H_b + H_r,
+  // eta_I = 1 + c1 H_p + c2 Hsum, eta_L = c1 (H_p - Hsum/2) = c1 H_p - c3 Hsum,
+  // eta_V = c4 (H_r - H_b), and the rho's likewise with F.
+  float c1;     // eta0 sin^2(g) / 2
+  float c2;     // eta0 (1 + cos^2 g) / 4
+  float c3;     // eta0 sin^2(g) / 4
+  float c4;     // eta0 cos(g) / 2
+  // inclination derivatives (per degree): d eta_I/dg = d eta_L/dg =
+  // g1 (H_p - Hsum/2), d eta_V/dg = g2 (H_r - H_b), rho's likewise
+  float g1;     // eta0 sin(2g) / 2 * pi/180
+  float g2;     // -eta0 sin(g) / 2 * pi/180
 };
 
 __device__ __forceinline__ PixK make_pixk(const LineK& lk, float B, float gam_deg,
@@ -87,22 +100,41 @@ __device__ __forceinline__ PixK make_pixk(const LineK& lk, float B, float gam_de
   P.uv = lk.cv * v * P.invD;
   P.uB = lk.cB * B * P.invD;
   P.a = a;
-  P.eta0 = eta0;
   float sg, cg;
   sincosf(gam_deg * kDeg, &sg, &cg);
-  P.s2 = sg * sg;
-  P.c2p1 = fmaf(cg, cg, 1.0f);
-  P.cg = cg;
-  P.kB = lk.cB * P.invD;
-  P.kv = -lk.cv * P.invD;
-  P.ds2 = 2.0f * sg * cg * kDeg;
-  P.dcg = -sg * kDeg;
+  const float s2 = sg * sg;
+  P.c1 = 0.5f * eta0 * s2;
+  P.c2 = 0.25f * eta0 * fmaf(cg, cg, 1.0f);
+  P.c3 = 0.25f * eta0 * s2;
+  P.c4 = 0.5f * eta0 * cg;
+  P.g1 = eta0 * sg * cg * kDeg;
+  P.g2 = -0.5f * eta0 * sg * kDeg;
   return P;
 }
 
+// Per-pixel factors applied to the filtered derivative rows after the
+// wavelength loop (they do not depend on wavelength): row r of the
+// accumulators times rowscale[r] is d(unit-S1 Stokes)/d(parameter).
+struct RowScale {
+  float s[7];
+};
+__device__ __forceinline__ RowScale row_scale(const LineK& lk, float eta0, float dld) {
+  RowScale R;
+  const float invD = __frcp_rn(dld);
+  R.s[0] = 1.0f;               // Stokes
+  R.s[1] = lk.cB * invD;       // B: du_blue/dB = -du_red/dB
+  R.s[2] = 1.0f;               // gamma (per degree)
+  R.s[3] = __frcp_rn(eta0);    // eta0: the elements are linear in eta0
+  R.s[4] = -invD;              // dlambdaD: du_k/d dlambdaD = -u_k / dlambdaD
+  R.s[5] = 1.0f;               // damping
+  R.s[6] = -lk.cv * invD;      // v: du_k/dv = -cv / dlambdaD
+  return R;
+}
+
 // Accumulator layout of the fused pass: row r = 0 holds the unit-S1 Stokes
-// profile K^{-1} e0 (I, Q0, U0, V in the psi = 0 frame); rows 1..6 hold its
-// derivatives with respect to B, gamma, eta0, dlambdaD, a, v_los.
+// profile K^{-1} e0 (I, Q0, U0, V in the psi = 0 frame); rows 1..6 hold
+// (up to the row scales above) its derivatives with respect to B, gamma,
+// eta0, dlambdaD, a, v_los.
 constexpr int kRows = 7;
 constexpr int kRowB = 1, kRowG = 2, kRowE = 3, kRowD = 4, kRowA = 5, kRowV = 6;
 
@@ -118,17 +150,17 @@ __device__ __forceinline__ void lambda_step(const Weideman& W, const PixK& P, fl
   faddeeva(W, up, P.a, Hp, Fp);
   faddeeva(W, ub, P.a, Hb, Fb);
   faddeeva(W, ur, P.a, Hr, Fr);
-  const float Hs = 0.5f * (Hb + Hr), Hd = 0.5f * (Hr - Hb);
-  const float Fs = 0.5f * (Fb + Fr), Fd = 0.5f * (Fr - Fb);
-  // absorption-matrix elements per unit eta0 (psi = 0 frame)
-  const float uI = 0.5f * fmaf(Hp, P.s2, Hs * P.c2p1);
-  const float uL = 0.5f * (Hp - Hs) * P.s2;
-  const float uV = Hd * P.cg;
-  const float urL = 0.5f * (Fp - Fs) * P.s2;
-  const float urV = Fd * P.cg;
-  const float eI = fmaf(P.eta0, uI, 1.0f);
-  const float eL = P.eta0 * uL, eV = P.eta0 * uV;
-  const float rL = P.eta0 * urL, rV = P.eta0 * urV;
+  const float Hsum = Hb + Hr, Hdif = Hr - Hb;
+  const float Fsum = Fb + Fr, Fdif = Fr - Fb;
+  // absorption-matrix elements (psi = 0 frame)
+  // (linear-polarisation elements written as c1 (X_p - Xsum/2): exactly zero
+  // when the three components coincide, B = 0)
+  const float hL = fmaf(-0.5f, Hsum, Hp), fL = fmaf(-0.5f, Fsum, Fp);
+  const float eI = fmaf(P.c1, Hp, fmaf(P.c2, Hsum, 1.0f));
+  const float eL = P.c1 * hL;
+  const float eV = P.c4 * Hdif;
+  const float rL = P.c1 * fL;
+  const float rV = P.c4 * Fdif;
   // closed-form Unno-Rachkovsky solution, unit S1, psi = 0 frame
   const float eI2 = eI * eI;
   const float Pi = fmaf(eL, rL, eV * rV);
@@ -157,81 +189,74 @@ __device__ __forceinline__ void lambda_step(const Weideman& W, const PixK& P, fl
     const float bep = fmaf(a2, Fp, -2.0f * up * Hp);
     const float beb = fmaf(a2, Fb, -2.0f * ub * Hb);
     const float ber = fmaf(a2, Fr, -2.0f * ur * Hr);
-    // partials of Delta and of the numerators w.r.t. (eI, eL, eV, rL, rV)
+    // partials of Delta w.r.t. (eI, eL, eV, rL, rV)
     const float dDe = 2.0f * eI * (eI2 + g);
     const float dDq = -2.0f * NQ, dDv = -2.0f * NV;
     const float dDr = 2.0f * fmaf(eI2, rL, -Pi * eL);
     const float dDt = 2.0f * fmaf(eI2, rV, -Pi * eV);
-    // y_S = s N_S / Delta  =>  dy_S/dX = (s dN_S/dX - y_S dDelta/dX) / Delta
-    const float Ie = iD * (fmaf(3.0f, eI2, rr) - yI * dDe);
-    const float Iq = -iD * yI * dDq, Iv = -iD * yI * dDv;
-    const float Ir = iD * (2.0f * eI * rL - yI * dDr);
-    const float It = iD * (2.0f * eI * rV - yI * dDt);
-    const float Qe = -iD * (2.0f * eI * eL + yQ * dDe);
-    const float Qq = -iD * (fmaf(rL, rL, eI2) + yQ * dDq);
-    const float Qv = -iD * (rL * rV + yQ * dDv);
-    const float Qr = -iD * (fmaf(rL, eL, Pi) + yQ * dDr);
-    const float Qt = -iD * (rL * eV + yQ * dDt);
-    const float Ue = -iD * (fmaf(eL, rV, -eV * rL) + yU * dDe);
-    const float Uq = -iD * (eI * rV + yU * dDq);
-    const float Uv = -iD * (-eI * rL + yU * dDv);
-    const float Ur = -iD * (-eI * eV + yU * dDr);
-    const float Ut = -iD * (eI * eL + yU * dDt);
-    const float Ve = -iD * (2.0f * eI * eV + yV * dDe);
-    const float Vq = -iD * (rV * rL + yV * dDq);
-    const float Vv = -iD * (fmaf(rV, rV, eI2) + yV * dDv);
-    const float Vr = -iD * (rV * eL + yV * dDr);
-    const float Vt = -iD * (fmaf(rV, eV, Pi) + yV * dDt);
+    const float e2 = 2.0f * eI;
+    // inclination derivatives of the elements
+    const float gIL = P.g1 * hL;
+    const float gV = P.g2 * Hdif;
+    const float gRL = P.g1 * fL;
+    const float gRV = P.g2 * Fdif;
+#if VFISV_FOLD_ID_IN_WEIGHTS
+    // Weights of the derivative rows: the 1/Delta of every partial is folded
+    // into the filter weight.
+    float Td[NF];
+#pragma unroll
+    for (int k = 0; k < NF; ++k) Td[k] = T[k] * iD;
+#else
+    const float (&Td)[NF] = T;
+#endif
 
-    auto push = [&](int row, float de, float dq, float dv, float dr, float dt) {
-      const float dI = fmaf(Ie, de, fmaf(Iq, dq, fmaf(Iv, dv, fmaf(Ir, dr, It * dt))));
-      const float dQ = fmaf(Qe, de, fmaf(Qq, dq, fmaf(Qv, dv, fmaf(Qr, dr, Qt * dt))));
-      const float dU = fmaf(Ue, de, fmaf(Uq, dq, fmaf(Uv, dv, fmaf(Ur, dr, Ut * dt))));
-      const float dV = fmaf(Ve, de, fmaf(Vq, dq, fmaf(Vv, dv, fmaf(Vr, dr, Vt * dt))));
+    // For each Stokes parameter: the partials p_X = Delta * dy_S/dX w.r.t.
+    // the five elements, then the chain rule through the profiles.
+    auto stokes = [&](int S, float pe, float pq, float pv, float pr, float pt) {
+      // d/dH_k and d/dF_k of the component profiles
+      const float peq = pe + pq;
+      const float SHp = peq * P.c1;
+      const float tH = fmaf(pe, P.c2, -pq * P.c3);
+      const float SHb = fmaf(-pv, P.c4, tH), SHr = fmaf(pv, P.c4, tH);
+      const float SFp = pr * P.c1;
+      const float tF = -pr * P.c3;
+      const float SFb = fmaf(-pt, P.c4, tF), SFr = fmaf(pt, P.c4, tF);
+      // d/du_k = dS/dH beta - dS/dF alpha
+      const float Gp = fmaf(SHp, bep, -SFp * alp);
+      const float Gb = fmaf(SHb, beb, -SFb * alb);
+      const float Gr = fmaf(SHr, ber, -SFr * alr);
+      float vB = Gb - Gr;                                  // x kB
+      float vG = fmaf(peq, gIL, fmaf(pv, gV, fmaf(pr, gRL, pt * gRV)));
+      float vE = fmaf(pe, eI - 1.0f, fmaf(pq, eL, fmaf(pv, eV, fmaf(pr, rL, pt * rV))));
+      float vD = fmaf(up, Gp, fmaf(ub, Gb, ur * Gr));      // x (-1/dlambdaD)
+      float vA = fmaf(SHp, alp, fmaf(SFp, bep, fmaf(SHb, alb, fmaf(SFb, beb,
+                       fmaf(SHr, alr, SFr * ber)))));
+      float vV = Gp + Gb + Gr;                             // x kv
+#if !VFISV_FOLD_ID_IN_WEIGHTS
+      // the 1/Delta of every partial, applied to the six row values
+      vB *= iD; vG *= iD; vE *= iD; vD *= iD; vA *= iD; vV *= iD;
+#endif
 #pragma unroll
       for (int k = 0; k < NF; ++k) {
-        acc[row][0][k] = fmaf(T[k], dI, acc[row][0][k]);
-        acc[row][1][k] = fmaf(T[k], dQ, acc[row][1][k]);
-        acc[row][2][k] = fmaf(T[k], dU, acc[row][2][k]);
-        acc[row][3][k] = fmaf(T[k], dV, acc[row][3][k]);
+        acc[kRowB][S][k] = fmaf(Td[k], vB, acc[kRowB][S][k]);
+        acc[kRowG][S][k] = fmaf(Td[k], vG, acc[kRowG][S][k]);
+        acc[kRowE][S][k] = fmaf(Td[k], vE, acc[kRowE][S][k]);
+        acc[kRowD][S][k] = fmaf(Td[k], vD, acc[kRowD][S][k]);
+        acc[kRowA][S][k] = fmaf(Td[k], vA, acc[kRowA][S][k]);
+        acc[kRowV][S][k] = fmaf(Td[k], vV, acc[kRowV][S][k]);
       }
     };
-    // element derivatives from profile derivatives (pi, sigma sum, sigma difference)
-    auto shape = [&](int row, float dHp, float dHs, float dHd, float dFp, float dFs, float dFd) {
-      const float e = P.eta0;
-      push(row, e * 0.5f * fmaf(dHp, P.s2, dHs * P.c2p1), e * 0.5f * (dHp - dHs) * P.s2,
-           e * dHd * P.cg, e * 0.5f * (dFp - dFs) * P.s2, e * dFd * P.cg);
-    };
-    // B: only the sigma components move, u_b = u_p + uB, u_r = u_p - uB
-    {
-      const float h = 0.5f * P.kB;
-      shape(kRowB, 0.0f, h * (beb - ber), -h * (beb + ber), 0.0f, h * (alr - alb), h * (alb + alr));
-    }
-    // gamma (per degree)
-    {
-      const float he = 0.5f * P.eta0;
-      const float dIL = he * (Hp - Hs) * P.ds2;
-      push(kRowG, dIL, dIL, P.eta0 * Hd * P.dcg, he * (Fp - Fs) * P.ds2, P.eta0 * Fd * P.dcg);
-    }
-    // eta0: the elements are linear in it
-    push(kRowE, uI, uL, uV, urL, urV);
-    // dlambdaD: d u_k / d dlambdaD = -u_k / dlambdaD
-    {
-      const float ip = up * P.invD, ib = ub * P.invD, ir = ur * P.invD;
-      const float hbp = -bep * ip, hbb = -beb * ib, hbr = -ber * ir;
-      const float fap = alp * ip, fab = alb * ib, far_ = alr * ir;
-      shape(kRowD, hbp, 0.5f * (hbb + hbr), 0.5f * (hbr - hbb), fap, 0.5f * (fab + far_),
-            0.5f * (far_ - fab));
-    }
-    // damping: dH/da = alpha, dF/da = beta
-    shape(kRowA, alp, 0.5f * (alb + alr), 0.5f * (alr - alb), bep, 0.5f * (beb + ber),
-          0.5f * (ber - beb));
-    // v_los: d u_k / dv = kv for all components
-    {
-      const float kv = P.kv;
-      shape(kRowV, kv * bep, kv * 0.5f * (beb + ber), kv * 0.5f * (ber - beb), -kv * alp,
-            -kv * 0.5f * (alb + alr), -kv * 0.5f * (alr - alb));
-    }
+    // y_S = s N_S / Delta => Delta dy_S/dX = s dN_S/dX - y_S dDelta/dX
+    stokes(0, fmaf(-yI, dDe, fmaf(3.0f, eI2, rr)), -yI * dDq, -yI * dDv,
+           fmaf(-yI, dDr, e2 * rL), fmaf(-yI, dDt, e2 * rV));
+    stokes(1, fmaf(-yQ, dDe, -e2 * eL), fmaf(-yQ, dDq, -fmaf(rL, rL, eI2)),
+           fmaf(-yQ, dDv, -rL * rV), fmaf(-yQ, dDr, -fmaf(rL, eL, Pi)),
+           fmaf(-yQ, dDt, -rL * eV));
+    stokes(2, fmaf(-yU, dDe, -fmaf(eL, rV, -eV * rL)), fmaf(-yU, dDq, -eI * rV),
+           fmaf(-yU, dDv, eI * rL), fmaf(-yU, dDr, eI * eV), fmaf(-yU, dDt, -eI * eL));
+    stokes(3, fmaf(-yV, dDe, -e2 * eV), fmaf(-yV, dDq, -rV * rL),
+           fmaf(-yV, dDv, -fmaf(rV, rV, eI2)), fmaf(-yV, dDr, -rV * eL),
+           fmaf(-yV, dDt, -fmaf(rV, eV, Pi)));
   }
 }
 

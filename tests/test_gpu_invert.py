@@ -173,7 +173,7 @@ def test_empty_map(vf):
 
 def test_full_map_sampled(vf):
     """The 1024x1024 map inverted in the launch configuration the benchmark
-    times; 128 sampled pixels carry oracle-synthesised observations and are
+    times; 400 sampled pixels carry oracle-synthesised observations and are
     compared with the oracle's inversion of the same observations."""
     v, h, torch = vf
     npix = 1024 * 1024
@@ -186,7 +186,7 @@ def test_full_map_sampled(vf):
     sig = 1e-3 * (t(p[:, 7]) + t(p[:, 8]))[:, None]
     obs = syn + sig * nz
     w = (1.0 / (sig * sig)).expand(npix, 24).contiguous()
-    idx = np.sort(np.random.default_rng(1).choice(npix, 128, replace=False))
+    idx = np.sort(np.random.default_rng(1).choice(npix, 400, replace=False))
     s_or = me.synth(p[idx], f32(T), f32(X), LINE).reshape(len(idx), 24)
     o_obs, o_w = W.observe(s_or, p[idx], W.noise(npix, 24, seed)[idx])
     o_obs, o_w = f32(o_obs), f32(o_w)
