@@ -70,7 +70,8 @@ enum {
   VFISV_E_UNSUPPORTED = -3, /* nfilt not compiled into this kernel */
   VFISV_E_CUDA = -4,        /* a CUDA runtime call failed */
   VFISV_E_DEVICE = -5,      /* a kernel reported an internal error */
-  VFISV_E_NOMEM = -6        /* a workspace allocation failed */
+  VFISV_E_NOMEM = -6,       /* a workspace allocation failed */
+  VFISV_E_CAPTURE = -7      /* a workspace would have to grow during capture */
 };
 
 /* Per-pixel status codes written to status_out. */
@@ -119,6 +120,30 @@ int vfisv_create(vfisv_handle** out, int device);
 void vfisv_destroy(vfisv_handle* h);
 void vfisv_config_default(vfisv_config* cfg);
 const char* vfisv_strerror(int code);
+
+/* Whole-map CUDA graphs.  vfisv_graph_begin starts a (relaxed-mode) capture
+ * on `stream` (not the legacy NULL stream); every vfisv_* call made with the
+ * handle and device buffers until vfisv_graph_end is recorded instead of
+ * run, and vfisv_graph_end instantiates the graph.  Workspaces cannot grow
+ * while capturing (VFISV_E_CAPTURE): make one uncaptured call with the same
+ * sizes first.  vfisv_graph_launch replays it (same buffers, new contents);
+ * calls that synchronise (vfisv_check, host buffers, vfisv_autotune) are not
+ * capturable. */
+typedef struct vfisv_graph vfisv_graph;
+int vfisv_graph_begin(vfisv_handle* h, void* stream);
+int vfisv_graph_end(vfisv_handle* h, void* stream, vfisv_graph** out);
+int vfisv_graph_launch(vfisv_graph* g, void* stream);
+void vfisv_graph_destroy(vfisv_graph* g);
+
+/* Autotuner: time the LM kernel with 64, 128 and 256 pixel slots per CTA on
+ * the given sample (arguments as vfisv_invert, no covariance), keep the
+ * fastest for this handle's later inversions and return it in best_block
+ * (and the times in ms_out[3] if not NULL).  Synchronises `stream`. */
+int vfisv_autotune(vfisv_handle* h, const float* obs, const float* weights,
+                   int32_t weights_per_pixel, const float* filters, int32_t nfilt,
+                   const float* wl_mA, int32_t nlam, const vfisv_line* line,
+                   const vfisv_config* cfg, int64_t npix, int32_t* best_block, float* ms_out,
+                   void* stream);
 
 /* Synchronise `stream` and report any error a kernel of this handle flagged
  * on the device since the last check (VFISV_E_DEVICE) or a CUDA error. */

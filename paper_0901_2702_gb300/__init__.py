@@ -18,7 +18,9 @@ import numpy as np
 __all__ = [
     "vfisv_create", "vfisv_destroy", "vfisv_synth", "vfisv_invert", "vfisv_check",
     "vfisv_strerror", "vfisv_config_default", "vfisv_nn_init", "vfisv_nn_train",
-    "vfisv_nn_grad", "vfisv_nn_infer", "vfisv_invert_nn", "VfisvError", "library_path", "load",
+    "vfisv_nn_grad", "vfisv_nn_infer", "vfisv_invert_nn", "vfisv_graph_begin", "vfisv_graph_end",
+    "vfisv_graph_launch", "vfisv_graph_destroy", "vfisv_autotune", "VfisvError", "library_path",
+    "load",
     "NN_NBLOB", "NN_NTRAIN",
 ]
 
@@ -91,6 +93,18 @@ def load():
                                     ctypes.POINTER(vfisv_config), ctypes.POINTER(vfisv_config),
                                     ctypes.c_double, I32, I64, P, P, P, P, P, P, P]
     lib.vfisv_invert_nn.restype = ctypes.c_int
+    lib.vfisv_graph_begin.argtypes = [P, P]
+    lib.vfisv_graph_begin.restype = ctypes.c_int
+    lib.vfisv_graph_end.argtypes = [P, P, ctypes.POINTER(ctypes.c_void_p)]
+    lib.vfisv_graph_end.restype = ctypes.c_int
+    lib.vfisv_graph_launch.argtypes = [P, P]
+    lib.vfisv_graph_launch.restype = ctypes.c_int
+    lib.vfisv_graph_destroy.argtypes = [P]
+    lib.vfisv_graph_destroy.restype = None
+    lib.vfisv_autotune.argtypes = [P, P, P, I32, P, I32, P, I32, ctypes.POINTER(vfisv_line),
+                                   ctypes.POINTER(vfisv_config), I64, ctypes.POINTER(I32),
+                                   P, P]
+    lib.vfisv_autotune.restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -355,3 +369,62 @@ def vfisv_invert_nn(h: Handle, blob, obs, weights, filters, wl_mA, line, config_
         if dst is not None and not _is_torch(dst) and k is not dst:
             dst[...] = k
     return out
+
+
+class Graph:
+    """An instantiated CUDA graph of captured vfisv_* calls."""
+
+    def __init__(self, ptr):
+        self.ptr = ptr
+
+    def launch(self, stream):
+        vfisv_graph_launch(self, stream)
+
+    def close(self):
+        if getattr(self, "ptr", None):
+            load().vfisv_graph_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def vfisv_graph_begin(h: Handle, stream) -> None:
+    _check(load().vfisv_graph_begin(h.ptr, ctypes.c_void_p(_stream(None, stream))),
+           "vfisv_graph_begin")
+
+
+def vfisv_graph_end(h: Handle, stream) -> Graph:
+    g = ctypes.c_void_p()
+    _check(load().vfisv_graph_end(h.ptr, ctypes.c_void_p(_stream(None, stream)), ctypes.byref(g)),
+           "vfisv_graph_end")
+    return Graph(g)
+
+
+def vfisv_graph_launch(g: Graph, stream) -> None:
+    _check(load().vfisv_graph_launch(g.ptr, ctypes.c_void_p(_stream(None, stream))),
+           "vfisv_graph_launch")
+
+
+def vfisv_graph_destroy(g: Graph) -> None:
+    g.close()
+
+
+def vfisv_autotune(h: Handle, obs, weights, filters, wl_mA, line, config=None, stream=None):
+    """Pick the LM kernel's pixel slots per CTA on a sample; returns (best, [ms x 3])."""
+    npix = int(obs.shape[0])
+    nfilt, nlam = int(filters.shape[0]), int(filters.shape[1])
+    per_pixel = 1 if (len(weights.shape) >= 2 and int(weights.shape[0]) == npix) else 0
+    cfg = config if isinstance(config, vfisv_config) else vfisv_config_default(**(config or {}))
+    ptrs = [_ptr(x, np.float32) for x in (obs, weights, filters, wl_mA)]
+    best = ctypes.c_int32()
+    ms = np.zeros(3, np.float32)
+    ln = _line(line)
+    _check(load().vfisv_autotune(h.ptr, ptrs[0][0], ptrs[1][0], per_pixel, ptrs[2][0], nfilt,
+                                 ptrs[3][0], nlam, ctypes.byref(ln), ctypes.byref(cfg), npix,
+                                 ctypes.byref(best), ms.ctypes.data,
+                                 ctypes.c_void_p(_stream(obs, stream))), "vfisv_autotune")
+    return int(best.value), ms.tolist()

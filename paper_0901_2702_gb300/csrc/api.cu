@@ -23,6 +23,13 @@ struct vfisv_handle {
   size_t nnws_bytes = 0;
   void* mixws = nullptr;   // mixed inversion: guesses, gathered pixels, 2nd run
   size_t mixws_bytes = 0;
+  int lm_block = 128;      // LM pixel slots per CTA (vfisv_autotune)
+  bool capturing = false;  // between vfisv_graph_begin and vfisv_graph_end
+};
+
+struct vfisv_graph {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
 };
 
 namespace {
@@ -71,8 +78,13 @@ bool is_device_ptr(const void* p) {
   return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
+// Set while a handle is capturing a graph: workspaces must not grow then
+// (a cudaMalloc / cudaFree would not be recorded and would synchronise).
+thread_local bool t_capturing = false;
+
 int grow(void** buf, size_t* have, size_t need) {
   if (*have >= need) return VFISV_OK;
+  if (t_capturing) return VFISV_E_CAPTURE;
   if (*buf) {
     cudaDeviceSynchronize();
     cudaFree(*buf);
@@ -172,6 +184,7 @@ WsLayout layout(int nf, int nlam, int64_t nslots) {
 }
 
 int set_device(vfisv_handle* h) {
+  t_capturing = h->capturing;
   return cudaSetDevice(h->device) == cudaSuccess ? VFISV_OK : VFISV_E_CUDA;
 }
 
@@ -212,7 +225,7 @@ int invert_device(vfisv_handle* h, const DevInvert& d, int nfilt, int nlam,
                   const vfisv_line* line, const vfisv_config* cfg, int64_t npix,
                   const int64_t* npix_dev, cudaStream_t s) {
   int64_t nslots = 0;
-  int grid = 0, block = 0;
+  int grid = 0, block = h->lm_block;
   size_t smem = 0;
   if (invert_slots(nfilt, nlam, npix, &nslots, &grid, &block, &smem) != cudaSuccess) {
     cudaGetLastError();
@@ -276,6 +289,9 @@ const char* vfisv_strerror(int code) {
     case VFISV_E_CUDA: return "CUDA runtime error";
     case VFISV_E_DEVICE: return "a kernel reported an internal error";
     case VFISV_E_NOMEM: return "device workspace allocation failed";
+    case VFISV_E_CAPTURE:
+      return "a workspace would have to grow during graph capture: make one uncaptured call "
+             "with the same sizes first";
     default: return "unknown error";
   }
 }
@@ -319,6 +335,108 @@ void vfisv_destroy(vfisv_handle* h) {
   if (h->nnws) cudaFree(h->nnws);
   if (h->mixws) cudaFree(h->mixws);
   delete h;
+}
+
+int vfisv_graph_begin(vfisv_handle* h, void* stream) {
+  if (!h || !stream || h->capturing) return VFISV_E_ARG;
+  if (set_device(h)) return VFISV_E_CUDA;
+  if (cudaStreamBeginCapture((cudaStream_t)stream, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+    cudaGetLastError();
+    return VFISV_E_CUDA;
+  }
+  h->capturing = true;
+  t_capturing = true;
+  return VFISV_OK;
+}
+
+int vfisv_graph_end(vfisv_handle* h, void* stream, vfisv_graph** out) {
+  if (!h || !stream || !out || !h->capturing) return VFISV_E_ARG;
+  *out = nullptr;
+  h->capturing = false;
+  t_capturing = false;
+  if (set_device(h)) return VFISV_E_CUDA;
+  cudaGraph_t g = nullptr;
+  if (cudaStreamEndCapture((cudaStream_t)stream, &g) != cudaSuccess || !g) {
+    cudaGetLastError();
+    return VFISV_E_CUDA;
+  }
+  cudaGraphExec_t ex = nullptr;
+  if (cudaGraphInstantiate(&ex, g, 0) != cudaSuccess) {
+    cudaGetLastError();
+    cudaGraphDestroy(g);
+    return VFISV_E_CUDA;
+  }
+  vfisv_graph* r = new vfisv_graph();
+  r->graph = g;
+  r->exec = ex;
+  *out = r;
+  return VFISV_OK;
+}
+
+int vfisv_graph_launch(vfisv_graph* g, void* stream) {
+  if (!g || !g->exec) return VFISV_E_ARG;
+  return cudaGraphLaunch(g->exec, (cudaStream_t)stream) == cudaSuccess ? VFISV_OK : VFISV_E_CUDA;
+}
+
+void vfisv_graph_destroy(vfisv_graph* g) {
+  if (!g) return;
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  if (g->graph) cudaGraphDestroy(g->graph);
+  delete g;
+}
+
+int vfisv_autotune(vfisv_handle* h, const float* obs, const float* weights,
+                   int32_t weights_per_pixel, const float* filters, int32_t nfilt,
+                   const float* wl_mA, int32_t nlam, const vfisv_line* line,
+                   const vfisv_config* cfg, int64_t npix, int32_t* best_block, float* ms_out,
+                   void* stream) {
+  if (!h || !best_block || h->capturing) return VFISV_E_ARG;
+  if (npix < 1) return VFISV_E_SIZE;
+  if (set_device(h)) return VFISV_E_CUDA;
+  cudaStream_t s = (cudaStream_t)stream;
+  // outputs of the trial runs live in the mixed-inversion workspace
+  size_t off = 0;
+  auto place = [&](size_t bytes) {
+    const size_t at = off;
+    off += up(bytes);
+    return at;
+  };
+  const size_t o_p = place((size_t)npix * 40), o_c = place((size_t)npix * 4),
+               o_i = place((size_t)npix * 4), o_s = place((size_t)npix * 4);
+  int rc = grow(&h->mixws, &h->mixws_bytes, off);
+  if (rc) return rc;
+  char* mw = (char*)h->mixws;
+  const int cand[3] = {64, 128, 256};
+  float best = 0.0f;
+  int best_b = 128;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  for (int c = 0; c < 3; ++c) {
+    h->lm_block = cand[c];
+    float ms = 0.0f;
+    for (int rep = 0; rep < 2; ++rep) {  // the first run warms up
+      cudaEventRecord(e0, s);
+      rc = vfisv_invert(h, obs, weights, weights_per_pixel, filters, nfilt, wl_mA, nlam, line,
+                        nullptr, cfg, npix, (float*)(mw + o_p), (float*)(mw + o_c),
+                        (int32_t*)(mw + o_i), (int32_t*)(mw + o_s), nullptr, stream);
+      cudaEventRecord(e1, s);
+      if (rc) break;
+      cudaEventSynchronize(e1);
+      cudaEventElapsedTime(&ms, e0, e1);
+    }
+    if (rc) break;
+    if (ms_out) ms_out[c] = ms;
+    if (c == 0 || ms < best) {
+      best = ms;
+      best_b = cand[c];
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  h->lm_block = best_b;
+  *best_block = best_b;
+  return rc;
 }
 
 int vfisv_check(vfisv_handle* h, void* stream) {

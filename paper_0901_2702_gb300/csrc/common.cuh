@@ -141,8 +141,9 @@ constexpr int kScratchPerSlot = 45 + 9;  // packed J^T W J and J^T W r
 cudaError_t launch_pack_table(const float* filters, int nf, const float* wl, int nlam,
                               float* table, cudaStream_t s);
 cudaError_t launch_synth(const SynthArgs& a, int nf, cudaStream_t s);
-// Persistent LM kernel: returns the number of resident slots it will use
-// for `npix` pixels (the scratch it needs) without launching when dry_run.
+// Persistent LM kernel: launch shape for `npix` pixels with *block pixel
+// slots per CTA (64, 128 or 256; anything else selects 128 and is written
+// back), and the number of resident slots (the scratch it needs).
 cudaError_t invert_slots(int nf, int nlam, int64_t npix, int64_t* nslots, int* grid,
                          int* block, size_t* smem);
 // Upload the Weideman coefficients to the LM kernel's constant bank on the

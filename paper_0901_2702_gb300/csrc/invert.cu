@@ -14,7 +14,7 @@
 
 namespace vfisv {
 
-constexpr int kInvThreads = 128;
+constexpr int kInvThreadsDefault = 128;  // pixel slots per CTA unless autotuned
 constexpr int kNP = 9;    // parameters taking part in the solve (alpha held)
 constexpr int kNPk = 45;  // packed lower triangle of a 9x9 matrix
 
@@ -306,8 +306,8 @@ __host__ __device__ constexpr size_t invert_smem_bytes(int tabf, int nacc, int n
   return (size_t)tabf * 4 + (size_t)nacc * nt * 4 + (size_t)kStateWords * nt * 4 + 16;
 }
 
-template <int NF>
-__global__ void __launch_bounds__(kInvThreads, 1) invert_kernel(InvertArgs A) {
+template <int NF, int BS>
+__global__ void __launch_bounds__(BS, 1) invert_kernel(InvertArgs A) {
   constexpr int NOBS = 4 * NF;
   constexpr int NACC = kRows * 4 * NF;
   extern __shared__ __align__(16) float smem[];
@@ -602,29 +602,38 @@ cudaError_t launch_covariance(float* cov, const int32_t* status, int64_t npix,
   return cudaGetLastError();
 }
 
-cudaError_t invert_slots(int nf, int nlam, int64_t npix, int64_t* nslots, int* grid,
-                         int* block, size_t* smem) {
-  if (nf != 6) return cudaErrorInvalidValue;
-  auto kern = invert_kernel<6>;
-  const int bs = kInvThreads;
-  const size_t sm = invert_smem_bytes(table_floats(6, nlam), kRows * 4 * 6, bs);
+template <int BS>
+static cudaError_t slots_for(int nlam, int64_t npix, int64_t* nslots, int* grid, size_t* smem) {
+  auto kern = invert_kernel<6, BS>;
+  const size_t sm = invert_smem_bytes(table_floats(6, nlam), kRows * 4 * 6, BS);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   int dev = 0, nsm = 0, per = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, bs, sm);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, BS, sm);
   if (e != cudaSuccess) return e;
   if (per < 1) return cudaErrorLaunchOutOfResources;
   int64_t g = (int64_t)nsm * per;
-  const int64_t need = (npix + bs - 1) / bs;
+  const int64_t need = (npix + BS - 1) / BS;
   if (need < g) g = need;
   if (g < 1) g = 1;
   *grid = (int)g;
-  *block = bs;
   *smem = sm;
-  *nslots = g * bs;
+  *nslots = g * BS;
   return cudaSuccess;
+}
+
+cudaError_t invert_slots(int nf, int nlam, int64_t npix, int64_t* nslots, int* grid,
+                         int* block, size_t* smem) {
+  if (nf != 6) return cudaErrorInvalidValue;
+  const int bs = (*block == 64 || *block == 256) ? *block : kInvThreadsDefault;
+  *block = bs;
+  switch (bs) {
+    case 64: return slots_for<64>(nlam, npix, nslots, grid, smem);
+    case 256: return slots_for<256>(nlam, npix, nslots, grid, smem);
+    default: return slots_for<128>(nlam, npix, nslots, grid, smem);
+  }
 }
 
 cudaError_t invert_set_constants(const Weideman& W) {
@@ -634,7 +643,12 @@ cudaError_t invert_set_constants(const Weideman& W) {
 cudaError_t launch_invert(const InvertArgs& a, int nf, int grid, int block, size_t smem,
                           cudaStream_t s) {
   if (nf != 6) return cudaErrorInvalidValue;
-  invert_kernel<6><<<grid, block, smem, s>>>(a);
+  switch (block) {
+    case 64: invert_kernel<6, 64><<<grid, 64, smem, s>>>(a); break;
+    case 256: invert_kernel<6, 256><<<grid, 256, smem, s>>>(a); break;
+    case 128: invert_kernel<6, 128><<<grid, 128, smem, s>>>(a); break;
+    default: return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 

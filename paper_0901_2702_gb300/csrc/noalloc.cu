@@ -104,7 +104,7 @@ extern "C" int vfisv_invert_noalloc(const float* obs, const float* weights,
   cudaStream_t s = (cudaStream_t)stream;
 
   int64_t nslots = 0;
-  int grid = 0, block = 0;
+  int grid = 0, block = 128;
   size_t smem = 0;
   if (invert_slots(nfilt, nlam, npix, &nslots, &grid, &block, &smem) != cudaSuccess) {
     cudaGetLastError();

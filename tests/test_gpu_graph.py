@@ -1,0 +1,80 @@
+"""Whole-map CUDA graphs and the launch-shape autotuner."""
+import numpy as np
+import pytest
+
+import workloads as W
+from gpu_common import LINE, T, X, vf  # noqa: F401
+
+pytestmark = pytest.mark.gpu
+
+
+def _map(v, h, torch, n, seed, dev):
+    t = lambda a: torch.tensor(np.asarray(a, np.float32), device=dev)  # noqa: E731
+    p = W.quiet_and_active_params(n, seed)
+    tf, tx = t(T), t(X)
+    syn = v.vfisv_synth(h, t(p), tf, tx, LINE).reshape(n, 24)
+    sig = 1e-3 * t(W.continuum(p))[:, None]
+    obs = (syn + sig * t(W.noise(n, 24, seed))).contiguous()
+    w = (1.0 / (sig * sig)).expand(n, 24).contiguous()
+    torch.cuda.synchronize()
+    return obs, w, tf, tx
+
+
+def test_graph_replay_matches_direct_calls(vf):
+    v, h, torch = vf
+    dev = torch.device("cuda:0")
+    n = 20000
+    obs, w, tf, tx = _map(v, h, torch, n, 61, dev)
+    obs2, _, _, _ = _map(v, h, torch, n, 62, dev)
+    s = torch.cuda.Stream(dev)
+    out = {"params": torch.empty(n, 10, device=dev), "chi2": torch.empty(n, device=dev),
+           "iters": torch.empty(n, dtype=torch.int32, device=dev),
+           "status": torch.empty(n, dtype=torch.int32, device=dev),
+           "cov": torch.empty(n, 10, 10, device=dev)}
+    src = obs.clone()
+    with torch.cuda.stream(s):
+        v.vfisv_invert(h, src, w, tf, tx, LINE, out=out, stream=s)   # sizes the workspaces
+        s.synchronize()
+        v.vfisv_graph_begin(h, s)
+        v.vfisv_invert(h, src, w, tf, tx, LINE, out=out, stream=s)
+        g = v.vfisv_graph_end(h, s)
+        for data in (obs, obs2):
+            src.copy_(data)
+            g.launch(s)
+            s.synchronize()
+            ref = v.vfisv_invert(h, data, w, tf, tx, LINE, stream=s)
+            s.synchronize()
+            for k in ref:
+                assert torch.equal(out[k], ref[k]), k
+    g.close()
+
+
+def test_capture_refuses_to_grow_workspaces(vf):
+    v, h, torch = vf
+    dev = torch.device("cuda:0")
+    h2 = v.vfisv_create(0)
+    obs, w, tf, tx = _map(v, h2, torch, 512, 63, dev)
+    s = torch.cuda.Stream(dev)
+    with torch.cuda.stream(s):
+        v.vfisv_graph_begin(h2, s)
+        with pytest.raises(v.VfisvError) as e:
+            v.vfisv_invert(h2, obs, w, tf, tx, LINE, stream=s)   # fresh handle: must grow
+        assert e.value.code == -7
+        try:
+            v.vfisv_graph_end(h2, s)
+        except v.VfisvError:
+            pass
+    h2.close()
+
+
+def test_autotune_picks_a_shape_and_keeps_results(vf):
+    v, h, torch = vf
+    dev = torch.device("cuda:0")
+    obs, w, tf, tx = _map(v, h, torch, 30000, 64, dev)
+    base = v.vfisv_invert(h, obs, w, tf, tx, LINE)
+    best, ms = v.vfisv_autotune(h, obs, w, tf, tx, LINE)
+    assert best in (64, 128, 256) and all(m > 0 for m in ms)
+    tuned = v.vfisv_invert(h, obs, w, tf, tx, LINE)
+    v.vfisv_check(h)
+    for k in base:
+        assert torch.equal(base[k], tuned[k]), k
