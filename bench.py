@@ -113,6 +113,19 @@ class ClockSampler:
                 "power_w_max": max(pw) if pw else None, "samples": len(rows)}
 
 
+def reduce_over_ranks(times_ms, counts, device):
+    """Whole-job numbers from every rank's: the slowest rank's times (each
+    rank inverts its own map, so the job ends with the last one) and the
+    summed converged-pixel counts."""
+    import torch
+    import torch.distributed as tdist
+    t = torch.tensor([float(x) for x in times_ms], device=device, dtype=torch.float64)
+    tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    c = torch.tensor([int(x) for x in counts], device=device, dtype=torch.int64)
+    tdist.all_reduce(c, op=tdist.ReduceOp.SUM)
+    return [float(x) for x in t.tolist()], [int(x) for x in c.tolist()]
+
+
 def map_params(workload: str, rank: int):
     if workload == "disk":
         p, _ = W.full_disk_params(W.SEEDS["disk"] + 1000 * rank)
@@ -235,13 +248,8 @@ def run_ours(args, rank, world):
     conv = lambda o: int(((o["status"] == 0) | (o["status"] == 2)).sum().item())  # noqa: E731
     conv_m, conv_p = conv(out_m), conv(out_p)
     if dist:
-        import torch.distributed as tdist
-        t = torch.tensor([ms_mixed, ms_plain], device=dev)
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-        ms_mixed, ms_plain = (float(a) for a in t.tolist())
-        c = torch.tensor([conv_m, conv_p], device=dev, dtype=torch.int64)
-        tdist.all_reduce(c)
-        conv_m_tot, conv_p_tot = (int(a) for a in c.tolist())
+        (ms_mixed, ms_plain), (conv_m_tot, conv_p_tot) = reduce_over_ranks(
+            (ms_mixed, ms_plain), (conv_m, conv_p), dev)
     else:
         conv_m_tot, conv_p_tot = conv_m, conv_p
     value = conv_m_tot / (ms_mixed / 1e3)

@@ -233,3 +233,33 @@ def invert(obs, w, filters, x, line, init=None, max_iter=50, conv_rtol=1e-4,
     if trace:
         out["trace"] = hist
     return out
+
+
+def invert_mixed(obs, w, filters, x, line, blob, nn_cap=20, plain_cap=50, chi2_flag=3.0,
+                 flag_unconverged=True, **kw):
+    """Network-initialised inversion with plain re-inversion of flagged pixels.
+
+    The network (FP64 forward of ``blob``) gives the initial models; LM runs
+    with ``nn_cap``; pixels ending with chi2 > chi2_flag (or, with
+    flag_unconverged, not converged) are inverted again from the standard
+    guess with ``plain_cap`` and keep the lower chi2; iteration counts add."""
+    from . import mlp
+    mu = float(line.get("mu", 1.0))
+    weights, stats = mlp.unpack(blob)
+    y, _ = mlp.forward(weights, mlp.features(obs, stats))
+    init = mlp.decode(y, obs, stats, mu)
+    r = invert(obs, w, filters, x, line, init=init, max_iter=nn_cap, **kw)
+    conv = np.isin(r["status"], (CONVERGED, STALLED))
+    flag = (r["status"] != BAD_INPUT) & ((flag_unconverged & ~conv) | ~(r["chi2"] <= chi2_flag))
+    out = {k: np.array(v, copy=True) for k, v in r.items()}
+    out["flagged"] = flag.astype(np.int32)
+    if flag.any():
+        q = invert(obs[flag], w[flag], filters, x, line, init=None, max_iter=plain_cap, **kw)
+        ids = np.flatnonzero(flag)
+        out["iters"][ids] += q["iters"]
+        plain_ok = (q["status"] != NAN_STATE) & np.isfinite(q["chi2"])
+        nn_ok = (r["status"][ids] != NAN_STATE) & np.isfinite(r["chi2"][ids])
+        take = plain_ok & (~nn_ok | (q["chi2"] < r["chi2"][ids]))
+        for k in ("params", "chi2", "status", "cov"):
+            out[k][ids[take]] = q[k][take]
+    return out

@@ -205,3 +205,31 @@ def loss_and_grad(blob, obs, params):
     grads = backward(weights, cache, dy)
     g = pack([(gw, gb) for gw, gb in grads], {k: np.zeros_like(v) for k, v in stats.items()})
     return L, g[:blob_layout()["in_mean"][0]], y
+
+
+def train(obs, params, steps, batch, lr0=1e-3, seed=0):
+    """FP64 Adam with cosine decay on (obs, params) pairs; returns a blob.
+
+    He-uniform weights from a numpy generator, zero biases, statistics of the
+    training set; minibatches drawn without replacement per epoch."""
+    rng = np.random.default_rng(seed)
+    weights = [(rng.uniform(-1, 1, (a, b)) * np.sqrt(6.0 / a), np.zeros(b))
+               for a, b in zip(LAYERS[:-1], LAYERS[1:])]
+    stats = statistics(obs, params)
+    blob = pack(weights, stats)
+    ntrain = blob_layout()["in_mean"][0]
+    m = np.zeros(ntrain)
+    v = np.zeros(ntrain)
+    n = len(obs)
+    order = rng.permutation(n)
+    pos = 0
+    for t in range(steps):
+        if pos + batch > n:
+            order = rng.permutation(n)
+            pos = 0
+        idx = order[pos:pos + batch]
+        pos += batch
+        _, g, _ = loss_and_grad(blob, obs[idx], params[idx])
+        lr = cosine_lr(lr0, t, steps)
+        blob[:ntrain], m, v = adam_step(blob[:ntrain], g, m, v, t + 1, lr)
+    return blob

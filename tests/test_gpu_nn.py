@@ -135,29 +135,52 @@ def test_network_gain_over_plain_lm(vf):
     assert better >= 0.9
 
 
+_ORACLE_BLOB = {}
+
+
+def _oracle_blob():
+    """A network trained by the oracle (FP64 Adam) on oracle-synthesised
+    profiles, so that no oracle input comes from the CUDA path."""
+    if "blob" not in _ORACLE_BLOB:
+        tp, tobs, tw = _oracle_set(16384, 46)
+        _ORACLE_BLOB["blob"] = f32(mlp.train(tobs, tp, steps=150, batch=1024, lr0=2e-3, seed=3))
+    return _ORACLE_BLOB["blob"]
+
+
 def test_mixed_first_stage_vs_oracle(vf):
-    """LM from the network's guess vs the oracle's LM from its own FP64
-    evaluation of the same network."""
+    """The network's guess on the GPU (BF16) vs the oracle's FP64 evaluation of
+    the same network, and LM from that guess on both sides."""
     v, h, torch = vf
-    p, obs, w = _oracle_set(2048, 44)
-    tp, gobs, tf, tx = _gpu_training_set(v, h, torch, 131072, 45)
-    blob = v.vfisv_nn_init(h, gobs, tp, seed=1)
-    v.vfisv_nn_train(h, blob, gobs, tp, batch=4096, epochs=4, lr0=1e-3, seed=2)
-    blob = blob.cpu().numpy()
-    n = 600
-    o, ww = obs[:n], w[:n]
+    p, obs, w = _oracle_set(600, 44)
+    blob = _oracle_blob()
     weights, st = mlp.unpack(blob)
-    y, _ = mlp.forward(weights, mlp.features(o, st))
-    init_ref = mlp.decode(y, o, st)
-    r = v.vfisv_nn_infer(h, blob, o.astype(np.float32), LINE)
-    # the GPU's BF16 guess and the oracle's FP64 guess agree closely ...
+    y, _ = mlp.forward(weights, mlp.features(obs, st))
+    init_ref = mlp.decode(y, obs, st)
+    r = v.vfisv_nn_infer(h, blob.astype(np.float32), obs.astype(np.float32), LINE)
     assert np.median(np.abs(r["init"][:, 0] - init_ref[:, 0])) < 30.0
-    # ... and LM from the oracle's guess on both sides converges to the same chi2
     init = f32(init_ref)
-    g = v.vfisv_invert(h, o.astype(np.float32), ww.astype(np.float32), T.astype(np.float32),
+    g = v.vfisv_invert(h, obs.astype(np.float32), w.astype(np.float32), T.astype(np.float32),
                        X.astype(np.float32), LINE, init=init.astype(np.float32),
                        config={"max_iter": 20})
-    ref = lm.invert(o, ww, f32(T), f32(X), LINE, init=init, max_iter=20)
+    ref = lm.invert(obs, w, f32(T), f32(X), LINE, init=init, max_iter=20)
     both = np.isin(g["status"], (0, 2)) & np.isin(ref["status"], (0, 2))
     rel = np.abs(g["chi2"][both] / ref["chi2"][both] - 1)
-    assert both.mean() > 0.5 and np.mean(rel <= 1e-3) >= 0.98
+    assert both.mean() > 0.3 and np.mean(rel <= 1e-3) >= 0.98
+
+
+def test_mixed_pipeline_vs_oracle(vf):
+    """vfisv_invert_nn vs the oracle's mixed inversion with the same network
+    (trained by the oracle itself, in FP64): flags, and chi2 of pixels
+    converged in both."""
+    v, h, torch = vf
+    blob = _oracle_blob()
+    p, obs, w = _oracle_set(600, 47)
+    ref = lm.invert_mixed(obs, w, f32(T), f32(X), LINE, blob, nn_cap=20, plain_cap=50,
+                          chi2_flag=3.0, flag_unconverged=True)
+    g = v.vfisv_invert_nn(h, blob.astype(np.float32), obs.astype(np.float32),
+                          w.astype(np.float32), T.astype(np.float32), X.astype(np.float32),
+                          LINE, chi2_flag=3.0, flag_unconverged=True)
+    assert np.mean(g["flagged"] == ref["flagged"]) >= 0.85
+    both = np.isin(g["status"], (0, 2)) & np.isin(ref["status"], (0, 2))
+    rel = np.abs(g["chi2"][both] / ref["chi2"][both] - 1)
+    assert both.mean() > 0.5 and np.mean(rel <= 1e-3) >= 0.95
