@@ -121,6 +121,17 @@ void vfisv_destroy(vfisv_handle* h);
 void vfisv_config_default(vfisv_config* cfg);
 const char* vfisv_strerror(int code);
 
+/* Voigt and Faraday-Voigt functions H(a,u) + i F(a,u) = w(u + i a) of n
+ * points (Sec. 3.2), a >= 0:
+ *   method 0  the Weideman rational series the synthesis kernels use;
+ *   method 1  the paper's Taylor table, first order (Eqs. 8-9, 12-13):
+ *             H, F tabulated at u = 0..20 step 0.04 and a = 0..5 step 0.05,
+ *             extrapolated from the nearest node;
+ *   method 2  the same to second order (Eqs. 10-13).
+ * Points outside the table use the rational series.  Arrays float32[n]. */
+int vfisv_voigt(vfisv_handle* h, const float* a, const float* u, int64_t n, int32_t method,
+                float* H, float* F, void* stream);
+
 /* Whole-map CUDA graphs.  vfisv_graph_begin starts a (relaxed-mode) capture
  * on `stream` (not the legacy NULL stream); every vfisv_* call made with the
  * handle and device buffers until vfisv_graph_end is recorded instead of

@@ -19,7 +19,8 @@ __all__ = [
     "vfisv_create", "vfisv_destroy", "vfisv_synth", "vfisv_invert", "vfisv_check",
     "vfisv_strerror", "vfisv_config_default", "vfisv_nn_init", "vfisv_nn_train",
     "vfisv_nn_grad", "vfisv_nn_infer", "vfisv_invert_nn", "vfisv_graph_begin", "vfisv_graph_end",
-    "vfisv_graph_launch", "vfisv_graph_destroy", "vfisv_autotune", "VfisvError", "library_path",
+    "vfisv_graph_launch", "vfisv_graph_destroy", "vfisv_autotune", "vfisv_voigt", "VfisvError",
+    "library_path",
     "load",
     "NN_NBLOB", "NN_NTRAIN",
 ]
@@ -105,6 +106,8 @@ def load():
                                    ctypes.POINTER(vfisv_config), I64, ctypes.POINTER(I32),
                                    P, P]
     lib.vfisv_autotune.restype = ctypes.c_int
+    lib.vfisv_voigt.argtypes = [P, P, P, I64, I32, P, P, P]
+    lib.vfisv_voigt.restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -428,3 +431,23 @@ def vfisv_autotune(h: Handle, obs, weights, filters, wl_mA, line, config=None, s
                                  ctypes.byref(best), ms.ctypes.data,
                                  ctypes.c_void_p(_stream(obs, stream))), "vfisv_autotune")
     return int(best.value), ms.tolist()
+
+
+VOIGT_RATIONAL, VOIGT_TAYLOR1, VOIGT_TAYLOR2 = 0, 1, 2
+
+
+def vfisv_voigt(h: Handle, a, u, method: int = VOIGT_RATIONAL, stream=None):
+    """(H, F) = (Re, Im) w(u + i a) for arrays a, u of equal length."""
+    n = int(np.prod(u.shape))
+    H = _empty(u, tuple(u.shape), np.float32)
+    F = _empty(u, tuple(u.shape), np.float32)
+    ap, k1 = _ptr(a, np.float32)
+    up_, k2 = _ptr(u, np.float32)
+    hp, kh = _ptr(H, np.float32)
+    fp, kf = _ptr(F, np.float32)
+    _check(load().vfisv_voigt(h.ptr, ap, up_, n, int(method), hp, fp,
+                              ctypes.c_void_p(_stream(u, stream))), "vfisv_voigt")
+    for dst, k in ((H, kh), (F, kf)):
+        if not _is_torch(dst) and k is not dst:
+            dst[...] = k
+    return H, F

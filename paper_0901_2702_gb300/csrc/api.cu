@@ -24,6 +24,7 @@ struct vfisv_handle {
   void* mixws = nullptr;   // mixed inversion: guesses, gathered pixels, 2nd run
   size_t mixws_bytes = 0;
   int lm_block = 128;      // LM pixel slots per CTA (vfisv_autotune)
+  void* vtab = nullptr;    // Taylor table of H, F (built on first use)
   bool capturing = false;  // between vfisv_graph_begin and vfisv_graph_end
 };
 
@@ -334,6 +335,7 @@ void vfisv_destroy(vfisv_handle* h) {
   if (h->stage) cudaFree(h->stage);
   if (h->nnws) cudaFree(h->nnws);
   if (h->mixws) cudaFree(h->mixws);
+  if (h->vtab) cudaFree(h->vtab);
   delete h;
 }
 
@@ -437,6 +439,33 @@ int vfisv_autotune(vfisv_handle* h, const float* obs, const float* weights,
   h->lm_block = best_b;
   *best_block = best_b;
   return rc;
+}
+
+int vfisv_voigt(vfisv_handle* h, const float* a, const float* u, int64_t n, int32_t method,
+                float* H, float* F, void* stream) {
+  if (!h || !a || !u || !H || !F || method < 0 || method > 2) return VFISV_E_ARG;
+  if (n < 0) return VFISV_E_SIZE;
+  if (n == 0) return VFISV_OK;
+  if (set_device(h)) return VFISV_E_CUDA;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (method > 0 && !h->vtab) {
+    size_t have = 0;
+    int rc = grow(&h->vtab, &have, voigt_table_bytes());
+    if (rc) return rc;
+    if (launch_voigt_table(h->W, h->vtab, s) != cudaSuccess) return VFISV_E_CUDA;
+  }
+  Staging st;
+  st.add(a, (size_t)n * sizeof(float), false);
+  st.add(u, (size_t)n * sizeof(float), false);
+  st.add(H, (size_t)n * sizeof(float), true);
+  st.add(F, (size_t)n * sizeof(float), true);
+  int rc = st.prepare(h, s);
+  if (rc) return rc;
+  if (launch_voigt(method, h->W, h->vtab, (const float*)st.bufs[0].dev,
+                   (const float*)st.bufs[1].dev, n, (float*)st.bufs[2].dev,
+                   (float*)st.bufs[3].dev, s) != cudaSuccess)
+    return VFISV_E_CUDA;
+  return st.finish(s);
 }
 
 int vfisv_check(vfisv_handle* h, void* stream) {

@@ -154,4 +154,10 @@ cudaError_t launch_covariance(float* cov, const int32_t* status, int64_t npix,
 cudaError_t launch_invert(const InvertArgs& a, int nf, int grid, int block, size_t smem,
                           cudaStream_t s);
 
+// voigt.cu: bulk Voigt/Faraday-Voigt evaluation and the Taylor table.
+size_t voigt_table_bytes();
+cudaError_t launch_voigt_table(const Weideman& W, void* tab, cudaStream_t s);
+cudaError_t launch_voigt(int method, const Weideman& W, const void* tab, const float* a,
+                         const float* u, int64_t n, float* H, float* F, cudaStream_t s);
+
 }  // namespace vfisv
