@@ -61,6 +61,12 @@ TRAIN_N, TRAIN_EPOCHS, TRAIN_BATCH = 1 << 22, 8, 8192
 # filtered derivative rows 4 x 132.
 FLOP_PER_LAMBDA = 4 + 3 * 135 + 16 + 32 + 48 + 28 + 14 + 4 + 6 + 63 + 4 * 132
 FLOP_PER_PASS_EXTRA = 60  # model and residual outside the wavelength loop
+# DRAM bytes (read + write) of one plain-LM launch without covariance, per
+# pixel, from one ncu capture of invert_kernel on 262,144 pixels of the
+# 1024^2 distributions (54.8 MB read + 147.0 MB write; profiles/
+# invert_kernel_traffic.md); scaled by the pixels of a launch.  Algorithmic:
+# 192 B read (observables, weights) + 52 B written (model, chi2, counts).
+TRAFFIC_BYTES_PER_PIXEL = 201_875_968 / 262_144
 
 
 def fp32_peak_tflops(sm_mhz: float, nsm: int = 152) -> float:
@@ -321,7 +327,11 @@ def run_ours(args, rank, world):
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": None,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak,
+                     "traffic": int(TRAFFIC_BYTES_PER_PIXEL * npix),
+                     "traffic_note": "dram read+write bytes per launch, scaled by pixels from a "
+                                     "262,144-pixel ncu capture (770 B/px; algorithmic 244 B/px, "
+                                     "the rest is register-spill/call-stack write-back)",
                      "kernel": "invert_kernel<6> (plain LM pass, no covariance)",
                      "kernel_ms": ms_lm,
                      "note": "peak = FP32 pipe, 152 SM x 128 lanes x 2 flop x 2070 MHz (no "
