@@ -132,6 +132,16 @@ const char* vfisv_strerror(int code);
 int vfisv_voigt(vfisv_handle* h, const float* a, const float* u, int64_t n, int32_t method,
                 float* H, float* F, void* stream);
 
+/* Weights for full-disk maps (Sec. 4.3): w_I = 0.7778 |I_cont(mu) - I_c| + 0.3
+ * (Eq. 14) with I_cont(mu) the quintic centre-to-limb law of Eq. 15 and I_c
+ * the pixel's largest Stokes I sample divided by the disk-centre continuum
+ * ic0; w_Q = w_U = w_V = 1.  Writes weights_out[npix][4][nfilt] = w^2 /
+ * sigma^2 with sigma4 (host float[4]) the noise of I, Q, U, V; mu[npix] is the
+ * heliocentric angle cosine of each pixel. */
+int vfisv_limb_weights(vfisv_handle* h, const float* obs, const float* mu, int64_t npix,
+                       int32_t nfilt, float ic0, const float* sigma4, float* weights_out,
+                       void* stream);
+
 /* Whole-map CUDA graphs.  vfisv_graph_begin starts a (relaxed-mode) capture
  * on `stream` (not the legacy NULL stream); every vfisv_* call made with the
  * handle and device buffers until vfisv_graph_end is recorded instead of

@@ -263,3 +263,28 @@ def invert_mixed(obs, w, filters, x, line, blob, nn_cap=20, plain_cap=50, chi2_f
         for k in ("params", "chi2", "status", "cov"):
             out[k][ids[take]] = q[k][take]
     return out
+
+
+# --- Sec. 4.3: weights for full-disk maps ----------------------------------
+
+ICONT_MU_COEFFS = (0.33644, 1.30590, -1.79238, 2.45050, -1.89979, 0.59943)
+
+
+def icont_mu(mu):
+    """Eq. 15: continuum intensity versus mu near 6173 A (disk centre = 1)."""
+    mu = np.asarray(mu, dtype=np.float64)
+    return sum(c * mu ** k for k, c in enumerate(ICONT_MU_COEFFS))
+
+
+def limb_weights(obs, mu, ic0, sigma, nfilt=6):
+    """Eq. 14 weights as w^2 / sigma^2 per observable [npix, 4*nfilt]:
+    w_I = 0.7778 |I_cont(mu) - I_cont(x,y)| + 0.3, w_Q = w_U = w_V = 1, with
+    I_cont(x,y) the pixel's largest Stokes I sample divided by the disk-centre
+    continuum ic0; sigma[4] is the noise of I, Q, U, V."""
+    obs = np.asarray(obs, dtype=np.float64)
+    ic = obs[:, :nfilt].max(axis=1) / ic0
+    wI = 0.7778 * np.abs(icont_mu(mu) - ic) + 0.3
+    w = np.ones((obs.shape[0], 4))
+    w[:, 0] = wI
+    s = np.asarray(sigma, dtype=np.float64)[None, :]
+    return np.repeat(w * w / (s * s), nfilt, axis=1)

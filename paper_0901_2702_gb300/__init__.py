@@ -19,7 +19,8 @@ __all__ = [
     "vfisv_create", "vfisv_destroy", "vfisv_synth", "vfisv_invert", "vfisv_check",
     "vfisv_strerror", "vfisv_config_default", "vfisv_nn_init", "vfisv_nn_train",
     "vfisv_nn_grad", "vfisv_nn_infer", "vfisv_invert_nn", "vfisv_graph_begin", "vfisv_graph_end",
-    "vfisv_graph_launch", "vfisv_graph_destroy", "vfisv_autotune", "vfisv_voigt", "VfisvError",
+    "vfisv_graph_launch", "vfisv_graph_destroy", "vfisv_autotune", "vfisv_voigt",
+    "vfisv_limb_weights", "VfisvError",
     "library_path",
     "load",
     "NN_NBLOB", "NN_NTRAIN",
@@ -108,6 +109,8 @@ def load():
     lib.vfisv_autotune.restype = ctypes.c_int
     lib.vfisv_voigt.argtypes = [P, P, P, I64, I32, P, P, P]
     lib.vfisv_voigt.restype = ctypes.c_int
+    lib.vfisv_limb_weights.argtypes = [P, P, P, I64, I32, ctypes.c_float, P, P, P]
+    lib.vfisv_limb_weights.restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -451,3 +454,20 @@ def vfisv_voigt(h: Handle, a, u, method: int = VOIGT_RATIONAL, stream=None):
         if not _is_torch(dst) and k is not dst:
             dst[...] = k
     return H, F
+
+
+def vfisv_limb_weights(h: Handle, obs, mu, ic0: float, sigma4, stream=None):
+    """Eq. 14 weights (w^2/sigma^2) [npix, 4*nfilt] for observables obs [npix, 4*nfilt]."""
+    npix = int(obs.shape[0])
+    nobs = int(np.prod(obs.shape)) // max(npix, 1)
+    out = _empty(obs, (npix, nobs), np.float32)
+    op, k1 = _ptr(obs, np.float32)
+    mp, k2 = _ptr(mu, np.float32)
+    outp, ko = _ptr(out, np.float32)
+    s4 = np.ascontiguousarray(sigma4, dtype=np.float32)
+    _check(load().vfisv_limb_weights(h.ptr, op, mp, npix, nobs // 4, float(ic0), s4.ctypes.data,
+                                     outp, ctypes.c_void_p(_stream(obs, stream))),
+           "vfisv_limb_weights")
+    if not _is_torch(out) and ko is not out:
+        out[...] = ko
+    return out

@@ -468,6 +468,28 @@ int vfisv_voigt(vfisv_handle* h, const float* a, const float* u, int64_t n, int3
   return st.finish(s);
 }
 
+int vfisv_limb_weights(vfisv_handle* h, const float* obs, const float* mu, int64_t npix,
+                       int32_t nfilt, float ic0, const float* sigma4, float* weights_out,
+                       void* stream) {
+  if (!h || !obs || !mu || !sigma4 || !weights_out || !(ic0 > 0)) return VFISV_E_ARG;
+  for (int i = 0; i < 4; ++i)
+    if (!(sigma4[i] > 0)) return VFISV_E_ARG;
+  if (npix < 0 || nfilt < 1 || nfilt > 64) return VFISV_E_SIZE;
+  if (npix == 0) return VFISV_OK;
+  if (set_device(h)) return VFISV_E_CUDA;
+  cudaStream_t s = (cudaStream_t)stream;
+  Staging st;
+  st.add(obs, (size_t)npix * 4 * nfilt * sizeof(float), false);
+  st.add(mu, (size_t)npix * sizeof(float), false);
+  st.add(weights_out, (size_t)npix * 4 * nfilt * sizeof(float), true);
+  int rc = st.prepare(h, s);
+  if (rc) return rc;
+  if (launch_limb_weights((const float*)st.bufs[0].dev, (const float*)st.bufs[1].dev, npix, nfilt,
+                          ic0, sigma4, (float*)st.bufs[2].dev, s) != cudaSuccess)
+    return VFISV_E_CUDA;
+  return st.finish(s);
+}
+
 int vfisv_check(vfisv_handle* h, void* stream) {
   if (!h) return VFISV_E_ARG;
   if (set_device(h)) return VFISV_E_CUDA;

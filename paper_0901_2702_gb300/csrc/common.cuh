@@ -160,4 +160,8 @@ cudaError_t launch_voigt_table(const Weideman& W, void* tab, cudaStream_t s);
 cudaError_t launch_voigt(int method, const Weideman& W, const void* tab, const float* a,
                          const float* u, int64_t n, float* H, float* F, cudaStream_t s);
 
+// prep.cu: Eq. 14-15 weights
+cudaError_t launch_limb_weights(const float* obs, const float* mu, int64_t npix, int nf,
+                                float ic0, const float* sigma4, float* w, cudaStream_t s);
+
 }  // namespace vfisv

@@ -154,3 +154,22 @@ def test_bounds_equivalences():
     q = p.copy()
     q[:, 1] = -q[:, 1]
     np.testing.assert_allclose(me.synth(q, T, X, LINE), me.synth(lm.apply_bounds(q), T, X, LINE), atol=1e-13)
+
+
+def test_eq15_limb_darkening_golden():
+    rows = np.loadtxt(os.path.join(GOLD, "eq15_icont.txt"))
+    for mu, ic in rows:
+        assert abs(lm.icont_mu(mu) - ic) < 1e-12
+    mu = np.linspace(0.05, 1, 50)
+    assert np.all(np.diff(lm.icont_mu(mu)) > 0)   # limb darkening: brighter towards the centre
+
+
+def test_eq14_weights():
+    obs = np.zeros((3, 24))
+    obs[:, :6] = np.array([[1.0], [0.5], [0.2]])   # continuum 1, 0.5, 0.2 of disk centre
+    w = lm.limb_weights(obs, np.array([1.0, 1.0, 1.0]), 1.0, [1e-3, 1e-3, 1e-3, 1e-3])
+    wI = 0.7778 * np.abs(1.0001 - np.array([1.0, 0.5, 0.2])) + 0.3
+    np.testing.assert_allclose(w[:, 0], wI ** 2 / 1e-6, rtol=1e-12)
+    np.testing.assert_allclose(w[:, 6:], 1e6, rtol=1e-12)
+    # quiet Sun (continuum ~ I_cont(mu)) gets w_I ~ 0.3, a dark umbra ~ 1
+    assert abs(np.sqrt(w[0, 0] * 1e-6) - 0.3) < 1e-3 and np.sqrt(w[2, 0] * 1e-6) > 0.9

@@ -127,6 +127,14 @@ def disk_mask(side: int = 4096, radius: float = 2073.0) -> np.ndarray:
     return (xx - c) ** 2 + (yy - c) ** 2 <= radius * radius
 
 
+def disk_mu(idx: np.ndarray, side: int = 4096, radius: float = 2073.0) -> np.ndarray:
+    """Heliocentric angle cosine mu = sqrt(1 - (r/R)^2) of flat pixel indices."""
+    c = (side - 1) / 2.0
+    x = (idx % side).astype(np.float64) - c
+    y = (idx // side).astype(np.float64) - c
+    return np.sqrt(np.clip(1.0 - (x * x + y * y) / (radius * radius), 0.0, 1.0))
+
+
 def full_disk_params(seed: int, side: int = 4096, radius: float = 2073.0,
                      active_fraction: float = 0.10):
     """Full-disk map: returns (params [n_on_disk, 10], flat pixel indices).
