@@ -102,13 +102,33 @@ typedef struct {
  *   conv_rtol  converged when a successful step lowers chi2 by less than
  *              conv_rtol relative while the damping used was <= conv_eps.
  *   eps0       initial damping.
- * vfisv_config_default() fills: 50, 0x1FF, 1e-4, 1.0, 1.0. */
+ *   restarts   randomised restarts (Sec. 4.2), a bit mask; 0 = off (a pixel
+ *              stops when converged).  With any bit set every pixel runs
+ *              exactly max_iter iterations and a restart is due
+ *                bit 0  when a step meets the convergence test or the pixel
+ *                       stalls (else such a pixel stops there),
+ *                bit 1  (the paper's (a)) at iteration 10 if the best chi2 is
+ *                       not below a tenth of the initial chi2,
+ *                bit 2  (the paper's (b)) after 5 failed trials in a row;
+ *              7 = the paper's rule.  A restart replaces the next trial: the
+ *              best model of all segments, perturbed as vfisv_restart_models
+ *              does with k = the pixel's restart count, starts a new segment
+ *              whatever its chi2, with the damping reset to eps0; it counts
+ *              as one iteration.  Outputs are the best model of all segments,
+ *              its chi2 and covariance; status CONVERGED if any segment
+ *              converged, else STALLED if any stalled, else MAXITER.
+ *              The pixel number of the perturbations is the pixel's index in
+ *              the call.  max_iter must stay below 2^20 with restarts.
+ *   seed       key of the perturbations.
+ * vfisv_config_default() fills: 50, 0x1FF, 1e-4, 1.0, 1.0, 0, 0. */
 typedef struct {
   int32_t max_iter;
   uint32_t free_mask;
   double conv_rtol;
   double conv_eps;
   double eps0;
+  int32_t restarts;
+  uint64_t seed;
 } vfisv_config;
 
 typedef struct vfisv_handle vfisv_handle;
@@ -131,6 +151,20 @@ const char* vfisv_strerror(int code);
  * Points outside the table use the rational series.  Arrays float32[n]. */
 int vfisv_voigt(vfisv_handle* h, const float* a, const float* u, int64_t n, int32_t method,
                 float* H, float* F, void* stream);
+
+/* The perturbation of a randomised restart (Sec. 4.2), in bulk: models_out
+ * [n][10] = restart number k (1 <= k < 2^20) of pixels pixel0 .. pixel0+n-1
+ * from models [n][10].  With r = 2u - 1 and u uniform in [0, 1), the free
+ * parameters among B, gamma, psi, eta0, dlambdaD, a, v move by r*k times
+ * 150 G, 10 deg, 15 deg, (ln eta0) 0.25, 4 mA, 0.05, 0.25 km/s; S0, S1,
+ * alpha and held parameters (free_mask bit clear) are copied; the model
+ * bounds of vfisv_invert are applied.  u is the top 53 bits of SplitMix64
+ * (Steele, Lea & Flood 2014) output number (pixel << 24 | k << 4 | p) of the
+ * stream keyed by `seed`, p the parameter's index.  Host or device buffers.
+ * pixel0 + n <= 2^40. */
+int vfisv_restart_models(vfisv_handle* h, const float* models, int64_t n, int64_t pixel0,
+                         int32_t k, uint32_t free_mask, uint64_t seed, float* models_out,
+                         void* stream);
 
 /* Weights for full-disk maps (Sec. 4.3): w_I = 0.7778 |I_cont(mu) - I_c| + 0.3
  * (Eq. 14) with I_cont(mu) the quintic centre-to-limb law of Eq. 15 and I_c
@@ -271,7 +305,7 @@ int vfisv_invert_nn(vfisv_handle* h, const float* blob, const float* obs, const 
  *   - All pointers must be device memory; arguments and outputs are those
  *     of vfisv_invert, on the current CUDA device, asynchronous on `stream`.
  *   - nlam <= VFISV_NOALLOC_MAX_NLAM (4096) and nfilt == 6, else
- *     VFISV_E_SIZE / VFISV_E_UNSUPPORTED.  Any npix works: at most
+ *     VFISV_E_SIZE / VFISV_E_UNSUPPORTED; cfg->restarts must be 0.  Any npix works: at most
  *     VFISV_NOALLOC_MAX_SLOTS pixels are resident at once and the others
  *     queue behind them.
  *   - The first call on a device looks up the array's device address and

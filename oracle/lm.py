@@ -41,6 +41,25 @@ Readings of points the paper leaves open or prints garbled:
 * Covariance: (J^T W J)^+ at the final model (eps = 0), computed in the
   Jacobi-scaled form with the same SVD truncation, zero for held
   parameters.
+* Randomised restarts (Sec. 4.2, optional, ``restarts`` a bit mask): every
+  pixel runs exactly ``max_iter`` iterations.  A restart is due (bit 0)
+  when a step meets the convergence test or the pixel stalls, (bit 1, the
+  paper's (a)) at iteration 10 of the inversion if chi2 is not below a
+  tenth of its initial value, (bit 2, the paper's (b)) when 5 trials in a
+  row have failed.  The paper states (a) for "the first 10 iterations", so
+  it is tested once, with the best chi2 so far, not in every segment.  The restart replaces the next
+  trial: the best model of all segments so far, perturbed with amplitudes
+  proportional to the restart count k (uniform in B +- 150k G,
+  gamma +- 10k deg, psi +- 15k deg, ln eta0 +- 0.25k, dlambdaD +- 4k mA,
+  a +- 0.05k, v +- 0.25k km/s; S0, S1 and held parameters untouched; bounds
+  applied), is evaluated and taken as the start of a new segment whatever
+  its chi2 (a non-finite one is retried with k + 1), with the damping reset
+  to eps0.  It counts as one iteration.  The result is the best model of
+  all segments (with its covariance); the status is CONVERGED if any
+  segment converged, else STALLED if any stalled, else MAXITER.  The
+  uniforms are SplitMix64 outputs (Steele, Lea & Flood 2014) at counter
+  (pixel << 24) | (k << 4) | p for parameter p, keyed by ``seed``; pixel is
+  the pixel's index in the call.
 """
 from __future__ import annotations
 
@@ -149,12 +168,55 @@ def covariance(A, free):
     return P * s[:, :, None] * s[:, None, :]
 
 
+# --- Sec. 4.2: randomised restarts ------------------------------------------
+
+_M64 = (1 << 64) - 1
+SPLITMIX_GAMMA = 0x9E3779B97F4A7C15
+RESTART_AMPLITUDE = np.array([150.0, 10.0, 15.0, 0.25, 4.0, 0.05, 0.25])  # per unit k; eta0 in ln
+RESTART_AT_CONVERGENCE, RESTART_A, RESTART_B = 1, 2, 4
+RESTART_A_ITER, RESTART_A_FACTOR, RESTART_B_FAILS = 10, 10.0, 5
+
+
+def splitmix64(seed, counter):
+    """The counter-th output (0-based) of SplitMix64 started from ``seed``:
+    the state advanced counter+1 times by the golden-ratio increment, then
+    the variant-13 64-bit finaliser (xor-shift 30, 27, 31 with the two odd
+    multipliers).  Python integers, so the wrap-around is explicit."""
+    z = (int(seed) + (int(counter) + 1) * SPLITMIX_GAMMA) & _M64
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & _M64
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & _M64
+    return z ^ (z >> 31)
+
+
+def restart_uniform(seed, pix, k, p):
+    """Uniform in [0, 1) from the top 53 bits of one SplitMix64 output."""
+    return (splitmix64(seed, (int(pix) << 24) | (int(k) << 4) | int(p)) >> 11) * 2.0 ** -53
+
+
+def restart_model(m, pix, k, seed, free):
+    """Perturbed copy of models m [n, 10] for restart number k of pixels pix."""
+    out = np.array(m, dtype=np.float64, copy=True)
+    for i, (px, kk) in enumerate(zip(np.atleast_1d(pix), np.broadcast_to(k, len(out)))):
+        for p in range(7):
+            if not free[p]:
+                continue
+            r = 2.0 * restart_uniform(seed, px, kk, p) - 1.0
+            amp = RESTART_AMPLITUDE[p] * kk * r
+            if p == me.ETA0:
+                out[i, p] *= np.exp(amp)
+            else:
+                out[i, p] += amp
+    return apply_bounds(out)
+
+
 def invert(obs, w, filters, x, line, init=None, max_iter=50, conv_rtol=1e-4,
-           conv_eps=1.0, eps0=1.0, free_mask=DEFAULT_FREE, trace=False):
+           conv_eps=1.0, eps0=1.0, free_mask=DEFAULT_FREE, restarts=0, seed=0,
+           trace=False):
     """Invert observed Stokes [npix, 4*nfilt] with weights w^2/sigma^2.
 
     Returns a dict with params [npix,10], chi2 [npix], iters [npix],
-    status [npix], cov [npix,10,10], accepted [npix].
+    status [npix], cov [npix,10,10], accepted [npix] (and, with restarts,
+    restarts [npix]).
     """
     obs = np.asarray(obs, dtype=np.float64)
     w = np.asarray(w, dtype=np.float64)
@@ -195,11 +257,38 @@ def invert(obs, w, filters, x, line, init=None, max_iter=50, conv_rtol=1e-4,
     status[nan0] = NAN_STATE
     done = bad | nan0
     hist = []
+    if restarts:
+        best_m, best_c2, best_A, best_g = m.copy(), c2.copy(), A.copy(), g.copy()
+        c2_first = c2.copy()
+        nfail = np.zeros(npix, dtype=np.int64)
+        nrestart = np.zeros(npix, dtype=np.int64)
+        ever_conv = np.zeros(npix, dtype=bool)
+        ever_stall = np.zeros(npix, dtype=bool)
+        pending = np.zeros(npix, dtype=bool)
 
     for _ in range(max_iter):
         act = np.flatnonzero(~done)
         if act.size == 0:
             break
+        rs = np.zeros(0, dtype=np.int64)
+        if restarts:
+            rs = act[pending[act]]
+            act = act[~pending[act]]
+            if rs.size:
+                # the restart pass: perturbed best model, a new segment
+                nrestart[rs] += 1
+                mt = restart_model(best_m[rs], rs, nrestart[rs], seed, free)
+                sr, Jr = model(mt, True)
+                cr = chi2(obs_s[rs], sr, w_s[rs], nfree)
+                iters[rs] += 1
+                fin = np.isfinite(cr)
+                ok_r = rs[fin]
+                m[ok_r], c2[ok_r] = mt[fin], cr[fin]
+                Ar, gr = normal_equations(Jr[fin], obs_s[ok_r] - sr[fin], w_s[ok_r], free)
+                A[ok_r], g[ok_r] = Ar, gr
+                nfail[ok_r] = 0
+                eps[ok_r] = float(eps0)
+                pending[ok_r] = False        # a non-finite restart is retried with k + 1
         delta = damped_step(A[act], g[act], eps[act], free)
         mt = apply_bounds(m[act] + delta)
         st = model(mt, False)
@@ -209,6 +298,7 @@ def invert(obs, w, filters, x, line, init=None, max_iter=50, conv_rtol=1e-4,
         eps_used = eps[act].copy()
         eps[act] = eps_update(eps_used, ok)
         acc = act[ok]
+        conv_now = np.zeros(0, dtype=np.int64)
         if acc.size:
             rel = (c2[acc] - ct[ok]) / c2[acc]
             m[acc] = mt[ok]
@@ -218,18 +308,51 @@ def invert(obs, w, filters, x, line, init=None, max_iter=50, conv_rtol=1e-4,
             Aa, ga = normal_equations(Ja, obs_s[acc] - sa, w_s[acc], free)
             A[acc], g[acc] = Aa, ga
             conv = (rel < conv_rtol) & (eps_used[ok] <= conv_eps)
-            status[acc[conv]] = CONVERGED
-            done[acc[conv]] = True
+            conv_now = acc[conv]
         rej = act[~ok]
-        stall = rej[eps[rej] >= EPS_MAX]
-        status[stall] = STALLED
-        done[stall] = True
+        stall_now = rej[eps[rej] >= EPS_MAX]
+        if restarts:
+            moved = np.concatenate([acc, rs])
+            nb = moved[c2[moved] < best_c2[moved]]
+            best_m[nb], best_c2[nb], best_A[nb], best_g[nb] = m[nb], c2[nb], A[nb], g[nb]
+            nfail[acc] = 0
+            nfail[rej] += 1
+            ever_conv[conv_now] = True
+            ever_stall[stall_now] = True
+            trig = np.zeros(npix, dtype=bool)
+            if restarts & RESTART_AT_CONVERGENCE:
+                trig[conv_now] = True
+                trig[stall_now] = True
+            else:                                # a converged or stalled pixel stops
+                status[conv_now] = CONVERGED
+                status[stall_now] = STALLED
+                done[conv_now] = True
+                done[stall_now] = True
+            if restarts & RESTART_A:
+                trig[act] |= (iters[act] == RESTART_A_ITER) & ~(best_c2[act] <= c2_first[act] / RESTART_A_FACTOR)
+            if restarts & RESTART_B:
+                trig[act] |= nfail[act] >= RESTART_B_FAILS
+            pending |= trig & ~done
+            done |= iters >= max_iter
+        else:
+            status[conv_now] = CONVERGED
+            done[conv_now] = True
+            status[stall_now] = STALLED
+            done[stall_now] = True
         if trace:
-            hist.append((act.size, acc.size))
+            hist.append((act.size + rs.size, acc.size))
 
+    out = {"accepted": nacc, "iters": iters}
+    if restarts:
+        ran = ~bad & ~nan0
+        m = np.where(ran[:, None], best_m, m)
+        c2 = np.where(ran, best_c2, c2)
+        A = np.where(ran[:, None, None], best_A, A)
+        status[ran] = np.where(ever_conv[ran], CONVERGED,
+                               np.where(ever_stall[ran], STALLED, MAXITER))
+        out["restarts"] = nrestart
     cov = covariance(A, free)
-    out = {"params": m, "chi2": c2, "iters": iters, "status": status,
-           "cov": cov, "accepted": nacc}
+    out.update({"params": m, "chi2": c2, "status": status, "cov": cov})
     if trace:
         out["trace"] = hist
     return out

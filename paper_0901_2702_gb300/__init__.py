@@ -20,7 +20,7 @@ __all__ = [
     "vfisv_strerror", "vfisv_config_default", "vfisv_nn_init", "vfisv_nn_train",
     "vfisv_nn_grad", "vfisv_nn_infer", "vfisv_invert_nn", "vfisv_graph_begin", "vfisv_graph_end",
     "vfisv_graph_launch", "vfisv_graph_destroy", "vfisv_autotune", "vfisv_voigt",
-    "vfisv_limb_weights", "VfisvError",
+    "vfisv_limb_weights", "vfisv_restart_models", "VfisvError",
     "library_path",
     "load",
     "NN_NBLOB", "NN_NTRAIN",
@@ -50,7 +50,8 @@ class vfisv_line(ctypes.Structure):
 class vfisv_config(ctypes.Structure):
     _fields_ = [("max_iter", ctypes.c_int32), ("free_mask", ctypes.c_uint32),
                 ("conv_rtol", ctypes.c_double), ("conv_eps", ctypes.c_double),
-                ("eps0", ctypes.c_double)]
+                ("eps0", ctypes.c_double), ("restarts", ctypes.c_int32),
+                ("seed", ctypes.c_uint64)]
 
 
 def library_path() -> str:
@@ -111,6 +112,8 @@ def load():
     lib.vfisv_voigt.restype = ctypes.c_int
     lib.vfisv_limb_weights.argtypes = [P, P, P, I64, I32, ctypes.c_float, P, P, P]
     lib.vfisv_limb_weights.restype = ctypes.c_int
+    lib.vfisv_restart_models.argtypes = [P, P, I64, I64, I32, ctypes.c_uint32, U64, P, P]
+    lib.vfisv_restart_models.restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -468,6 +471,21 @@ def vfisv_limb_weights(h: Handle, obs, mu, ic0: float, sigma4, stream=None):
     _check(load().vfisv_limb_weights(h.ptr, op, mp, npix, nobs // 4, float(ic0), s4.ctypes.data,
                                      outp, ctypes.c_void_p(_stream(obs, stream))),
            "vfisv_limb_weights")
+    if not _is_torch(out) and ko is not out:
+        out[...] = ko
+    return out
+
+
+def vfisv_restart_models(h: Handle, models, pixel0: int, k: int, free_mask: int = 0x1FF,
+                         seed: int = 0, stream=None):
+    """Restart number k of pixels pixel0.. from models [n, 10] (Sec. 4.2)."""
+    n = int(models.shape[0])
+    out = _empty(models, (n, 10), np.float32)
+    mp, k1 = _ptr(models, np.float32)
+    outp, ko = _ptr(out, np.float32)
+    _check(load().vfisv_restart_models(h.ptr, mp, n, int(pixel0), int(k), int(free_mask),
+                                       int(seed), outp, ctypes.c_void_p(_stream(models, stream))),
+           "vfisv_restart_models")
     if not _is_torch(out) and ko is not out:
         out[...] = ko
     return out

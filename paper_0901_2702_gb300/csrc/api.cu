@@ -172,15 +172,16 @@ struct Staging {
   }
 };
 
-// Workspace layout: [err int | queue u64 | pad] [table] [scratch]
+// Workspace layout: [err int | queue u64 | pad] [table] [scratch] [restart state]
 struct WsLayout {
-  size_t err = 0, queue = 64, table = 256, scratch = 0, total = 0;
+  size_t err = 0, queue = 64, table = 256, scratch = 0, rs = 0, total = 0;
 };
 
-WsLayout layout(int nf, int nlam, int64_t nslots) {
+WsLayout layout(int nf, int nlam, int64_t nslots, bool restarts) {
   WsLayout L;
   L.scratch = L.table + up((size_t)table_floats(nf, nlam) * sizeof(float));
-  L.total = L.scratch + up((size_t)kScratchPerSlot * (size_t)nslots * sizeof(float));
+  L.rs = L.scratch + up((size_t)kScratchPerSlot * (size_t)nslots * sizeof(float));
+  L.total = L.rs + (restarts ? up(kRsBytesPerSlot * (size_t)nslots) : 0);
   return L;
 }
 
@@ -195,6 +196,8 @@ int check_config(const vfisv_config* cfg, int nfilt) {
   if (cfg->max_iter < 0 || (cfg->free_mask & ~0x1FFu) || !(cfg->conv_rtol >= 0) ||
       !(cfg->conv_eps >= 0) || !(cfg->eps0 > 0) || !isfinite(cfg->eps0))
     return VFISV_E_ARG;
+  // restart counters are 20 bits wide (each restart costs an iteration)
+  if ((cfg->restarts & ~7) || (cfg->restarts && cfg->max_iter >= (1 << 20))) return VFISV_E_ARG;
   if (4 * nfilt - __builtin_popcount(cfg->free_mask) <= 0) return VFISV_E_ARG;
   return VFISV_OK;
 }
@@ -228,11 +231,12 @@ int invert_device(vfisv_handle* h, const DevInvert& d, int nfilt, int nlam,
   int64_t nslots = 0;
   int grid = 0, block = h->lm_block;
   size_t smem = 0;
-  if (invert_slots(nfilt, nlam, npix, &nslots, &grid, &block, &smem) != cudaSuccess) {
+  if (invert_slots(nfilt, nlam, npix, cfg->restarts, &nslots, &grid, &block, &smem) !=
+      cudaSuccess) {
     cudaGetLastError();
     return VFISV_E_CUDA;
   }
-  WsLayout L = layout(nfilt, nlam, nslots);
+  WsLayout L = layout(nfilt, nlam, nslots, cfg->restarts != 0);
   if (h->ws_bytes < L.total) {
     int rc = grow(&h->ws, &h->ws_bytes, L.total);
     if (rc) return rc;
@@ -270,6 +274,9 @@ int invert_device(vfisv_handle* h, const DevInvert& d, int nfilt, int nlam,
   a.conv_rtol = cfg->conv_rtol;
   a.conv_eps = cfg->conv_eps;
   a.eps0 = cfg->eps0;
+  a.restarts = cfg->restarts;
+  a.seed = cfg->seed;
+  a.rs_state = cfg->restarts ? ws + L.rs : nullptr;
   if (launch_invert(a, nfilt, grid, block, smem, s) != cudaSuccess) return VFISV_E_CUDA;
   if (d.cov && launch_covariance(d.cov, d.status, npix, npix_dev, cfg->free_mask, s) !=
                    cudaSuccess)
@@ -304,6 +311,8 @@ void vfisv_config_default(vfisv_config* c) {
   c->conv_rtol = 1e-4;
   c->conv_eps = 1.0;
   c->eps0 = 1.0;
+  c->restarts = 0;
+  c->seed = 0;
 }
 
 int vfisv_create(vfisv_handle** out, int device) {
@@ -468,6 +477,26 @@ int vfisv_voigt(vfisv_handle* h, const float* a, const float* u, int64_t n, int3
   return st.finish(s);
 }
 
+int vfisv_restart_models(vfisv_handle* h, const float* models, int64_t n, int64_t pixel0,
+                         int32_t k, uint32_t free_mask, uint64_t seed, float* models_out,
+                         void* stream) {
+  if (!h || !models || !models_out || (free_mask & ~0x1FFu)) return VFISV_E_ARG;
+  if (n < 0 || pixel0 < 0 || pixel0 + n > (1ll << 40) || k < 1 || k >= (1 << 20))
+    return VFISV_E_SIZE;
+  if (n == 0) return VFISV_OK;
+  if (set_device(h)) return VFISV_E_CUDA;
+  cudaStream_t s = (cudaStream_t)stream;
+  Staging st;
+  st.add(models, (size_t)n * 10 * sizeof(float), false);
+  st.add(models_out, (size_t)n * 10 * sizeof(float), true);
+  int rc = st.prepare(h, s);
+  if (rc) return rc;
+  if (launch_restart_perturb((const float*)st.bufs[0].dev, n, pixel0, k, free_mask, seed,
+                             (float*)st.bufs[1].dev, s) != cudaSuccess)
+    return VFISV_E_CUDA;
+  return st.finish(s);
+}
+
 int vfisv_limb_weights(vfisv_handle* h, const float* obs, const float* mu, int64_t npix,
                        int32_t nfilt, float ic0, const float* sigma4, float* weights_out,
                        void* stream) {
@@ -516,7 +545,7 @@ int vfisv_synth(vfisv_handle* h, const float* params, int64_t npix, const float*
   if (npix == 0) return VFISV_OK;
   if (set_device(h)) return VFISV_E_CUDA;
   cudaStream_t s = (cudaStream_t)stream;
-  WsLayout L = layout(nfilt, nlam, 0);
+  WsLayout L = layout(nfilt, nlam, 0, false);
   if (h->ws_bytes < L.total) {
     int rc = grow(&h->ws, &h->ws_bytes, L.total);
     if (rc) return rc;

@@ -134,9 +134,29 @@ struct InvertArgs {
   double conv_rtol;
   double conv_eps;
   double eps0;
+  int restarts = 0;          // randomised restarts (Sec. 4.2): trigger bit mask, 0 = off
+  uint64_t seed = 0;         // key of the restart perturbations
+  char* rs_state = nullptr;  // restarts: per-slot state, layout RestartState
 };
 
 constexpr int kScratchPerSlot = 45 + 9;  // packed J^T W J and J^T W r
+
+// Per-slot state of the randomised restarts, structure of arrays over the
+// slots: FP64 [2][ns] (best chi2, initial chi2), FP32 [64][ns] (J^T W J,
+// J^T W r and the model at the best chi2), int [3][ns] (failed trials in a
+// row, restart count, flags).
+constexpr int kRsDoubles = 2, kRsFloats = kScratchPerSlot + 10, kRsInts = 3;
+constexpr size_t kRsBytesPerSlot = 8 * kRsDoubles + 4 * kRsFloats + 4 * kRsInts;
+struct RestartState {
+  double* chi2;  // [2][ns]
+  float* f;      // [64][ns]
+  int* i;        // [3][ns]
+  __host__ __device__ RestartState(char* base, int64_t ns)
+      : chi2(reinterpret_cast<double*>(base)),
+        f(reinterpret_cast<float*>(base + 8 * kRsDoubles * ns)),
+        i(reinterpret_cast<int*>(base + (8 * kRsDoubles + 4 * kRsFloats) * ns)) {}
+};
+constexpr int kRestartAtConvergence = 1, kRestartA = 2, kRestartB = 4;
 
 cudaError_t launch_pack_table(const float* filters, int nf, const float* wl, int nlam,
                               float* table, cudaStream_t s);
@@ -144,8 +164,10 @@ cudaError_t launch_synth(const SynthArgs& a, int nf, cudaStream_t s);
 // Persistent LM kernel: launch shape for `npix` pixels with *block pixel
 // slots per CTA (64, 128 or 256; anything else selects 128 and is written
 // back), and the number of resident slots (the scratch it needs).
-cudaError_t invert_slots(int nf, int nlam, int64_t npix, int64_t* nslots, int* grid,
-                         int* block, size_t* smem);
+cudaError_t invert_slots(int nf, int nlam, int64_t npix, int restarts, int64_t* nslots,
+                         int* grid, int* block, size_t* smem);
+cudaError_t launch_restart_perturb(const float* in, int64_t n, int64_t pix0, int k,
+                                   uint32_t free_mask, uint64_t seed, float* out, cudaStream_t s);
 // Upload the Weideman coefficients to the LM kernel's constant bank on the
 // current device (once per device).
 cudaError_t invert_set_constants(const Weideman& W);

@@ -267,6 +267,57 @@ __device__ __noinline__ bool covariance(const float* scr, int64_t ns, uint32_t f
   return true;
 }
 
+// ---- randomised restarts (Sec. 4.2) ----
+// SplitMix64 (Steele, Lea & Flood 2014) read as a counter-based generator:
+// output number `ctr` of the stream started at `seed` is the variant-13
+// finaliser applied to seed + (ctr + 1) * golden-ratio increment.
+__host__ __device__ __forceinline__ uint64_t splitmix64(uint64_t seed, uint64_t ctr) {
+  uint64_t z = seed + (ctr + 1ull) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// Restart number k of pixel `pix`: uniform perturbations of the seven
+// non-linear parameters with half-widths proportional to k (eta0 in its
+// logarithm); S0, S1 and held parameters are left alone; bounds applied.
+__device__ __forceinline__ void restart_model(float (&m)[10], long long pix, int k,
+                                              uint64_t seed, uint32_t free_mask) {
+  constexpr double amp[7] = {150.0, 10.0, 15.0, 0.25, 4.0, 0.05, 0.25};
+#pragma unroll
+  for (int p = 0; p < 7; ++p) {
+    if (!((free_mask >> p) & 1u)) continue;
+    const uint64_t z = splitmix64(seed, ((uint64_t)pix << 24) | ((uint64_t)k << 4) | (uint64_t)p);
+    const double u = (double)(z >> 11) * 0x1.0p-53;  // [0, 1), 53 bits
+    const double d = amp[p] * (double)k * (2.0 * u - 1.0);
+    m[p] = (p == 3) ? (float)((double)m[p] * exp(d)) : (float)((double)m[p] + d);
+  }
+  apply_bounds(m);
+}
+
+__global__ void restart_perturb_kernel(const float* __restrict__ in, int64_t n, int64_t pix0,
+                                       int k, uint32_t free_mask, uint64_t seed,
+                                       float* __restrict__ out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    float m[10];
+#pragma unroll
+    for (int j = 0; j < 10; ++j) m[j] = in[i * 10 + j];
+    restart_model(m, pix0 + i, k, seed, free_mask);
+#pragma unroll
+    for (int j = 0; j < 10; ++j) out[i * 10 + j] = m[j];
+  }
+}
+
+cudaError_t launch_restart_perturb(const float* in, int64_t n, int64_t pix0, int k,
+                                   uint32_t free_mask, uint64_t seed, float* out, cudaStream_t s) {
+  int64_t grid = (n + 255) / 256;
+  if (grid > 4096) grid = 4096;
+  if (grid < 1) grid = 1;
+  restart_perturb_kernel<<<(int)grid, 256, 0, s>>>(in, n, pix0, k, free_mask, seed, out);
+  return cudaGetLastError();
+}
+
 // Weideman coefficients of this translation unit (set by invert_set_constants).
 __constant__ Weideman c_W;
 
@@ -306,7 +357,8 @@ __host__ __device__ constexpr size_t invert_smem_bytes(int tabf, int nacc, int n
   return (size_t)tabf * 4 + (size_t)nacc * nt * 4 + (size_t)kStateWords * nt * 4 + 16;
 }
 
-template <int NF, int BS>
+// RS: randomised restarts compiled in (A.restarts != 0).
+template <int NF, int BS, bool RS>
 __global__ void __launch_bounds__(BS, 1) invert_kernel(InvertArgs A) {
   constexpr int NOBS = 4 * NF;
   constexpr int NACC = kRows * 4 * NF;
@@ -331,10 +383,20 @@ __global__ void __launch_bounds__(BS, 1) invert_kernel(InvertArgs A) {
   const int dof = NOBS - A.nfree;
   const int64_t npix = A.npix_dev ? *A.npix_dev : A.npix;
 #define ST(arr, j) arr[(j) * nt + tid]
+  // restart state of this slot: best chi2, initial chi2; best J^T W J, J^T W r,
+  // model; failed trials in a row, restart count, flags
+  const RestartState R0(A.rs_state, ns);
+  double* rsBest = R0.chi2 + slot;
+  double* rsFirst = R0.chi2 + ns + slot;
+  float* rsF = R0.f + slot;  // row j at rsF[j * ns]; model from row kScratchPerSlot
+  int* rsFail = R0.i + slot;
+  int* rsCount = R0.i + ns + slot;
+  int* rsFlags = R0.i + 2 * ns + slot;
+  constexpr int kEverConv = 1, kEverStall = 2, kPending = 4;
 
   sPix[tid] = -1;
   while (true) {
-    bool fresh = false;
+    bool fresh = false, restart = false;
     {
       long long pix = sPix[tid];
       if (pix < 0) {
@@ -385,6 +447,22 @@ __global__ void __launch_bounds__(BS, 1) invert_kernel(InvertArgs A) {
         for (int j = 0; j < 10; ++j) ST(sMt, j) = Mt[j];
         sIt[tid] = 0;
         sEps[tid] = A.eps0;
+        if (RS) {
+          *rsBest = INFINITY;
+          *rsFail = 0;
+          *rsCount = 0;
+          *rsFlags = 0;
+        }
+      } else if (RS && (*rsFlags & kPending)) {
+        // restart pass: the best model so far, perturbed
+        const int k = ++*rsCount;
+        float Mt[10];
+#pragma unroll
+        for (int j = 0; j < 10; ++j) Mt[j] = rsF[(kScratchPerSlot + j) * ns];
+        restart_model(Mt, pix, k, A.seed, A.free_mask);
+#pragma unroll
+        for (int j = 0; j < 10; ++j) ST(sMt, j) = Mt[j];
+        restart = true;
       } else {
         double d[kNP];
         damped_step(scr, ns, A.free_mask, sEps[tid], d);
@@ -439,6 +517,17 @@ __global__ void __launch_bounds__(BS, 1) invert_kernel(InvertArgs A) {
         retire = true;
         status = VFISV_PIX_NAN_STATE;
       }
+      if (RS) *rsFirst = c2;
+    } else if (RS && restart) {
+      // a new segment starts at the perturbed model whatever its chi2; a
+      // non-finite one leaves the restart pending (retried with k + 1)
+      ++it;
+      accept = isfinite(c2);
+      if (accept) {
+        sEps[tid] = A.eps0;
+        *rsFail = 0;
+        *rsFlags &= ~kPending;
+      }
     } else {
       ++it;
       const double chi2b = sChi[tid];
@@ -446,15 +535,37 @@ __global__ void __launch_bounds__(BS, 1) invert_kernel(InvertArgs A) {
       const double eps_used = sEps[tid];
       const double eps = eps_update(eps_used, accept);
       sEps[tid] = eps;
+      bool conv = false, stall = false;
       if (accept) {
         const double rel = (chi2b - c2) / chi2b;
-        if (rel < A.conv_rtol && eps_used <= A.conv_eps) {
+        conv = rel < A.conv_rtol && eps_used <= A.conv_eps;
+      } else {
+        stall = eps >= 1e12;
+      }
+      if (!RS) {
+        if (conv || stall) {
           retire = true;
-          status = VFISV_PIX_CONVERGED;
+          status = conv ? VFISV_PIX_CONVERGED : VFISV_PIX_STALLED;
         }
-      } else if (eps >= 1e12) {
-        retire = true;
-        status = VFISV_PIX_STALLED;
+      } else {
+        int fl = *rsFlags;
+        const int nfail = accept ? 0 : *rsFail + 1;
+        *rsFail = nfail;
+        fl |= (conv ? kEverConv : 0) | (stall ? kEverStall : 0);
+        bool trig = false;
+        if (conv || stall) {
+          if (A.restarts & kRestartAtConvergence) trig = true;
+          else retire = true;
+        }
+        // (a) at iteration 10, chi2 not down by a decade from its first value
+        // (the best chi2 so far counts, including this trial's)
+        if ((A.restarts & kRestartA) && it == 10) {
+          const double best = (accept && c2 < *rsBest) ? c2 : *rsBest;
+          trig |= !(best <= *rsFirst / 10.0);
+        }
+        if ((A.restarts & kRestartB) && nfail >= 5) trig = true;  // (b)
+        if (trig && !retire) fl |= kPending;
+        *rsFlags = fl;
       }
     }
     sIt[tid] = it;
@@ -514,15 +625,33 @@ __global__ void __launch_bounds__(BS, 1) invert_kernel(InvertArgs A) {
       for (int i = 0; i < kNPk; ++i) scr[(int64_t)i * ns] = a[i].value();
 #pragma unroll
       for (int i = 0; i < kNP; ++i) scr[(int64_t)(kNPk + i) * ns] = g[i].value();
+      if (RS && c2 < *rsBest) {
+        // a new best over all segments: keep it with its normal equations
+        *rsBest = c2;
+#pragma unroll 1
+        for (int i = 0; i < kScratchPerSlot; ++i) rsF[i * ns] = scr[(int64_t)i * ns];
+#pragma unroll
+        for (int j = 0; j < 10; ++j) rsF[(kScratchPerSlot + j) * ns] = ST(sM, j);
+      }
     }
     if (!retire && it >= A.max_iter) retire = true;  // status stays MAXITER
 
     if (retire) {
       double chi2b = sChi[tid];
+      // with restarts the result is the best model of all segments
+      const float* src = scr;
       if (status == VFISV_PIX_NAN_STATE) {
 #pragma unroll
         for (int j = 0; j < 10; ++j) ST(sM, j) = ST(sMt, j);
         chi2b = c2;
+      } else if (RS) {
+        const int fl = *rsFlags;
+        status = (fl & kEverConv) ? VFISV_PIX_CONVERGED
+                                  : ((fl & kEverStall) ? VFISV_PIX_STALLED : VFISV_PIX_MAXITER);
+        chi2b = *rsBest;
+#pragma unroll
+        for (int j = 0; j < 10; ++j) ST(sM, j) = rsF[(kScratchPerSlot + j) * ns];
+        src = rsF;
       }
       for (int j = 0; j < 10; ++j) A.params_out[pix * 10 + j] = ST(sM, j);
       A.chi2_out[pix] = (float)chi2b;
@@ -536,7 +665,7 @@ __global__ void __launch_bounds__(BS, 1) invert_kernel(InvertArgs A) {
         if (status == VFISV_PIX_NAN_STATE) {
           for (int j = 0; j < 100; ++j) cv[j] = 0.0f;
         } else {
-          for (int j = 0; j < kNPk; ++j) cv[j] = scr[(int64_t)j * ns];
+          for (int j = 0; j < kNPk; ++j) cv[j] = src[(int64_t)j * ns];
         }
       }
       sPix[tid] = -1;
@@ -602,9 +731,9 @@ cudaError_t launch_covariance(float* cov, const int32_t* status, int64_t npix,
   return cudaGetLastError();
 }
 
-template <int BS>
+template <int BS, bool RS>
 static cudaError_t slots_for(int nlam, int64_t npix, int64_t* nslots, int* grid, size_t* smem) {
-  auto kern = invert_kernel<6, BS>;
+  auto kern = invert_kernel<6, BS, RS>;
   const size_t sm = invert_smem_bytes(table_floats(6, nlam), kRows * 4 * 6, BS);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
@@ -624,15 +753,19 @@ static cudaError_t slots_for(int nlam, int64_t npix, int64_t* nslots, int* grid,
   return cudaSuccess;
 }
 
-cudaError_t invert_slots(int nf, int nlam, int64_t npix, int64_t* nslots, int* grid,
-                         int* block, size_t* smem) {
+cudaError_t invert_slots(int nf, int nlam, int64_t npix, int restarts, int64_t* nslots,
+                         int* grid, int* block, size_t* smem) {
   if (nf != 6) return cudaErrorInvalidValue;
+  if (restarts) {  // compiled for the default slot count only
+    *block = kInvThreadsDefault;
+    return slots_for<kInvThreadsDefault, true>(nlam, npix, nslots, grid, smem);
+  }
   const int bs = (*block == 64 || *block == 256) ? *block : kInvThreadsDefault;
   *block = bs;
   switch (bs) {
-    case 64: return slots_for<64>(nlam, npix, nslots, grid, smem);
-    case 256: return slots_for<256>(nlam, npix, nslots, grid, smem);
-    default: return slots_for<128>(nlam, npix, nslots, grid, smem);
+    case 64: return slots_for<64, false>(nlam, npix, nslots, grid, smem);
+    case 256: return slots_for<256, false>(nlam, npix, nslots, grid, smem);
+    default: return slots_for<128, false>(nlam, npix, nslots, grid, smem);
   }
 }
 
@@ -643,10 +776,15 @@ cudaError_t invert_set_constants(const Weideman& W) {
 cudaError_t launch_invert(const InvertArgs& a, int nf, int grid, int block, size_t smem,
                           cudaStream_t s) {
   if (nf != 6) return cudaErrorInvalidValue;
+  if (a.restarts) {
+    if (block != kInvThreadsDefault || !a.rs_state) return cudaErrorInvalidValue;
+    invert_kernel<6, kInvThreadsDefault, true><<<grid, block, smem, s>>>(a);
+    return cudaGetLastError();
+  }
   switch (block) {
-    case 64: invert_kernel<6, 64><<<grid, 64, smem, s>>>(a); break;
-    case 256: invert_kernel<6, 256><<<grid, 256, smem, s>>>(a); break;
-    case 128: invert_kernel<6, 128><<<grid, 128, smem, s>>>(a); break;
+    case 64: invert_kernel<6, 64, false><<<grid, 64, smem, s>>>(a); break;
+    case 256: invert_kernel<6, 256, false><<<grid, 256, smem, s>>>(a); break;
+    case 128: invert_kernel<6, 128, false><<<grid, 128, smem, s>>>(a); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

@@ -91,6 +91,7 @@ extern "C" int vfisv_invert_noalloc(const float* obs, const float* weights,
   if (npix < 0 || nfilt < 1 || nlam < 1) return VFISV_E_SIZE;
   if (nlam > kMaxNlam) return VFISV_E_SIZE;  // the fixed table holds 4096 wavelengths
   if (nfilt != 6) return VFISV_E_UNSUPPORTED;
+  if (cfg->restarts != 0) return VFISV_E_UNSUPPORTED;  // restart state is not in the fixed array
   if (cfg->max_iter < 0 || (cfg->free_mask & ~0x1FFu) || !(cfg->conv_rtol >= 0) ||
       !(cfg->conv_eps >= 0) || !(cfg->eps0 > 0) || !isfinite(cfg->eps0) ||
       4 * nfilt - __builtin_popcount(cfg->free_mask) <= 0)
@@ -106,7 +107,7 @@ extern "C" int vfisv_invert_noalloc(const float* obs, const float* weights,
   int64_t nslots = 0;
   int grid = 0, block = 128;
   size_t smem = 0;
-  if (invert_slots(nfilt, nlam, npix, &nslots, &grid, &block, &smem) != cudaSuccess) {
+  if (invert_slots(nfilt, nlam, npix, 0, &nslots, &grid, &block, &smem) != cudaSuccess) {
     cudaGetLastError();
     return VFISV_E_CUDA;
   }
