@@ -120,7 +120,12 @@ typedef struct {
  *              The pixel number of the perturbations is the pixel's index in
  *              the call.  max_iter must stay below 2^20 with restarts.
  *   seed       key of the perturbations.
- * vfisv_config_default() fills: 50, 0x1FF, 1e-4, 1.0, 1.0, 0, 0. */
+ *   hess_reuse Hessian reuse near the minimum (Sec. 4.4), 0 = off: when an
+ *              accepted step lowered chi2 by less than hess_reuse relative,
+ *              and so did the previous accepted step, J^T W J is kept from
+ *              the previous model and only J^T W r is rebuilt; the
+ *              covariance comes from the matrix in use.
+ * vfisv_config_default() fills: 50, 0x1FF, 1e-4, 1.0, 1.0, 0, 0, 0.0. */
 typedef struct {
   int32_t max_iter;
   uint32_t free_mask;
@@ -129,6 +134,7 @@ typedef struct {
   double eps0;
   int32_t restarts;
   uint64_t seed;
+  double hess_reuse;
 } vfisv_config;
 
 typedef struct vfisv_handle vfisv_handle;

@@ -41,6 +41,14 @@ Readings of points the paper leaves open or prints garbled:
 * Covariance: (J^T W J)^+ at the final model (eps = 0), computed in the
   Jacobi-scaled form with the same SVD truncation, zero for held
   parameters.
+* Hessian reuse near the minimum (Sec. 4.4, Fig. 6, optional): the paper
+  skips the Hessian when "chi2 << 1", a level the Eq. 1 normalisation never
+  reaches (chi2 ~ 1 at the fit).  Read here as: an accepted step is close to
+  the minimum when it lowered chi2 by less than ``hess_reuse`` relative;
+  when it and the previous accepted step both are, J^T W J is kept from the
+  previous model and only J^T W r is rebuilt (the derivatives are still
+  computed, Fig. 6).  The covariance then comes from the matrix in use.
+  0 disables it.  A restart clears the "previous step close" state.
 * Randomised restarts (Sec. 4.2, optional, ``restarts`` a bit mask): every
   pixel runs exactly ``max_iter`` iterations.  A restart is due (bit 0)
   when a step meets the convergence test or the pixel stalls, (bit 1, the
@@ -211,7 +219,7 @@ def restart_model(m, pix, k, seed, free):
 
 def invert(obs, w, filters, x, line, init=None, max_iter=50, conv_rtol=1e-4,
            conv_eps=1.0, eps0=1.0, free_mask=DEFAULT_FREE, restarts=0, seed=0,
-           trace=False):
+           hess_reuse=0.0, trace=False):
     """Invert observed Stokes [npix, 4*nfilt] with weights w^2/sigma^2.
 
     Returns a dict with params [npix,10], chi2 [npix], iters [npix],
@@ -257,6 +265,7 @@ def invert(obs, w, filters, x, line, init=None, max_iter=50, conv_rtol=1e-4,
     status[nan0] = NAN_STATE
     done = bad | nan0
     hist = []
+    near_prev = np.zeros(npix, dtype=bool)   # previous accepted step close to the minimum
     if restarts:
         best_m, best_c2, best_A, best_g = m.copy(), c2.copy(), A.copy(), g.copy()
         c2_first = c2.copy()
@@ -287,6 +296,7 @@ def invert(obs, w, filters, x, line, init=None, max_iter=50, conv_rtol=1e-4,
                 Ar, gr = normal_equations(Jr[fin], obs_s[ok_r] - sr[fin], w_s[ok_r], free)
                 A[ok_r], g[ok_r] = Ar, gr
                 nfail[ok_r] = 0
+                near_prev[ok_r] = False
                 eps[ok_r] = float(eps0)
                 pending[ok_r] = False        # a non-finite restart is retried with k + 1
         delta = damped_step(A[act], g[act], eps[act], free)
@@ -306,7 +316,11 @@ def invert(obs, w, filters, x, line, init=None, max_iter=50, conv_rtol=1e-4,
             nacc[acc] += 1
             sa, Ja = model(m[acc], True)
             Aa, ga = normal_equations(Ja, obs_s[acc] - sa, w_s[acc], free)
-            A[acc], g[acc] = Aa, ga
+            near = rel < hess_reuse
+            keep = near & near_prev[acc]          # reuse J^T W J of the previous model
+            A[acc[~keep]] = Aa[~keep]
+            g[acc] = ga
+            near_prev[acc] = near
             conv = (rel < conv_rtol) & (eps_used[ok] <= conv_eps)
             conv_now = acc[conv]
         rej = act[~ok]

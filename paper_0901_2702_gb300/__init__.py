@@ -51,7 +51,7 @@ class vfisv_config(ctypes.Structure):
     _fields_ = [("max_iter", ctypes.c_int32), ("free_mask", ctypes.c_uint32),
                 ("conv_rtol", ctypes.c_double), ("conv_eps", ctypes.c_double),
                 ("eps0", ctypes.c_double), ("restarts", ctypes.c_int32),
-                ("seed", ctypes.c_uint64)]
+                ("seed", ctypes.c_uint64), ("hess_reuse", ctypes.c_double)]
 
 
 def library_path() -> str:

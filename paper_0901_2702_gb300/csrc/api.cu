@@ -198,6 +198,7 @@ int check_config(const vfisv_config* cfg, int nfilt) {
     return VFISV_E_ARG;
   // restart counters are 20 bits wide (each restart costs an iteration)
   if ((cfg->restarts & ~7) || (cfg->restarts && cfg->max_iter >= (1 << 20))) return VFISV_E_ARG;
+  if (!(cfg->hess_reuse >= 0) || !isfinite(cfg->hess_reuse)) return VFISV_E_ARG;
   if (4 * nfilt - __builtin_popcount(cfg->free_mask) <= 0) return VFISV_E_ARG;
   return VFISV_OK;
 }
@@ -276,6 +277,7 @@ int invert_device(vfisv_handle* h, const DevInvert& d, int nfilt, int nlam,
   a.eps0 = cfg->eps0;
   a.restarts = cfg->restarts;
   a.seed = cfg->seed;
+  a.hess_reuse = cfg->hess_reuse;
   a.rs_state = cfg->restarts ? ws + L.rs : nullptr;
   if (launch_invert(a, nfilt, grid, block, smem, s) != cudaSuccess) return VFISV_E_CUDA;
   if (d.cov && launch_covariance(d.cov, d.status, npix, npix_dev, cfg->free_mask, s) !=
@@ -313,6 +315,7 @@ void vfisv_config_default(vfisv_config* c) {
   c->eps0 = 1.0;
   c->restarts = 0;
   c->seed = 0;
+  c->hess_reuse = 0.0;
 }
 
 int vfisv_create(vfisv_handle** out, int device) {

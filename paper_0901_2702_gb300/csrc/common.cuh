@@ -134,6 +134,7 @@ struct InvertArgs {
   double conv_rtol;
   double conv_eps;
   double eps0;
+  double hess_reuse = 0.0;   // Hessian reuse threshold (Sec. 4.4), 0 = off
   int restarts = 0;          // randomised restarts (Sec. 4.2): trigger bit mask, 0 = off
   uint64_t seed = 0;         // key of the restart perturbations
   char* rs_state = nullptr;  // restarts: per-slot state, layout RestartState

@@ -352,7 +352,7 @@ __device__ __noinline__ void fused_pass(const PixK P, const float* __restrict__ 
 // Per-slot LM state kept in shared memory (structure of arrays, one column
 // per thread) so that the registers of the wavelength loop hold only its
 // accumulators.
-constexpr int kStateWords = 10 + 10 + 2 + 2 + 2 + 1;  // M, Mt, chi2b, eps, pix, it
+constexpr int kStateWords = 10 + 10 + 2 + 2 + 2 + 1 + 1;  // M, Mt, chi2b, eps, pix, it, near
 __host__ __device__ constexpr size_t invert_smem_bytes(int tabf, int nacc, int nt) {
   return (size_t)tabf * 4 + (size_t)nacc * nt * 4 + (size_t)kStateWords * nt * 4 + 16;
 }
@@ -374,6 +374,7 @@ __global__ void __launch_bounds__(BS, 1) invert_kernel(InvertArgs A) {
   double* sEps = sChi + nt;                       // [nt]
   long long* sPix = reinterpret_cast<long long*>(sEps + nt);  // [nt]
   int* sIt = reinterpret_cast<int*>(sPix + nt);   // [nt]
+  int* sNear = sIt + nt;  // [nt] last accepted step was close to the minimum (Hessian reuse)
   uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + (invert_smem_bytes(tabf, NACC, nt) - 16) / 4);
   if (!tma_load_table(tab, A.table, (uint32_t)(tabf * sizeof(float)), mbar, A.err)) return;
   const float* tau = tab + (size_t)A.nlam * S;
@@ -447,6 +448,7 @@ __global__ void __launch_bounds__(BS, 1) invert_kernel(InvertArgs A) {
         for (int j = 0; j < 10; ++j) ST(sMt, j) = Mt[j];
         sIt[tid] = 0;
         sEps[tid] = A.eps0;
+        sNear[tid] = 0;
         if (RS) {
           *rsBest = INFINITY;
           *rsFail = 0;
@@ -511,6 +513,7 @@ __global__ void __launch_bounds__(BS, 1) invert_kernel(InvertArgs A) {
     bool accept, retire = false;
     int status = VFISV_PIX_MAXITER;
     int it = sIt[tid];
+    double rel_acc = INFINITY;  // relative chi2 decrease of an accepted trial step
     if (fresh) {
       accept = isfinite(c2);
       if (!accept) {
@@ -538,6 +541,7 @@ __global__ void __launch_bounds__(BS, 1) invert_kernel(InvertArgs A) {
       bool conv = false, stall = false;
       if (accept) {
         const double rel = (chi2b - c2) / chi2b;
+        rel_acc = rel;
         conv = rel < A.conv_rtol && eps_used <= A.conv_eps;
       } else {
         stall = eps >= 1e12;
@@ -583,6 +587,11 @@ __global__ void __launch_bounds__(BS, 1) invert_kernel(InvertArgs A) {
       constexpr int rowOf[kNP] = {kRowB, kRowG, -1, kRowE, kRowD, kRowA, kRowV, -1, -1};
       const float mu = A.lk.mu;
       const RowScale R = row_scale(A.lk, ST(sMt, 3), ST(sMt, 4));
+      // Hessian reuse (Sec. 4.4): this and the previous accepted step both
+      // close to the minimum -> keep J^T W J, rebuild J^T W r only
+      const bool near = rel_acc < A.hess_reuse;
+      const bool keepA = near && sNear[tid];
+      sNear[tid] = near;
       // Runtime loops over (filter, Stokes) keep this block small: it runs
       // on accepted steps only and must not evict the wavelength loop from
       // the instruction cache.  Observable (s, k) of row r is
@@ -616,13 +625,17 @@ __global__ void __launch_bounds__(BS, 1) invert_kernel(InvertArgs A) {
           for (int p = 0; p < kNP; ++p) {
             const float wj = ww * J[p];
             g[p].add(wj, rr);
+            if (!keepA) {
 #pragma unroll
-            for (int q = 0; q <= p; ++q) a[tri(p, q)].add(wj, J[q]);
+              for (int q = 0; q <= p; ++q) a[tri(p, q)].add(wj, J[q]);
+            }
           }
         }
       }
+      if (!keepA) {
 #pragma unroll
-      for (int i = 0; i < kNPk; ++i) scr[(int64_t)i * ns] = a[i].value();
+        for (int i = 0; i < kNPk; ++i) scr[(int64_t)i * ns] = a[i].value();
+      }
 #pragma unroll
       for (int i = 0; i < kNP; ++i) scr[(int64_t)(kNPk + i) * ns] = g[i].value();
       if (RS && c2 < *rsBest) {

@@ -92,6 +92,7 @@ extern "C" int vfisv_invert_noalloc(const float* obs, const float* weights,
   if (nlam > kMaxNlam) return VFISV_E_SIZE;  // the fixed table holds 4096 wavelengths
   if (nfilt != 6) return VFISV_E_UNSUPPORTED;
   if (cfg->restarts != 0) return VFISV_E_UNSUPPORTED;  // restart state is not in the fixed array
+  if (!(cfg->hess_reuse >= 0) || !isfinite(cfg->hess_reuse)) return VFISV_E_ARG;
   if (cfg->max_iter < 0 || (cfg->free_mask & ~0x1FFu) || !(cfg->conv_rtol >= 0) ||
       !(cfg->conv_eps >= 0) || !(cfg->eps0 > 0) || !isfinite(cfg->eps0) ||
       4 * nfilt - __builtin_popcount(cfg->free_mask) <= 0)
@@ -150,6 +151,7 @@ extern "C" int vfisv_invert_noalloc(const float* obs, const float* weights,
   a.conv_rtol = cfg->conv_rtol;
   a.conv_eps = cfg->conv_eps;
   a.eps0 = cfg->eps0;
+  a.hess_reuse = cfg->hess_reuse;
   if (launch_invert(a, nfilt, grid, block, smem, s) != cudaSuccess) return VFISV_E_CUDA;
   if (cov_out &&
       launch_covariance(cov_out, status_out, npix, nullptr, cfg->free_mask, s) != cudaSuccess)

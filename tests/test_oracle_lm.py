@@ -173,3 +173,21 @@ def test_eq14_weights():
     np.testing.assert_allclose(w[:, 6:], 1e6, rtol=1e-12)
     # quiet Sun (continuum ~ I_cont(mu)) gets w_I ~ 0.3, a dark umbra ~ 1
     assert abs(np.sqrt(w[0, 0] * 1e-6) - 0.3) < 1e-3 and np.sqrt(w[2, 0] * 1e-6) > 0.9
+
+
+def test_hessian_reuse_off_and_on():
+    """hess_reuse = 0 is the plain iteration bit for bit; with reuse the
+    iteration still reaches the same minimum (the fixed point of the step
+    does not depend on the matrix), and the gradient is exactly the one at
+    the final model."""
+    p, s, o, w = _obs(48, 29)
+    a = lm.invert(o, w, T, X, LINE, max_iter=60)
+    b = lm.invert(o, w, T, X, LINE, max_iter=60, hess_reuse=0.0)
+    assert np.array_equal(a["params"], b["params"]) and np.array_equal(a["chi2"], b["chi2"])
+    c = lm.invert(o, w, T, X, LINE, init=p, max_iter=200, conv_rtol=1e-9)
+    d = lm.invert(o, w, T, X, LINE, init=p, max_iter=200, conv_rtol=1e-9, hess_reuse=1e-2)
+    both = (c["status"] == lm.CONVERGED) & (d["status"] == lm.CONVERGED)
+    assert both.mean() > 0.8
+    # with a stale matrix the last steps converge linearly, not quadratically,
+    # so the stopping test (1e-9 per step) can end a few steps apart
+    np.testing.assert_allclose(d["chi2"][both], c["chi2"][both], rtol=1e-5)
