@@ -63,10 +63,12 @@ FLOP_PER_LAMBDA = 4 + 3 * 135 + 16 + 32 + 48 + 28 + 14 + 4 + 6 + 63 + 4 * 132
 FLOP_PER_PASS_EXTRA = 60  # model and residual outside the wavelength loop
 # DRAM bytes (read + write) of one plain-LM launch without covariance, per
 # pixel, from one ncu capture of invert_kernel on 262,144 pixels of the
-# 1024^2 distributions (54.8 MB read + 147.0 MB write; profiles/
+# 1024^2 distributions (51.5 MB read + 3.6 MB write; profiles/
 # invert_kernel_traffic.md); scaled by the pixels of a launch.  Algorithmic:
-# 192 B read (observables, weights) + 52 B written (model, chi2, counts).
-TRAFFIC_BYTES_PER_PIXEL = 201_875_968 / 262_144
+# 192 B read (observables, weights) + 52 B written (model, chi2, counts);
+# at that size most of the written outputs are still in L2 when the kernel
+# ends, so the scaled figure can undercount writes by up to 52 B/pixel.
+TRAFFIC_BYTES_PER_PIXEL = (51_455_232 + 3_640_576) / 262_144
 
 
 def fp32_peak_tflops(sm_mhz: float, nsm: int = 152) -> float:
@@ -298,7 +300,7 @@ def run_ours(args, rank, world):
         "metric": METRIC, "value": value, "unit": "pixels/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_mixed,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32 synthesis/Jacobian, f64 solve/chi2, bf16 network",
+        "dtype": "f32 synthesis/Jacobian, double-float (f32 pairs) solve, compensated f32 chi2, bf16 network",
         "data": "synthetic (seeded ME parameters, library-synthesised Stokes + Gaussian noise)",
         "config": {"workload": f"NN-initialised mixed inversion of the {wl}: Fe I 6173 A, "
                                f"6 filters x 149 wavelengths, network guess + LM cap {NN_CAP}, "
@@ -330,8 +332,9 @@ def run_ours(args, rank, world):
                      "frac": achieved / peak,
                      "traffic": int(TRAFFIC_BYTES_PER_PIXEL * npix),
                      "traffic_note": "dram read+write bytes per launch, scaled by pixels from a "
-                                     "262,144-pixel ncu capture (770 B/px; algorithmic 244 B/px, "
-                                     "the rest is register-spill/call-stack write-back)",
+                                     "262,144-pixel ncu capture (210 B/px; algorithmic 244 B/px: "
+                                     "reads 196 vs 192, the outputs of that launch mostly still in "
+                                     "L2 at its end)",
                      "kernel": "invert_kernel<6> (plain LM pass, no covariance)",
                      "kernel_ms": ms_lm,
                      "note": "peak = FP32 pipe, 152 SM x 128 lanes x 2 flop x 2070 MHz (no "

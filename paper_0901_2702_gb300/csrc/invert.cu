@@ -11,6 +11,7 @@
 #include <math.h>
 
 #include "common.cuh"
+#include "dfloat.cuh"
 
 namespace vfisv {
 
@@ -208,60 +209,152 @@ __device__ __forceinline__ void scaled_system(const float* scr, int64_t ns, uint
     }
 }
 
-// Eq. 5 with the Marquardt diagonal (Eq. 4): delta = (A + eps diag A)^-1 g.
-__device__ __noinline__ void damped_step(const float* scr, int64_t ns, uint32_t free_mask, double eps,
-                            double (&delta)[kNP]) {
-  double L[kNPk], sc[kNP];
-  bool held[kNP];
-  scaled_system(scr, ns, free_mask, eps, L, sc, held);
-  double y[kNP];
+// The same factorisation and solve in double-float arithmetic (the fast
+// path of the damped step; FP64 is kept for the rare singular fallback).
+__device__ __forceinline__ bool cholesky9_df(dfl (&L)[kNPk], dfl (&ri)[kNP]) {
 #pragma unroll
-  for (int i = 0; i < kNP; ++i)
-    y[i] = held[i] ? 0.0 : (double)scr[(int64_t)(kNPk + i) * ns] * sc[i];
-  double ri[kNP];
-  if (cholesky9(L, ri)) {
-    chol_solve9(L, ri, y);
-  } else {
-    // rebuild the scaled matrix (the factorisation overwrote it)
-    scaled_system(scr, ns, free_mask, eps, L, sc, held);
-    double b[kNP];
+  for (int j = 0; j < kNP; ++j) {
+    dfl d = L[tri(j, j)];
 #pragma unroll
-    for (int i = 0; i < kNP; ++i) b[i] = y[i];
-    jacobi_pinv(L, b, y, nullptr);
+    for (int k = 0; k < j; ++k) d = df_fma(df_neg(L[tri(j, k)]), L[tri(j, k)], d);
+    if (!(d.hi > 1e-10f)) return false;
+    const dfl r = df_rsqrt(d);
+    ri[j] = r;
+    L[tri(j, j)] = df_mul(d, r);
+#pragma unroll
+    for (int i = j + 1; i < kNP; ++i) {
+      dfl t = L[tri(i, j)];
+#pragma unroll
+      for (int k = 0; k < j; ++k) t = df_fma(df_neg(L[tri(i, k)]), L[tri(j, k)], t);
+      L[tri(i, j)] = df_mul(t, r);
+    }
+  }
+  return true;
+}
+
+__device__ __forceinline__ void chol_solve9_df(const dfl (&L)[kNPk], const dfl (&ri)[kNP],
+                                               dfl (&x)[kNP]) {
+#pragma unroll
+  for (int i = 0; i < kNP; ++i) {
+    dfl t = x[i];
+#pragma unroll
+    for (int k = 0; k < i; ++k) t = df_fma(df_neg(L[tri(i, k)]), x[k], t);
+    x[i] = df_mul(t, ri[i]);
   }
 #pragma unroll
-  for (int i = 0; i < kNP; ++i) delta[i] = held[i] ? 0.0 : sc[i] * y[i];
+  for (int i = kNP - 1; i >= 0; --i) {
+    dfl t = x[i];
+#pragma unroll
+    for (int k = i + 1; k < kNP; ++k) t = df_fma(df_neg(L[tri(k, i)]), x[k], t);
+    x[i] = df_mul(t, ri[i]);
+  }
+}
+
+// Eq. 5 with the Marquardt diagonal (Eq. 4): delta = (A + eps diag A)^-1 g,
+// Jacobi-scaled, in double-float; the result is delta[i].hi + delta[i].lo.
+__device__ __noinline__ void damped_step(const float* scr, int64_t ns, uint32_t free_mask, double eps,
+                                         dfl (&delta)[kNP]) {
+  dfl L[kNPk], sc[kNP], y[kNP];
+  bool held[kNP];
+  const dfl one_eps = df_add(df_from(1.0f), df_from_double(eps));
+#pragma unroll
+  for (int i = 0; i < kNP; ++i) {
+    const float d = scr[(int64_t)tri(i, i) * ns];
+    held[i] = !((free_mask >> i) & 1u) || !(d > 0.0f) || !isfinite(d);
+    sc[i] = held[i] ? df_from(0.0f) : df_rsqrt(df_from(d));
+    y[i] = held[i] ? df_from(0.0f) : df_mul(df_from(scr[(int64_t)(kNPk + i) * ns]), sc[i]);
+  }
+#pragma unroll
+  for (int i = 0; i < kNP; ++i)
+#pragma unroll
+    for (int j = 0; j <= i; ++j) {
+      dfl m;
+      if (i == j)
+        m = held[i] ? df_from(1.0f) : one_eps;
+      else
+        m = (held[i] || held[j])
+                ? df_from(0.0f)
+                : df_mul(df_mul(df_from(scr[(int64_t)tri(i, j) * ns]), sc[i]), sc[j]);
+      L[tri(i, j)] = m;
+    }
+  dfl ri[kNP];
+  if (!cholesky9_df(L, ri)) {
+    // numerically singular: truncated eigen-decomposition in FP64
+    double Ld[kNPk], scd[kNP], b[kNP], yd[kNP];
+    bool h2[kNP];
+    scaled_system(scr, ns, free_mask, eps, Ld, scd, h2);
+#pragma unroll
+    for (int i = 0; i < kNP; ++i) b[i] = df_to_double(y[i]);
+    jacobi_pinv(Ld, b, yd, nullptr);
+#pragma unroll
+    for (int i = 0; i < kNP; ++i) y[i] = df_from_double(yd[i]);
+  } else {
+    chol_solve9_df(L, ri, y);
+  }
+#pragma unroll
+  for (int i = 0; i < kNP; ++i) delta[i] = held[i] ? df_from(0.0f) : df_mul(sc[i], y[i]);
 }
 
 // Covariance (J^T W J)^+ at the final model, in parameter units, from the
 // packed J^T W J at scr[e * ns].  Reads everything before writing `out`, so
-// `out` may hold the packed matrix itself.  With try_only, returns false
-// without writing when the Cholesky factorisation fails (the caller then
-// runs the eigen-decomposition path for that pixel).
+// `out` may hold the packed matrix itself.  The Cholesky path runs in
+// double-float; with try_only, returns false without writing when the
+// factorisation fails (the caller then runs the FP64 eigen-decomposition
+// path for that pixel).
 __device__ __noinline__ bool covariance(const float* scr, int64_t ns, uint32_t free_mask,
                                         float* out, bool try_only) {
-  double L[kNPk], sc[kNP];
-  bool held[kNP];
-  scaled_system(scr, ns, free_mask, 0.0, L, sc, held);
-  double P[kNPk], ri[kNP];
-  if (cholesky9(L, ri)) {
-    for (int j = 0; j < kNP; ++j) {
-      double x[kNP];
+  uint32_t hmask = 0;
+  dfl sc[kNP];
 #pragma unroll
-      for (int i = 0; i < kNP; ++i) x[i] = (i == j) ? 1.0 : 0.0;
-      chol_solve9(L, ri, x);
-      for (int i = j; i < kNP; ++i) P[tri(i, j)] = x[i];
-    }
-  } else {
-    if (try_only) return false;
-    scaled_system(scr, ns, free_mask, 0.0, L, sc, held);
-    jacobi_pinv(L, nullptr, nullptr, P);
+  for (int i = 0; i < kNP; ++i) {
+    const float d = scr[(int64_t)tri(i, i) * ns];
+    const bool h = !((free_mask >> i) & 1u) || !(d > 0.0f) || !isfinite(d);
+    hmask |= (h ? 1u : 0u) << i;
+    sc[i] = h ? df_from(0.0f) : df_rsqrt(df_from(d));
   }
+  dfl L[kNPk], ri[kNP];
+#pragma unroll
+  for (int i = 0; i < kNP; ++i)
+#pragma unroll
+    for (int j = 0; j <= i; ++j)
+      L[tri(i, j)] = (i == j) ? df_from(1.0f)
+                     : (((hmask >> i) | (hmask >> j)) & 1u)
+                         ? df_from(0.0f)
+                         : df_mul(df_mul(df_from(scr[(int64_t)tri(i, j) * ns]), sc[i]), sc[j]);
+  if (cholesky9_df(L, ri)) {
+    // scr is no longer read: column j of S M^-1 S, S = diag(sc), straight to out
+#pragma unroll 1
+    for (int j = 0; j < kNP; ++j) {
+      dfl x[kNP];
+#pragma unroll
+      for (int i = 0; i < kNP; ++i) x[i] = (i == j) ? sc[i] : df_from(0.0f);
+      chol_solve9_df(L, ri, x);
+      const bool hj = (hmask >> j) & 1u;
+#pragma unroll
+      for (int i = 0; i < kNP; ++i) {
+        if (i < j) continue;
+        const float v = (hj || ((hmask >> i) & 1u)) ? 0.0f : df_mul(x[i], sc[i]).hi;
+        out[i * 10 + j] = v;
+        out[j * 10 + i] = v;
+      }
+    }
+    for (int k = 0; k < 10; ++k) {
+      out[90 + k] = 0.0f;
+      out[k * 10 + 9] = 0.0f;
+    }
+    return true;
+  }
+  if (try_only) return false;
+  // numerically singular: truncated eigen-decomposition in FP64
+  double Ld[kNPk], scd[kNP], Pd[kNPk];
+  bool held[kNP];
+  scaled_system(scr, ns, free_mask, 0.0, Ld, scd, held);
+  jacobi_pinv(Ld, nullptr, nullptr, Pd);
   for (int i = 0; i < 10; ++i)
     for (int j = 0; j < 10; ++j) {
       float v = 0.0f;
       if (i < kNP && j < kNP && !held[i] && !held[j])
-        v = (float)(sc[i] * sc[j] * ((i >= j) ? P[tri(i, j)] : P[tri(j, i)]));
+        v = (float)(scd[i] * scd[j] * ((i >= j) ? Pd[tri(i, j)] : Pd[tri(j, i)]));
       out[i * 10 + j] = v;
     }
   return true;
@@ -466,11 +559,14 @@ __global__ void __launch_bounds__(BS, 1) invert_kernel(InvertArgs A) {
         for (int j = 0; j < 10; ++j) ST(sMt, j) = Mt[j];
         restart = true;
       } else {
-        double d[kNP];
+        dfl d[kNP];
         damped_step(scr, ns, A.free_mask, sEps[tid], d);
         float Mt[10];
 #pragma unroll
-        for (int j = 0; j < kNP; ++j) Mt[j] = (float)((double)ST(sM, j) + d[j]);
+        for (int j = 0; j < kNP; ++j) {
+          const dfl t = two_sum(ST(sM, j), d[j].hi);
+          Mt[j] = t.hi + (t.lo + d[j].lo);  // the FP32 model nearest M + delta
+        }
         Mt[9] = 1.0f;
         apply_bounds(Mt);
 #pragma unroll
@@ -502,13 +598,15 @@ __global__ void __launch_bounds__(BS, 1) invert_kernel(InvertArgs A) {
       syn[2 * NF + k] = mus1 * fmaf(s2p, q0, c2p * u0);
       syn[3 * NF + k] = mus1 * D(0, 3, k);
     }
-    double c2 = 0.0;
+    // compensated FP32 sum of w r^2 (the residuals themselves carry the FP32
+    // synthesis error, ~1e-4 of chi2, so this is as exact as the data)
+    Dot2 q{0.0f, 0.0f};
 #pragma unroll
     for (int j = 0; j < NOBS; ++j) {
-      const double r = (double)(o[j] - syn[j]);
-      c2 = fma((double)wv[j] * r, r, c2);
+      const float r = o[j] - syn[j];
+      q.add(wv[j] * r, r);
     }
-    c2 /= (double)dof;
+    const double c2 = ((double)q.s + (double)q.c) / (double)dof;
 
     bool accept, retire = false;
     int status = VFISV_PIX_MAXITER;
@@ -678,7 +776,21 @@ __global__ void __launch_bounds__(BS, 1) invert_kernel(InvertArgs A) {
         if (status == VFISV_PIX_NAN_STATE) {
           for (int j = 0; j < 100; ++j) cv[j] = 0.0f;
         } else {
-          for (int j = 0; j < kNPk; ++j) cv[j] = src[(int64_t)j * ns];
+          // all 45 loads first (one retiring lane runs this while its warp
+          // waits), then 400-byte-aligned vector stores into the row
+          float v[48];
+#pragma unroll
+          for (int j = 0; j < kNPk; ++j) v[j] = src[(int64_t)j * ns];
+          v[45] = v[46] = v[47] = 0.0f;
+          if ((reinterpret_cast<uintptr_t>(A.cov_out) & 15u) == 0) {  // rows are 400 B
+            float4* c4 = reinterpret_cast<float4*>(cv);
+#pragma unroll
+            for (int j = 0; j < 12; ++j)
+              c4[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+          } else {
+#pragma unroll
+            for (int j = 0; j < kNPk; ++j) cv[j] = v[j];
+          }
         }
       }
       sPix[tid] = -1;
