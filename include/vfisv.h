@@ -120,12 +120,21 @@ typedef struct {
  *              The pixel number of the perturbations is the pixel's index in
  *              the call.  max_iter must stay below 2^20 with restarts.
  *   seed       key of the perturbations.
+ *   wfa_pol    initialisation from the filtergrams (Sec. 6), 0 = off.
+ *              Where an inversion starts without given models (vfisv_invert
+ *              with init == NULL, the re-inversion stage of vfisv_invert_nn),
+ *              > 0 starts from the models of vfisv_init_models instead of the
+ *              standard guess.  In the first stage of vfisv_invert_nn, > 0
+ *              combines the network's guess the paper's way: B and gamma from
+ *              the weak-field estimate where the polarisation level is below
+ *              wfa_pol (the paper: 0.06), the wing azimuth everywhere, the
+ *              network's values for the rest.
  *   hess_reuse Hessian reuse near the minimum (Sec. 4.4), 0 = off: when an
  *              accepted step lowered chi2 by less than hess_reuse relative,
  *              and so did the previous accepted step, J^T W J is kept from
  *              the previous model and only J^T W r is rebuilt; the
  *              covariance comes from the matrix in use.
- * vfisv_config_default() fills: 50, 0x1FF, 1e-4, 1.0, 1.0, 0, 0, 0.0. */
+ * vfisv_config_default() fills: 50, 0x1FF, 1e-4, 1.0, 1.0, 0, 0, 0.0, 0.0. */
 typedef struct {
   int32_t max_iter;
   uint32_t free_mask;
@@ -135,6 +144,7 @@ typedef struct {
   int32_t restarts;
   uint64_t seed;
   double hess_reuse;
+  double wfa_pol;
 } vfisv_config;
 
 typedef struct vfisv_handle vfisv_handle;
@@ -157,6 +167,30 @@ const char* vfisv_strerror(int code);
  * Points outside the table use the rational series.  Arrays float32[n]. */
 int vfisv_voigt(vfisv_handle* h, const float* a, const float* u, int64_t n, int32_t method,
                 float* H, float* F, void* stream);
+
+/* Initial models from the filtergrams (Sec. 6; the paper's methods are
+ * cited, not printed -- this is one reading of them).  For each pixel of
+ * obs [npix][4][nfilt] (3 <= nfilt <= 8; filters [nfilt][nlam] on wl_mA, any
+ * order of centres):
+ *   c_k      filter centres sum T_k x / sum T_k, taken in increasing order;
+ *   B_par    least-squares fit of V_k = -C B_par dI/dlambda_k, the derivative
+ *            by differences across the centres (central inside, one-sided
+ *            at the ends), C = 4.66685e-10 g lambda0^2 mA/G (Eq. 7);
+ *   B_perp   least-squares fit of |(Q_k, U_k)| = C^2 B_perp^2 / 4 |d2I/dlambda2_k|
+ *            over the interior centres;
+ *   psi      azimuth from the line wings: 2 psi = atan2(sum w_k U_k,
+ *            sum w_k Q_k), w_k = (c_k - mean c)^4;
+ *   B = hypot(B_par, B_perp), gamma = atan2(B_perp, B_par);
+ *   v        centre of gravity of the line depth I_c - I_k over the centres;
+ *   eta0 = 10, dlambdaD = 35 mA, a = 0.25, S0 = 0.25 I_c, S1 = 0.75 I_c / mu,
+ *   alpha = 1 (I_c = largest Stokes I sample); the model bounds applied.
+ * init_out [npix][10]; pol_out (optional) [npix] = max_k |(Q,U,V)_k| / I_c,
+ * the polarisation level the paper's 6 % switch uses.  A pixel with a
+ * non-finite observable gets a NaN model and pol (the inversion then flags
+ * it BAD_INPUT).  Host or device buffers. */
+int vfisv_init_models(vfisv_handle* h, const float* obs, int64_t npix, const float* filters,
+                      int32_t nfilt, const float* wl_mA, int32_t nlam, const vfisv_line* line,
+                      float* init_out, float* pol_out, void* stream);
 
 /* The perturbation of a randomised restart (Sec. 4.2), in bulk: models_out
  * [n][10] = restart number k (1 <= k < 2^20) of pixels pixel0 .. pixel0+n-1
@@ -311,7 +345,7 @@ int vfisv_invert_nn(vfisv_handle* h, const float* blob, const float* obs, const 
  *   - All pointers must be device memory; arguments and outputs are those
  *     of vfisv_invert, on the current CUDA device, asynchronous on `stream`.
  *   - nlam <= VFISV_NOALLOC_MAX_NLAM (4096) and nfilt == 6, else
- *     VFISV_E_SIZE / VFISV_E_UNSUPPORTED; cfg->restarts must be 0.  Any npix works: at most
+ *     VFISV_E_SIZE / VFISV_E_UNSUPPORTED; cfg->restarts and cfg->wfa_pol must be 0.  Any npix works: at most
  *     VFISV_NOALLOC_MAX_SLOTS pixels are resident at once and the others
  *     queue behind them.
  *   - The first call on a device looks up the array's device address and

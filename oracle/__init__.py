@@ -20,6 +20,9 @@ Modules
          derivatives only after a successful step (Fig. 6), covariance.
 ``mlp``  the initial-guess network (24 -> 256 -> 256 -> 256 -> 11, GELU):
          forward, backward, loss and Adam in FP64.
+``init`` initial models from the filtergrams (Sec. 6): weak-field B,
+         gamma, the azimuth from Q and U, the polarisation level, and the
+         paper's combination with the network.
 
 Parity status: every function is pinned by the tests under ``tests/``
 (closed forms, brute-force quadrature, invariants, finite differences,
@@ -28,4 +31,4 @@ noise-free round trips).  The sign convention of the magneto-optical
 only for self-consistency (closed form vs 4x4 solve): parity unpinned for
 that sign beyond self-consistency, as the paper does not print the matrix.
 """
-from . import me, lm, mlp  # noqa: F401
+from . import me, lm, mlp, init  # noqa: F401

@@ -30,7 +30,9 @@ Readings of points the paper leaves open or prints garbled:
   exceeds 1e12 after a failure (no decrease possible, status STALLED);
   otherwise it stops at ``max_iter`` trial steps (status MAXITER).  The
   iteration count is the number of trial solves (the paper's Svdcmp count).
-* Standard initial guess (the paper uses ANN/weak-field guesses):
+* Without given initial models the iteration starts from the filtergram
+  models of ``oracle.init`` when ``wfa_pol`` > 0 (Sec. 6), else from the
+  standard initial guess (the paper uses ANN/weak-field guesses):
   B = 500 G, gamma = 60 deg, psi = 45 deg, eta0 = 10, dlambdaD = 35 mA,
   a = 0.25, v = 0, S0 = 0.25 Ic, S1 = 0.75 Ic / mu, alpha = 1, where Ic is the
   largest observed Stokes I sample.
@@ -219,7 +221,7 @@ def restart_model(m, pix, k, seed, free):
 
 def invert(obs, w, filters, x, line, init=None, max_iter=50, conv_rtol=1e-4,
            conv_eps=1.0, eps0=1.0, free_mask=DEFAULT_FREE, restarts=0, seed=0,
-           hess_reuse=0.0, trace=False):
+           hess_reuse=0.0, wfa_pol=0.0, trace=False):
     """Invert observed Stokes [npix, 4*nfilt] with weights w^2/sigma^2.
 
     Returns a dict with params [npix,10], chi2 [npix], iters [npix],
@@ -235,7 +237,10 @@ def invert(obs, w, filters, x, line, init=None, max_iter=50, conv_rtol=1e-4,
     nfree = int(free.sum())
 
     bad = ~np.isfinite(obs).all(1) | ~np.isfinite(w).all(1) | ~(w.sum(1) > 0)
-    if init is None:
+    if init is None and wfa_pol > 0:
+        from . import init as init_mod   # Sec. 6: models from the filtergrams
+        m = init_mod.initial_models(np.where(np.isfinite(obs), obs, 0.0), filters, x, line)
+    elif init is None:
         m = standard_guess(np.where(np.isfinite(obs), obs, 0.0), nfilt, mu)
     else:
         m = np.asarray(init, dtype=np.float64).copy()
@@ -373,25 +378,33 @@ def invert(obs, w, filters, x, line, init=None, max_iter=50, conv_rtol=1e-4,
 
 
 def invert_mixed(obs, w, filters, x, line, blob, nn_cap=20, plain_cap=50, chi2_flag=3.0,
-                 flag_unconverged=True, **kw):
+                 flag_unconverged=True, wfa_pol=0.0, plain_wfa_pol=0.0, **kw):
     """Network-initialised inversion with plain re-inversion of flagged pixels.
 
     The network (FP64 forward of ``blob``) gives the initial models; LM runs
     with ``nn_cap``; pixels ending with chi2 > chi2_flag (or, with
     flag_unconverged, not converged) are inverted again from the standard
-    guess with ``plain_cap`` and keep the lower chi2; iteration counts add."""
-    from . import mlp
+    guess with ``plain_cap`` and keep the lower chi2; iteration counts add.
+    With ``wfa_pol`` > 0 the network's guess is combined the paper's way
+    (Sec. 6): weak-field B and gamma below that polarisation level, the
+    wing azimuth everywhere (``oracle.init.merge_paper``); with
+    ``plain_wfa_pol`` > 0 the re-inversion starts from the filtergram models
+    (``oracle.init.initial_models``) instead of the standard guess."""
+    from . import init as init_mod, mlp
     mu = float(line.get("mu", 1.0))
     weights, stats = mlp.unpack(blob)
     y, _ = mlp.forward(weights, mlp.features(obs, stats))
     init = mlp.decode(y, obs, stats, mu)
+    if wfa_pol > 0:
+        init = init_mod.merge_paper(init, obs, filters, x, line, wfa_pol)
     r = invert(obs, w, filters, x, line, init=init, max_iter=nn_cap, **kw)
     conv = np.isin(r["status"], (CONVERGED, STALLED))
     flag = (r["status"] != BAD_INPUT) & ((flag_unconverged & ~conv) | ~(r["chi2"] <= chi2_flag))
     out = {k: np.array(v, copy=True) for k, v in r.items()}
     out["flagged"] = flag.astype(np.int32)
     if flag.any():
-        q = invert(obs[flag], w[flag], filters, x, line, init=None, max_iter=plain_cap, **kw)
+        q = invert(obs[flag], w[flag], filters, x, line, init=None, max_iter=plain_cap,
+                   wfa_pol=plain_wfa_pol, **kw)
         ids = np.flatnonzero(flag)
         out["iters"][ids] += q["iters"]
         plain_ok = (q["status"] != NAN_STATE) & np.isfinite(q["chi2"])

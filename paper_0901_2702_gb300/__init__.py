@@ -20,7 +20,7 @@ __all__ = [
     "vfisv_strerror", "vfisv_config_default", "vfisv_nn_init", "vfisv_nn_train",
     "vfisv_nn_grad", "vfisv_nn_infer", "vfisv_invert_nn", "vfisv_graph_begin", "vfisv_graph_end",
     "vfisv_graph_launch", "vfisv_graph_destroy", "vfisv_autotune", "vfisv_voigt",
-    "vfisv_limb_weights", "vfisv_restart_models", "VfisvError",
+    "vfisv_limb_weights", "vfisv_restart_models", "vfisv_init_models", "VfisvError",
     "library_path",
     "load",
     "NN_NBLOB", "NN_NTRAIN",
@@ -51,7 +51,8 @@ class vfisv_config(ctypes.Structure):
     _fields_ = [("max_iter", ctypes.c_int32), ("free_mask", ctypes.c_uint32),
                 ("conv_rtol", ctypes.c_double), ("conv_eps", ctypes.c_double),
                 ("eps0", ctypes.c_double), ("restarts", ctypes.c_int32),
-                ("seed", ctypes.c_uint64), ("hess_reuse", ctypes.c_double)]
+                ("seed", ctypes.c_uint64), ("hess_reuse", ctypes.c_double),
+                ("wfa_pol", ctypes.c_double)]
 
 
 def library_path() -> str:
@@ -112,6 +113,9 @@ def load():
     lib.vfisv_voigt.restype = ctypes.c_int
     lib.vfisv_limb_weights.argtypes = [P, P, P, I64, I32, ctypes.c_float, P, P, P]
     lib.vfisv_limb_weights.restype = ctypes.c_int
+    lib.vfisv_init_models.argtypes = [P, P, I64, P, I32, P, I32, ctypes.POINTER(vfisv_line), P,
+                                      P, P]
+    lib.vfisv_init_models.restype = ctypes.c_int
     lib.vfisv_restart_models.argtypes = [P, P, I64, I64, I32, ctypes.c_uint32, U64, P, P]
     lib.vfisv_restart_models.restype = ctypes.c_int
     _lib = lib
@@ -488,4 +492,26 @@ def vfisv_restart_models(h: Handle, models, pixel0: int, k: int, free_mask: int 
            "vfisv_restart_models")
     if not _is_torch(out) and ko is not out:
         out[...] = ko
+    return out
+
+
+def vfisv_init_models(h: Handle, obs, filters, wl_mA, line, want_pol: bool = True, stream=None):
+    """Initial models [npix, 10] from the filtergrams (weak field, wing
+    azimuth, centre-of-gravity velocity) and the polarisation level [npix]."""
+    npix = int(obs.shape[0])
+    nfilt, nlam = int(filters.shape[0]), int(filters.shape[1])
+    out = {"init": _empty(obs, (npix, 10), np.float32),
+           "pol": _empty(obs, (npix,), np.float32) if want_pol else None}
+    op, k1 = _ptr(obs, np.float32)
+    fp, k2 = _ptr(filters, np.float32)
+    lp, k3 = _ptr(wl_mA, np.float32)
+    ip, k4 = _ptr(out["init"], np.float32)
+    pp, k5 = _ptr(out["pol"], np.float32)
+    ln = _line(line)
+    _check(load().vfisv_init_models(h.ptr, op, npix, fp, nfilt, lp, nlam, ctypes.byref(ln), ip, pp,
+                                    ctypes.c_void_p(_stream(obs, stream))), "vfisv_init_models")
+    for key, k in (("init", k4), ("pol", k5)):
+        dst = out.get(key)
+        if dst is not None and not _is_torch(dst) and k is not dst:
+            dst[...] = k
     return out

@@ -25,6 +25,10 @@ struct vfisv_handle {
   size_t mixws_bytes = 0;
   int lm_block = 128;      // LM pixel slots per CTA (vfisv_autotune)
   void* vtab = nullptr;    // Taylor table of H, F (built on first use)
+  void* geom = nullptr;    // filter centres and wing weights of the weak-field init
+  size_t geom_bytes = 0;
+  void* wfinit = nullptr;  // weak-field initial models of an inversion without init
+  size_t wfinit_bytes = 0;
   bool capturing = false;  // between vfisv_graph_begin and vfisv_graph_end
 };
 
@@ -199,6 +203,7 @@ int check_config(const vfisv_config* cfg, int nfilt) {
   // restart counters are 20 bits wide (each restart costs an iteration)
   if ((cfg->restarts & ~7) || (cfg->restarts && cfg->max_iter >= (1 << 20))) return VFISV_E_ARG;
   if (!(cfg->hess_reuse >= 0) || !isfinite(cfg->hess_reuse)) return VFISV_E_ARG;
+  if (!(cfg->wfa_pol >= 0) || !isfinite(cfg->wfa_pol)) return VFISV_E_ARG;
   if (4 * nfilt - __builtin_popcount(cfg->free_mask) <= 0) return VFISV_E_ARG;
   return VFISV_OK;
 }
@@ -245,6 +250,18 @@ int invert_device(vfisv_handle* h, const DevInvert& d, int nfilt, int nlam,
   }
   char* ws = (char*)h->ws;
   float* table = (float*)(ws + L.table);
+  const float* init = d.init;
+  if (!init && cfg->wfa_pol > 0.0) {
+    // start from the weak-field models of the filtergrams (Sec. 6)
+    int rc = grow(&h->geom, &h->geom_bytes, filter_geom_bytes());
+    if (!rc) rc = grow(&h->wfinit, &h->wfinit_bytes, (size_t)npix * 10 * sizeof(float));
+    if (rc) return rc;
+    if (launch_weak_field(d.obs, npix, npix_dev, d.filters, nfilt, d.wl, nlam,
+                          line_constants(line), 0, 0.0f, h->geom, (float*)h->wfinit, nullptr,
+                          s) != cudaSuccess)
+      return VFISV_E_CUDA;
+    init = (const float*)h->wfinit;
+  }
   if (launch_pack_table(d.filters, nfilt, d.wl, nlam, table, s) != cudaSuccess)
     return VFISV_E_CUDA;
   if (cudaMemsetAsync(ws + L.queue, 0, sizeof(unsigned long long), s) != cudaSuccess)
@@ -253,7 +270,7 @@ int invert_device(vfisv_handle* h, const DevInvert& d, int nfilt, int nlam,
   a.obs = d.obs;
   a.w = d.w;
   a.w_stride = d.w_stride;
-  a.init = d.init;
+  a.init = init;
   a.table = table;
   a.nlam = nlam;
   a.npix = npix;
@@ -316,6 +333,7 @@ void vfisv_config_default(vfisv_config* c) {
   c->restarts = 0;
   c->seed = 0;
   c->hess_reuse = 0.0;
+  c->wfa_pol = 0.0;
 }
 
 int vfisv_create(vfisv_handle** out, int device) {
@@ -348,6 +366,8 @@ void vfisv_destroy(vfisv_handle* h) {
   if (h->nnws) cudaFree(h->nnws);
   if (h->mixws) cudaFree(h->mixws);
   if (h->vtab) cudaFree(h->vtab);
+  if (h->geom) cudaFree(h->geom);
+  if (h->wfinit) cudaFree(h->wfinit);
   delete h;
 }
 
@@ -476,6 +496,32 @@ int vfisv_voigt(vfisv_handle* h, const float* a, const float* u, int64_t n, int3
   if (launch_voigt(method, h->W, h->vtab, (const float*)st.bufs[0].dev,
                    (const float*)st.bufs[1].dev, n, (float*)st.bufs[2].dev,
                    (float*)st.bufs[3].dev, s) != cudaSuccess)
+    return VFISV_E_CUDA;
+  return st.finish(s);
+}
+
+int vfisv_init_models(vfisv_handle* h, const float* obs, int64_t npix, const float* filters,
+                      int32_t nfilt, const float* wl_mA, int32_t nlam, const vfisv_line* line,
+                      float* init_out, float* pol_out, void* stream) {
+  if (!h || !obs || !filters || !wl_mA || !init_out || !line_ok(line)) return VFISV_E_ARG;
+  if (npix < 0 || nlam < 1 || nlam > 4096) return VFISV_E_SIZE;
+  if (nfilt < 3 || nfilt > 8) return VFISV_E_UNSUPPORTED;
+  if (npix == 0) return VFISV_OK;
+  if (set_device(h)) return VFISV_E_CUDA;
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc = grow(&h->geom, &h->geom_bytes, filter_geom_bytes());
+  if (rc) return rc;
+  Staging st;
+  st.add(obs, (size_t)npix * 4 * nfilt * sizeof(float), false);
+  st.add(filters, (size_t)nfilt * nlam * sizeof(float), false);
+  st.add(wl_mA, (size_t)nlam * sizeof(float), false);
+  st.add(init_out, (size_t)npix * 10 * sizeof(float), true);
+  st.add(pol_out, pol_out ? (size_t)npix * sizeof(float) : 0, true);
+  if ((rc = st.prepare(h, s))) return rc;
+  if (launch_weak_field((const float*)st.bufs[0].dev, npix, nullptr, (const float*)st.bufs[1].dev, nfilt,
+                        (const float*)st.bufs[2].dev, nlam, line_constants(line), 0, 0.0f,
+                        h->geom, (float*)st.bufs[3].dev, (float*)st.bufs[4].dev,
+                        s) != cudaSuccess)
     return VFISV_E_CUDA;
   return st.finish(s);
 }
@@ -766,6 +812,15 @@ int vfisv_invert_nn(vfisv_handle* h, const float* blob, const float* obs, const 
   if (nn::nn_infer(h->nnws, kInferChunk, (const float*)st.bufs[4].dev, o, npix, (float)line->mu,
                    init, nullptr, nullptr, s) != cudaSuccess)
     return VFISV_E_CUDA;
+  if (cfg_nn->wfa_pol > 0.0) {
+    // the paper's combination (Sec. 6): weak-field B, gamma below the
+    // polarisation threshold, the wing azimuth everywhere
+    if ((rc = grow(&h->geom, &h->geom_bytes, filter_geom_bytes()))) return rc;
+    if (launch_weak_field(o, npix, nullptr, (const float*)st.bufs[2].dev, nfilt,
+                          (const float*)st.bufs[3].dev, nlam, line_constants(line), 1,
+                          (float)cfg_nn->wfa_pol, h->geom, init, nullptr, s) != cudaSuccess)
+      return VFISV_E_CUDA;
+  }
   DevInvert d;
   d.obs = o;
   d.w = w;

@@ -183,6 +183,13 @@ cudaError_t launch_voigt_table(const Weideman& W, void* tab, cudaStream_t s);
 cudaError_t launch_voigt(int method, const Weideman& W, const void* tab, const float* a,
                          const float* u, int64_t n, float* H, float* F, cudaStream_t s);
 
+// prep.cu: initial models from the filtergrams (Sec. 6); `geom` is device
+// scratch of filter_geom_bytes()
+size_t filter_geom_bytes();
+cudaError_t launch_weak_field(const float* obs, int64_t npix, const int64_t* npix_dev,
+                              const float* filters, int nf, const float* wl, int nlam,
+                              const LineK& lk, int mode, float pol_thr, void* geom, float* init,
+                              float* pol_out, cudaStream_t s);
 // prep.cu: Eq. 14-15 weights
 cudaError_t launch_limb_weights(const float* obs, const float* mu, int64_t npix, int nf,
                                 float ic0, const float* sigma4, float* w, cudaStream_t s);

@@ -37,28 +37,6 @@ struct Dot2 {
   __device__ __forceinline__ float value() const { return s + c; }
 };
 
-// Bounds applied after every step (the oracle's reading).
-__device__ __forceinline__ void apply_bounds(float (&m)[10]) {
-  if (m[0] < 0.0f) {
-    m[0] = -m[0];
-    m[1] = 180.0f - m[1];
-  }
-  float g = fmodf(m[1], 360.0f);
-  if (g < 0.0f) g += 360.0f;
-  m[1] = (g > 180.0f) ? 360.0f - g : g;
-  float ps = fmodf(m[2], 180.0f);
-  if (ps < 0.0f) ps += 180.0f;
-  if (ps >= 180.0f) ps = 0.0f;
-  m[2] = ps;
-  m[0] = fminf(m[0], 6000.0f);
-  m[3] = fminf(fmaxf(m[3], 0.01f), 500.0f);
-  m[4] = fminf(fmaxf(m[4], 5.0f), 150.0f);
-  m[5] = fminf(fmaxf(m[5], 0.0f), 5.0f);
-  m[6] = fminf(fmaxf(m[6], -20.0f), 20.0f);
-  m[7] = fminf(fmaxf(m[7], 0.0f), 2.0f);
-  m[8] = fminf(fmaxf(m[8], 0.0f), 2.0f);
-}
-
 // Table 2 (with the oracle's reading of its overlapping rows).
 __device__ __forceinline__ double eps_update(double e, bool success) {
   double n;

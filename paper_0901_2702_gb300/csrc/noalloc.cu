@@ -92,6 +92,7 @@ extern "C" int vfisv_invert_noalloc(const float* obs, const float* weights,
   if (nlam > kMaxNlam) return VFISV_E_SIZE;  // the fixed table holds 4096 wavelengths
   if (nfilt != 6) return VFISV_E_UNSUPPORTED;
   if (cfg->restarts != 0) return VFISV_E_UNSUPPORTED;  // restart state is not in the fixed array
+  if (cfg->wfa_pol != 0.0) return VFISV_E_UNSUPPORTED;  // the weak-field start needs a buffer
   if (!(cfg->hess_reuse >= 0) || !isfinite(cfg->hess_reuse)) return VFISV_E_ARG;
   if (cfg->max_iter < 0 || (cfg->free_mask & ~0x1FFu) || !(cfg->conv_rtol >= 0) ||
       !(cfg->conv_eps >= 0) || !(cfg->eps0 > 0) || !isfinite(cfg->eps0) ||
