@@ -61,14 +61,13 @@ TRAIN_N, TRAIN_EPOCHS, TRAIN_BATCH = 1 << 22, 8, 8192
 # filtered derivative rows 4 x 132.
 FLOP_PER_LAMBDA = 4 + 3 * 135 + 16 + 32 + 48 + 28 + 14 + 4 + 6 + 63 + 4 * 132
 FLOP_PER_PASS_EXTRA = 60  # model and residual outside the wavelength loop
-# DRAM bytes (read + write) of one plain-LM launch without covariance, per
-# pixel, from one ncu capture of invert_kernel on 262,144 pixels of the
-# 1024^2 distributions (51.5 MB read + 3.6 MB write; profiles/
-# invert_kernel_traffic.md); scaled by the pixels of a launch.  Algorithmic:
-# 192 B read (observables, weights) + 52 B written (model, chi2, counts);
-# at that size most of the written outputs are still in L2 when the kernel
-# ends, so the scaled figure can undercount writes by up to 52 B/pixel.
-TRAFFIC_BYTES_PER_PIXEL = (51_455_232 + 3_640_576) / 262_144
+# DRAM bytes (read + write) of one plain-LM launch without covariance (FP64
+# solve, the default), per pixel, from one ncu capture of invert_kernel on
+# 262,144 pixels of the 1024^2 distributions (54.0 MB read + 102.2 MB write;
+# profiles/invert_kernel_traffic.md); scaled by the pixels of a launch.
+# Algorithmic: 192 B read (observables, weights) + 52 B written (model,
+# chi2, counts); the extra writes are the FP64 solve's call-stack traffic.
+TRAFFIC_BYTES_PER_PIXEL = (54_013_696 + 102_230_784) / 262_144
 
 
 def fp32_peak_tflops(sm_mhz: float, nsm: int = 152) -> float:
@@ -253,6 +252,32 @@ def run_ours(args, rank, world):
     ms_lm = timed(lambda: step_plain(out_r), 1, "timed_lm")
     v.vfisv_check(h, stream)
 
+    # the same mixed step with the opt-in double-float solve (fast_solve=1):
+    # reported beside the headline, which keeps the FP64 solve
+    cfg_nn_f = v.vfisv_config_default(max_iter=NN_CAP, fast_solve=1)
+    cfg_plain_f = v.vfisv_config_default(max_iter=PLAIN_CAP, fast_solve=1)
+    out_f = outputs(True)
+
+    def step_fast():
+        v.vfisv_invert_nn(h, blob, obs, wts, tf, tx, line, config_nn=cfg_nn_f,
+                          config_plain=cfg_plain_f, chi2_flag=CHI2_FLAG,
+                          flag_unconverged=FLAG_UNCONV, out=out_f, stream=stream)
+
+    step_fast()
+    v.vfisv_graph_begin(h, stream)
+    step_fast()
+    graph_fast = v.vfisv_graph_end(h, stream)
+    ms_fast = timed(lambda: graph_fast.launch(stream), max(1, min(args.steps, 2)), "timed_fast")
+    out_rf = outputs(False, cov=False)
+    v.vfisv_invert(h, obs, wts, tf, tx, line, config=cfg_plain_f, out=out_rf, stream=stream)
+    ms_lm_fast = timed(lambda: v.vfisv_invert(h, obs, wts, tf, tx, line, config=cfg_plain_f,
+                                              out=out_rf, stream=stream), 1, "timed_lm_fast")
+    v.vfisv_check(h, stream)
+    graph_fast.close()
+    conv_f = int(((out_f["status"] == 0) | (out_f["status"] == 2)).sum().item())
+    passes_f = int((out_rf["iters"].to(torch.int64) + 1).sum().item())
+    flops_f = passes_f * (NLAM * FLOP_PER_LAMBDA + FLOP_PER_PASS_EXTRA)
+
     conv = lambda o: int(((o["status"] == 0) | (o["status"] == 2)).sum().item())  # noqa: E731
     conv_m, conv_p = conv(out_m), conv(out_p)
     if dist:
@@ -300,7 +325,7 @@ def run_ours(args, rank, world):
         "metric": METRIC, "value": value, "unit": "pixels/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_mixed,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32 synthesis/Jacobian, double-float (f32 pairs) solve, compensated f32 chi2, bf16 network",
+        "dtype": "f32 synthesis/Jacobian, f64 solve/chi2, bf16 network",
         "data": "synthetic (seeded ME parameters, library-synthesised Stokes + Gaussian noise)",
         "config": {"workload": f"NN-initialised mixed inversion of the {wl}: Fe I 6173 A, "
                                f"6 filters x 149 wavelengths, network guess + LM cap {NN_CAP}, "
@@ -323,6 +348,12 @@ def run_ours(args, rank, world):
         "chi2_mixed_le_plain_frac": better,
         "chi2_mixed_le_plain_1pct_frac": better2,
         "chi2_mixed_over_plain_median": ratio_med,
+        "fast_solve": {"note": "same mixed step with the opt-in double-float solve and "
+                               "compensated f32 chi2 (no FP64 on the LM path); not the headline",
+                       "value": conv_f / (ms_fast / 1e3), "unit": "pixels/s",
+                       "ms_per_step": ms_fast, "converged_fraction": conv_f / npix,
+                       "lm_kernel_ms": ms_lm_fast,
+                       "lm_roofline_frac": flops_f / (ms_lm_fast / 1e3) / 1e12 / peak},
         "train": {"profiles": TRAIN_N, "epochs": TRAIN_EPOCHS, "batch": TRAIN_BATCH,
                   "seconds_incl_synthesis": train_s, "final_loss": final_loss},
         "e2e": {"value": conv_h * world / e2e_s, "unit": "pixels/s",
@@ -332,9 +363,9 @@ def run_ours(args, rank, world):
                      "frac": achieved / peak,
                      "traffic": int(TRAFFIC_BYTES_PER_PIXEL * npix),
                      "traffic_note": "dram read+write bytes per launch, scaled by pixels from a "
-                                     "262,144-pixel ncu capture (210 B/px; algorithmic 244 B/px: "
-                                     "reads 196 vs 192, the outputs of that launch mostly still in "
-                                     "L2 at its end)",
+                                     "262,144-pixel ncu capture (596 B/px; algorithmic 244 B/px: "
+                                     "reads 206 vs 192, writes 390 B/px of which ~350 are the FP64 "
+                                     "solve's call-stack write-back)",
                      "kernel": "invert_kernel<6> (plain LM pass, no covariance)",
                      "kernel_ms": ms_lm,
                      "note": "peak = FP32 pipe, 152 SM x 128 lanes x 2 flop x 2070 MHz (no "

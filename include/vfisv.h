@@ -129,12 +129,18 @@ typedef struct {
  *              the weak-field estimate where the polarisation level is below
  *              wfa_pol (the paper: 0.06), the wing azimuth everywhere, the
  *              network's values for the rest.
+ *   fast_solve 0 (default): the damped solve, the covariance and the chi2
+ *              acceptance sum in FP64.  1: the solve and the covariance in
+ *              double-float arithmetic (pairs of FP32 numbers, ~48 bits) and
+ *              chi2 by a compensated FP32 sum -- no FP64 on the fast path,
+ *              whose FP64 pipe issues 2 FMAs per SM per clock on GB300
+ *              against 128 in FP32.  Not the paper's precision: opt-in.
  *   hess_reuse Hessian reuse near the minimum (Sec. 4.4), 0 = off: when an
  *              accepted step lowered chi2 by less than hess_reuse relative,
  *              and so did the previous accepted step, J^T W J is kept from
  *              the previous model and only J^T W r is rebuilt; the
  *              covariance comes from the matrix in use.
- * vfisv_config_default() fills: 50, 0x1FF, 1e-4, 1.0, 1.0, 0, 0, 0.0, 0.0. */
+ * vfisv_config_default() fills: 50, 0x1FF, 1e-4, 1.0, 1.0, 0, 0, 0.0, 0.0, 0. */
 typedef struct {
   int32_t max_iter;
   uint32_t free_mask;
@@ -145,6 +151,7 @@ typedef struct {
   uint64_t seed;
   double hess_reuse;
   double wfa_pol;
+  int32_t fast_solve;
 } vfisv_config;
 
 typedef struct vfisv_handle vfisv_handle;

@@ -52,7 +52,7 @@ class vfisv_config(ctypes.Structure):
                 ("conv_rtol", ctypes.c_double), ("conv_eps", ctypes.c_double),
                 ("eps0", ctypes.c_double), ("restarts", ctypes.c_int32),
                 ("seed", ctypes.c_uint64), ("hess_reuse", ctypes.c_double),
-                ("wfa_pol", ctypes.c_double)]
+                ("wfa_pol", ctypes.c_double), ("fast_solve", ctypes.c_int32)]
 
 
 def library_path() -> str:

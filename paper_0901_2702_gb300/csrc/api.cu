@@ -204,6 +204,7 @@ int check_config(const vfisv_config* cfg, int nfilt) {
   if ((cfg->restarts & ~7) || (cfg->restarts && cfg->max_iter >= (1 << 20))) return VFISV_E_ARG;
   if (!(cfg->hess_reuse >= 0) || !isfinite(cfg->hess_reuse)) return VFISV_E_ARG;
   if (!(cfg->wfa_pol >= 0) || !isfinite(cfg->wfa_pol)) return VFISV_E_ARG;
+  if (cfg->fast_solve != 0 && cfg->fast_solve != 1) return VFISV_E_ARG;
   if (4 * nfilt - __builtin_popcount(cfg->free_mask) <= 0) return VFISV_E_ARG;
   return VFISV_OK;
 }
@@ -237,7 +238,8 @@ int invert_device(vfisv_handle* h, const DevInvert& d, int nfilt, int nlam,
   int64_t nslots = 0;
   int grid = 0, block = h->lm_block;
   size_t smem = 0;
-  if (invert_slots(nfilt, nlam, npix, cfg->restarts, &nslots, &grid, &block, &smem) !=
+  if (invert_slots(nfilt, nlam, npix, cfg->restarts, cfg->fast_solve, &nslots, &grid, &block,
+                   &smem) !=
       cudaSuccess) {
     cudaGetLastError();
     return VFISV_E_CUDA;
@@ -295,9 +297,11 @@ int invert_device(vfisv_handle* h, const DevInvert& d, int nfilt, int nlam,
   a.restarts = cfg->restarts;
   a.seed = cfg->seed;
   a.hess_reuse = cfg->hess_reuse;
+  a.fast_solve = cfg->fast_solve;
   a.rs_state = cfg->restarts ? ws + L.rs : nullptr;
   if (launch_invert(a, nfilt, grid, block, smem, s) != cudaSuccess) return VFISV_E_CUDA;
-  if (d.cov && launch_covariance(d.cov, d.status, npix, npix_dev, cfg->free_mask, s) !=
+  if (d.cov && launch_covariance(d.cov, d.status, npix, npix_dev, cfg->free_mask,
+                                cfg->fast_solve, s) !=
                    cudaSuccess)
     return VFISV_E_CUDA;
   return VFISV_OK;
@@ -334,6 +338,7 @@ void vfisv_config_default(vfisv_config* c) {
   c->seed = 0;
   c->hess_reuse = 0.0;
   c->wfa_pol = 0.0;
+  c->fast_solve = 0;
 }
 
 int vfisv_create(vfisv_handle** out, int device) {

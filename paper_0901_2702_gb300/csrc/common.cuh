@@ -135,6 +135,7 @@ struct InvertArgs {
   double conv_eps;
   double eps0;
   double hess_reuse = 0.0;   // Hessian reuse threshold (Sec. 4.4), 0 = off
+  int fast_solve = 0;        // 1: double-float solve, compensated FP32 chi2
   int restarts = 0;          // randomised restarts (Sec. 4.2): trigger bit mask, 0 = off
   uint64_t seed = 0;         // key of the restart perturbations
   char* rs_state = nullptr;  // restarts: per-slot state, layout RestartState
@@ -165,15 +166,16 @@ cudaError_t launch_synth(const SynthArgs& a, int nf, cudaStream_t s);
 // Persistent LM kernel: launch shape for `npix` pixels with *block pixel
 // slots per CTA (64, 128 or 256; anything else selects 128 and is written
 // back), and the number of resident slots (the scratch it needs).
-cudaError_t invert_slots(int nf, int nlam, int64_t npix, int restarts, int64_t* nslots,
-                         int* grid, int* block, size_t* smem);
+cudaError_t invert_slots(int nf, int nlam, int64_t npix, int restarts, int fast_solve,
+                         int64_t* nslots, int* grid, int* block, size_t* smem);
 cudaError_t launch_restart_perturb(const float* in, int64_t n, int64_t pix0, int k,
                                    uint32_t free_mask, uint64_t seed, float* out, cudaStream_t s);
 // Upload the Weideman coefficients to the LM kernel's constant bank on the
 // current device (once per device).
 cudaError_t invert_set_constants(const Weideman& W);
 cudaError_t launch_covariance(float* cov, const int32_t* status, int64_t npix,
-                              const int64_t* npix_dev, uint32_t free_mask, cudaStream_t s);
+                              const int64_t* npix_dev, uint32_t free_mask, int fast_solve,
+                              cudaStream_t s);
 cudaError_t launch_invert(const InvertArgs& a, int nf, int grid, int block, size_t smem,
                           cudaStream_t s);
 

@@ -229,8 +229,68 @@ __device__ __forceinline__ void chol_solve9_df(const dfl (&L)[kNPk], const dfl (
 }
 
 // Eq. 5 with the Marquardt diagonal (Eq. 4): delta = (A + eps diag A)^-1 g,
-// Jacobi-scaled, in double-float; the result is delta[i].hi + delta[i].lo.
-__device__ __noinline__ void damped_step(const float* scr, int64_t ns, uint32_t free_mask, double eps,
+// Jacobi-scaled, in FP64 (the default precision of the solve).
+__device__ __noinline__ void damped_step_fp64(const float* scr, int64_t ns, uint32_t free_mask, double eps,
+                            double (&delta)[kNP]) {
+  double L[kNPk], sc[kNP];
+  bool held[kNP];
+  scaled_system(scr, ns, free_mask, eps, L, sc, held);
+  double y[kNP];
+#pragma unroll
+  for (int i = 0; i < kNP; ++i)
+    y[i] = held[i] ? 0.0 : (double)scr[(int64_t)(kNPk + i) * ns] * sc[i];
+  double ri[kNP];
+  if (cholesky9(L, ri)) {
+    chol_solve9(L, ri, y);
+  } else {
+    // rebuild the scaled matrix (the factorisation overwrote it)
+    scaled_system(scr, ns, free_mask, eps, L, sc, held);
+    double b[kNP];
+#pragma unroll
+    for (int i = 0; i < kNP; ++i) b[i] = y[i];
+    jacobi_pinv(L, b, y, nullptr);
+  }
+#pragma unroll
+  for (int i = 0; i < kNP; ++i) delta[i] = held[i] ? 0.0 : sc[i] * y[i];
+}
+
+// Covariance (J^T W J)^+ at the final model, in parameter units, from the
+// packed J^T W J at scr[e * ns].  Reads everything before writing `out`, so
+// `out` may hold the packed matrix itself.  With try_only, returns false
+// without writing when the Cholesky factorisation fails (the caller then
+// runs the eigen-decomposition path for that pixel).
+__device__ __noinline__ bool covariance_fp64(const float* scr, int64_t ns, uint32_t free_mask,
+                                        float* out, bool try_only) {
+  double L[kNPk], sc[kNP];
+  bool held[kNP];
+  scaled_system(scr, ns, free_mask, 0.0, L, sc, held);
+  double P[kNPk], ri[kNP];
+  if (cholesky9(L, ri)) {
+    for (int j = 0; j < kNP; ++j) {
+      double x[kNP];
+#pragma unroll
+      for (int i = 0; i < kNP; ++i) x[i] = (i == j) ? 1.0 : 0.0;
+      chol_solve9(L, ri, x);
+      for (int i = j; i < kNP; ++i) P[tri(i, j)] = x[i];
+    }
+  } else {
+    if (try_only) return false;
+    scaled_system(scr, ns, free_mask, 0.0, L, sc, held);
+    jacobi_pinv(L, nullptr, nullptr, P);
+  }
+  for (int i = 0; i < 10; ++i)
+    for (int j = 0; j < 10; ++j) {
+      float v = 0.0f;
+      if (i < kNP && j < kNP && !held[i] && !held[j])
+        v = (float)(sc[i] * sc[j] * ((i >= j) ? P[tri(i, j)] : P[tri(j, i)]));
+      out[i * 10 + j] = v;
+    }
+  return true;
+}
+
+// The same step in double-float (the fast_solve option); the result is
+// delta[i].hi + delta[i].lo.
+__device__ __noinline__ void damped_step_df(const float* scr, int64_t ns, uint32_t free_mask, double eps,
                                          dfl (&delta)[kNP]) {
   dfl L[kNPk], sc[kNP], y[kNP];
   bool held[kNP];
@@ -276,11 +336,11 @@ __device__ __noinline__ void damped_step(const float* scr, int64_t ns, uint32_t 
 // Covariance (J^T W J)^+ at the final model, in parameter units, from the
 // packed J^T W J at scr[e * ns].  Reads everything before writing `out`, so
 // `out` may hold the packed matrix itself.  The Cholesky path runs in
-// double-float; with try_only, returns false without writing when the
-// factorisation fails (the caller then runs the FP64 eigen-decomposition
-// path for that pixel).
-__device__ __noinline__ bool covariance(const float* scr, int64_t ns, uint32_t free_mask,
-                                        float* out, bool try_only) {
+// double-float (the fast_solve option); with try_only, returns false
+// without writing when the factorisation fails (the caller then runs the
+// FP64 eigen-decomposition path for that pixel).
+__device__ __noinline__ bool covariance_df(const float* scr, int64_t ns, uint32_t free_mask,
+                                           float* out, bool try_only) {
   uint32_t hmask = 0;
   dfl sc[kNP];
 #pragma unroll
@@ -428,8 +488,10 @@ __host__ __device__ constexpr size_t invert_smem_bytes(int tabf, int nacc, int n
   return (size_t)tabf * 4 + (size_t)nacc * nt * 4 + (size_t)kStateWords * nt * 4 + 16;
 }
 
-// RS: randomised restarts compiled in (A.restarts != 0).
-template <int NF, int BS, bool RS>
+// RS: randomised restarts compiled in (A.restarts != 0).  DF: the damped
+// solve in double-float and chi2 by a compensated FP32 sum (fast_solve);
+// otherwise both in FP64.
+template <int NF, int BS, bool RS, bool DF>
 __global__ void __launch_bounds__(BS, 1) invert_kernel(InvertArgs A) {
   constexpr int NOBS = 4 * NF;
   constexpr int NACC = kRows * 4 * NF;
@@ -537,13 +599,20 @@ __global__ void __launch_bounds__(BS, 1) invert_kernel(InvertArgs A) {
         for (int j = 0; j < 10; ++j) ST(sMt, j) = Mt[j];
         restart = true;
       } else {
-        dfl d[kNP];
-        damped_step(scr, ns, A.free_mask, sEps[tid], d);
         float Mt[10];
+        if constexpr (DF) {
+          dfl d[kNP];
+          damped_step_df(scr, ns, A.free_mask, sEps[tid], d);
 #pragma unroll
-        for (int j = 0; j < kNP; ++j) {
-          const dfl t = two_sum(ST(sM, j), d[j].hi);
-          Mt[j] = t.hi + (t.lo + d[j].lo);  // the FP32 model nearest M + delta
+          for (int j = 0; j < kNP; ++j) {
+            const dfl t = two_sum(ST(sM, j), d[j].hi);
+            Mt[j] = t.hi + (t.lo + d[j].lo);  // the FP32 model nearest M + delta
+          }
+        } else {
+          double d[kNP];
+          damped_step_fp64(scr, ns, A.free_mask, sEps[tid], d);
+#pragma unroll
+          for (int j = 0; j < kNP; ++j) Mt[j] = (float)((double)ST(sM, j) + d[j]);
         }
         Mt[9] = 1.0f;
         apply_bounds(Mt);
@@ -576,15 +645,26 @@ __global__ void __launch_bounds__(BS, 1) invert_kernel(InvertArgs A) {
       syn[2 * NF + k] = mus1 * fmaf(s2p, q0, c2p * u0);
       syn[3 * NF + k] = mus1 * D(0, 3, k);
     }
-    // compensated FP32 sum of w r^2 (the residuals themselves carry the FP32
-    // synthesis error, ~1e-4 of chi2, so this is as exact as the data)
-    Dot2 q{0.0f, 0.0f};
+    double c2;
+    if constexpr (DF) {
+      // compensated FP32 sum of w r^2 (the residuals themselves carry the
+      // FP32 synthesis error, ~1e-4 of chi2)
+      Dot2 q{0.0f, 0.0f};
 #pragma unroll
-    for (int j = 0; j < NOBS; ++j) {
-      const float r = o[j] - syn[j];
-      q.add(wv[j] * r, r);
+      for (int j = 0; j < NOBS; ++j) {
+        const float r = o[j] - syn[j];
+        q.add(wv[j] * r, r);
+      }
+      c2 = ((double)q.s + (double)q.c) / (double)dof;
+    } else {
+      c2 = 0.0;
+#pragma unroll
+      for (int j = 0; j < NOBS; ++j) {
+        const double r = (double)(o[j] - syn[j]);
+        c2 = fma((double)wv[j] * r, r, c2);
+      }
+      c2 /= (double)dof;
     }
-    const double c2 = ((double)q.s + (double)q.c) / (double)dof;
 
     bool accept, retire = false;
     int status = VFISV_PIX_MAXITER;
@@ -785,6 +865,7 @@ __global__ void __launch_bounds__(BS, 1) invert_kernel(InvertArgs A) {
 // warp that happens to hold one such pixel.
 constexpr int kCovThreads = 128;
 constexpr int kCovQueue = 2 * kCovThreads;
+template <bool DF>
 __global__ void __launch_bounds__(kCovThreads) covariance_kernel(float* cov,
                                                                  const int32_t* status,
                                                                  int64_t npix_max,
@@ -802,7 +883,9 @@ __global__ void __launch_bounds__(kCovThreads) covariance_kernel(float* cov,
     if (p < npix) {
       const int st = status[p];
       if (st == VFISV_PIX_CONVERGED || st == VFISV_PIX_MAXITER || st == VFISV_PIX_STALLED) {
-        if (!covariance(cov + p * 100, 1, free_mask, cov + p * 100, true)) {
+        const bool ok = DF ? covariance_df(cov + p * 100, 1, free_mask, cov + p * 100, true)
+                           : covariance_fp64(cov + p * 100, 1, free_mask, cov + p * 100, true);
+        if (!ok) {
           const int slot = atomicAdd(&qn, 1);
           queue[slot] = p;  // slot < kCovQueue: drained below before it can fill
         }
@@ -813,7 +896,10 @@ __global__ void __launch_bounds__(kCovThreads) covariance_kernel(float* cov,
     if (qn >= kCovThreads || last) {
       const int n = qn;
       for (int i = threadIdx.x; i < n; i += blockDim.x)
-        covariance(cov + queue[i] * 100, 1, free_mask, cov + queue[i] * 100, false);
+        if (DF)
+          covariance_df(cov + queue[i] * 100, 1, free_mask, cov + queue[i] * 100, false);
+        else
+          covariance_fp64(cov + queue[i] * 100, 1, free_mask, cov + queue[i] * 100, false);
       __syncthreads();
       if (threadIdx.x == 0) qn = 0;
     }
@@ -822,7 +908,8 @@ __global__ void __launch_bounds__(kCovThreads) covariance_kernel(float* cov,
 }
 
 cudaError_t launch_covariance(float* cov, const int32_t* status, int64_t npix,
-                              const int64_t* npix_dev, uint32_t free_mask, cudaStream_t s) {
+                              const int64_t* npix_dev, uint32_t free_mask, int fast_solve,
+                              cudaStream_t s) {
   int dev = 0, nsm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -830,13 +917,16 @@ cudaError_t launch_covariance(float* cov, const int32_t* status, int64_t npix,
   int64_t grid = (npix + kCovThreads - 1) / kCovThreads;
   if (grid > (int64_t)nsm * 4) grid = (int64_t)nsm * 4;
   if (grid < 1) grid = 1;
-  covariance_kernel<<<(int)grid, kCovThreads, 0, s>>>(cov, status, npix, npix_dev, free_mask);
+  if (fast_solve)
+    covariance_kernel<true><<<(int)grid, kCovThreads, 0, s>>>(cov, status, npix, npix_dev, free_mask);
+  else
+    covariance_kernel<false><<<(int)grid, kCovThreads, 0, s>>>(cov, status, npix, npix_dev, free_mask);
   return cudaGetLastError();
 }
 
-template <int BS, bool RS>
+template <int BS, bool RS, bool DF>
 static cudaError_t slots_for(int nlam, int64_t npix, int64_t* nslots, int* grid, size_t* smem) {
-  auto kern = invert_kernel<6, BS, RS>;
+  auto kern = invert_kernel<6, BS, RS, DF>;
   const size_t sm = invert_smem_bytes(table_floats(6, nlam), kRows * 4 * 6, BS);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
@@ -856,41 +946,55 @@ static cudaError_t slots_for(int nlam, int64_t npix, int64_t* nslots, int* grid,
   return cudaSuccess;
 }
 
-cudaError_t invert_slots(int nf, int nlam, int64_t npix, int restarts, int64_t* nslots,
-                         int* grid, int* block, size_t* smem) {
-  if (nf != 6) return cudaErrorInvalidValue;
+template <bool DF>
+static cudaError_t invert_slots_t(int nlam, int64_t npix, int restarts, int64_t* nslots,
+                                  int* grid, int* block, size_t* smem) {
   if (restarts) {  // compiled for the default slot count only
     *block = kInvThreadsDefault;
-    return slots_for<kInvThreadsDefault, true>(nlam, npix, nslots, grid, smem);
+    return slots_for<kInvThreadsDefault, true, DF>(nlam, npix, nslots, grid, smem);
   }
   const int bs = (*block == 64 || *block == 256) ? *block : kInvThreadsDefault;
   *block = bs;
   switch (bs) {
-    case 64: return slots_for<64, false>(nlam, npix, nslots, grid, smem);
-    case 256: return slots_for<256, false>(nlam, npix, nslots, grid, smem);
-    default: return slots_for<128, false>(nlam, npix, nslots, grid, smem);
+    case 64: return slots_for<64, false, DF>(nlam, npix, nslots, grid, smem);
+    case 256: return slots_for<256, false, DF>(nlam, npix, nslots, grid, smem);
+    default: return slots_for<128, false, DF>(nlam, npix, nslots, grid, smem);
   }
+}
+
+cudaError_t invert_slots(int nf, int nlam, int64_t npix, int restarts, int fast_solve,
+                         int64_t* nslots, int* grid, int* block, size_t* smem) {
+  if (nf != 6) return cudaErrorInvalidValue;
+  return fast_solve ? invert_slots_t<true>(nlam, npix, restarts, nslots, grid, block, smem)
+                    : invert_slots_t<false>(nlam, npix, restarts, nslots, grid, block, smem);
 }
 
 cudaError_t invert_set_constants(const Weideman& W) {
   return cudaMemcpyToSymbol(c_W, &W, sizeof(W));
 }
 
-cudaError_t launch_invert(const InvertArgs& a, int nf, int grid, int block, size_t smem,
-                          cudaStream_t s) {
-  if (nf != 6) return cudaErrorInvalidValue;
+template <bool DF>
+static cudaError_t launch_invert_t(const InvertArgs& a, int grid, int block, size_t smem,
+                                   cudaStream_t s) {
   if (a.restarts) {
     if (block != kInvThreadsDefault || !a.rs_state) return cudaErrorInvalidValue;
-    invert_kernel<6, kInvThreadsDefault, true><<<grid, block, smem, s>>>(a);
+    invert_kernel<6, kInvThreadsDefault, true, DF><<<grid, block, smem, s>>>(a);
     return cudaGetLastError();
   }
   switch (block) {
-    case 64: invert_kernel<6, 64, false><<<grid, 64, smem, s>>>(a); break;
-    case 256: invert_kernel<6, 256, false><<<grid, 256, smem, s>>>(a); break;
-    case 128: invert_kernel<6, 128, false><<<grid, 128, smem, s>>>(a); break;
+    case 64: invert_kernel<6, 64, false, DF><<<grid, 64, smem, s>>>(a); break;
+    case 256: invert_kernel<6, 256, false, DF><<<grid, 256, smem, s>>>(a); break;
+    case 128: invert_kernel<6, 128, false, DF><<<grid, 128, smem, s>>>(a); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
+}
+
+cudaError_t launch_invert(const InvertArgs& a, int nf, int grid, int block, size_t smem,
+                          cudaStream_t s) {
+  if (nf != 6) return cudaErrorInvalidValue;
+  return a.fast_solve ? launch_invert_t<true>(a, grid, block, smem, s)
+                      : launch_invert_t<false>(a, grid, block, smem, s);
 }
 
 }  // namespace vfisv

@@ -93,6 +93,7 @@ extern "C" int vfisv_invert_noalloc(const float* obs, const float* weights,
   if (nfilt != 6) return VFISV_E_UNSUPPORTED;
   if (cfg->restarts != 0) return VFISV_E_UNSUPPORTED;  // restart state is not in the fixed array
   if (cfg->wfa_pol != 0.0) return VFISV_E_UNSUPPORTED;  // the weak-field start needs a buffer
+  if (cfg->fast_solve != 0 && cfg->fast_solve != 1) return VFISV_E_ARG;
   if (!(cfg->hess_reuse >= 0) || !isfinite(cfg->hess_reuse)) return VFISV_E_ARG;
   if (cfg->max_iter < 0 || (cfg->free_mask & ~0x1FFu) || !(cfg->conv_rtol >= 0) ||
       !(cfg->conv_eps >= 0) || !(cfg->eps0 > 0) || !isfinite(cfg->eps0) ||
@@ -109,7 +110,8 @@ extern "C" int vfisv_invert_noalloc(const float* obs, const float* weights,
   int64_t nslots = 0;
   int grid = 0, block = 128;
   size_t smem = 0;
-  if (invert_slots(nfilt, nlam, npix, 0, &nslots, &grid, &block, &smem) != cudaSuccess) {
+  if (invert_slots(nfilt, nlam, npix, 0, cfg->fast_solve, &nslots, &grid, &block, &smem) !=
+      cudaSuccess) {
     cudaGetLastError();
     return VFISV_E_CUDA;
   }
@@ -153,9 +155,11 @@ extern "C" int vfisv_invert_noalloc(const float* obs, const float* weights,
   a.conv_eps = cfg->conv_eps;
   a.eps0 = cfg->eps0;
   a.hess_reuse = cfg->hess_reuse;
+  a.fast_solve = cfg->fast_solve;
   if (launch_invert(a, nfilt, grid, block, smem, s) != cudaSuccess) return VFISV_E_CUDA;
   if (cov_out &&
-      launch_covariance(cov_out, status_out, npix, nullptr, cfg->free_mask, s) != cudaSuccess)
+      launch_covariance(cov_out, status_out, npix, nullptr, cfg->free_mask, cfg->fast_solve, s) !=
+          cudaSuccess)
     return VFISV_E_CUDA;
   return VFISV_OK;
 }

@@ -6,7 +6,7 @@ The map has the uniform parameter distributions of the 1024x1024 workload
 synthesised by the library itself.  Prints one JSON line with the time of
 the timed inversion (CUDA events, after --warmup untimed ones).
 
-    python -m paper_0901_2702_gb300.lm_bench --npix 262144 --no-cov
+    python -m paper_0901_2702_gb300.lm_bench --npix 262144 --no-cov [--fast-solve]
 """
 from __future__ import annotations
 
@@ -26,6 +26,7 @@ def main():
     ap.add_argument("--no-cov", action="store_true", help="skip the covariance output")
     ap.add_argument("--warmup", type=int, default=1)
     ap.add_argument("--max-iter", type=int, default=50)
+    ap.add_argument("--fast-solve", action="store_true", help="double-float solve (fast_solve=1)")
     args = ap.parse_args()
 
     import numpy as np
@@ -46,7 +47,7 @@ def main():
     sig = 1e-3 * (p[:, 7] + p[:, 8])[:, None]
     obs = (syn + sig * t32(W.noise(n, 24, args.seed))).contiguous()
     w = (1.0 / (sig * sig)).expand(n, 24).contiguous()
-    cfg = {"max_iter": args.max_iter}
+    cfg = {"max_iter": args.max_iter, "fast_solve": int(args.fast_solve)}
     for _ in range(args.warmup):
         v.vfisv_invert(h, obs, w, tf, tx, line, config=cfg, want_cov=not args.no_cov)
     torch.cuda.synchronize()
@@ -59,6 +60,7 @@ def main():
     v.vfisv_check(h)
     st = r["status"]
     print(json.dumps({"npix": n, "ms": e0.elapsed_time(e1), "cov": not args.no_cov,
+                      "fast_solve": bool(args.fast_solve),
                       "mean_iters": r["iters"].float().mean().item(),
                       "passes": int(r["iters"].sum().item()) + n,
                       "converged": ((st == 0) | (st == 2)).float().mean().item()}))
