@@ -183,7 +183,9 @@ struct WsLayout {
 
 WsLayout layout(int nf, int nlam, int64_t nslots, bool restarts) {
   WsLayout L;
-  L.scratch = L.table + up((size_t)table_floats(nf, nlam) * sizeof(float));
+  size_t tb = (size_t)table_floats(nf, nlam) * sizeof(float);
+  if (nf > 8 && wide_table_bytes(nf, nlam) > tb) tb = wide_table_bytes(nf, nlam);
+  L.scratch = L.table + up(tb);
   L.rs = L.scratch + up((size_t)kScratchPerSlot * (size_t)nslots * sizeof(float));
   L.total = L.rs + (restarts ? up(kRsBytesPerSlot * (size_t)nslots) : 0);
   return L;
@@ -218,7 +220,10 @@ int check_invert_args(vfisv_handle* h, const float* obs, const float* weights,
       !iters_out || !status_out || !line_ok(line))
     return VFISV_E_ARG;
   if (npix < 0 || nfilt < 1 || nlam < 1 || nlam > 4096) return VFISV_E_SIZE;
-  if (nfilt != 6) return VFISV_E_UNSUPPORTED;
+  if (nfilt != 6 && !(nfilt > 8 && wide_supported(nfilt, nlam))) return VFISV_E_UNSUPPORTED;
+  if (nfilt > 8 && cfg &&
+      (cfg->restarts || cfg->hess_reuse != 0.0 || cfg->wfa_pol != 0.0 || cfg->fast_solve))
+    return VFISV_E_UNSUPPORTED;  // options of the filter-position kernel only
   return check_config(cfg, nfilt);
 }
 
@@ -232,9 +237,58 @@ struct DevInvert {
 
 // Pack the filter table, zero the work queue, run the persistent LM kernel
 // and the batched covariance, all on stream s.
+// Many narrow instrument profiles (spectrograph-shaped inputs): the
+// warp-per-pixel kernel, which also writes the covariance.
+int invert_device_wide(vfisv_handle* h, const DevInvert& d, int nfilt, int nlam,
+                       const vfisv_line* line, const vfisv_config* cfg, int64_t npix,
+                       const int64_t* npix_dev, cudaStream_t s) {
+  WsLayout L = layout(nfilt, nlam, 0, false);
+  if (h->ws_bytes < L.total) {
+    int rc = grow(&h->ws, &h->ws_bytes, L.total);
+    if (rc) return rc;
+    if (cudaMemsetAsync(h->ws, 0, 64, s) != cudaSuccess) return VFISV_E_CUDA;
+  }
+  char* ws = (char*)h->ws;
+  float* table = (float*)(ws + L.table);
+  int* err = (int*)(ws + L.err);
+  if (launch_wide_pack(d.filters, nfilt, d.wl, nlam, table, err, s) != cudaSuccess)
+    return VFISV_E_CUDA;
+  if (cudaMemsetAsync(ws + L.queue, 0, sizeof(unsigned long long), s) != cudaSuccess)
+    return VFISV_E_CUDA;
+  InvertArgs a;
+  a.obs = d.obs;
+  a.w = d.w;
+  a.w_stride = d.w_stride;
+  a.init = d.init;
+  a.table = table;
+  a.nlam = nlam;
+  a.npix = npix;
+  a.npix_dev = npix_dev;
+  a.params_out = d.params;
+  a.chi2_out = d.chi2;
+  a.iters_out = d.iters;
+  a.status_out = d.status;
+  a.cov_out = d.cov;
+  a.scratch = nullptr;
+  a.nslots = 0;
+  a.queue = (unsigned long long*)(ws + L.queue);
+  a.err = err;
+  a.W = h->W;
+  a.lk = line_constants(line);
+  a.max_iter = cfg->max_iter;
+  a.free_mask = cfg->free_mask;
+  a.nfree = __builtin_popcount(cfg->free_mask);
+  a.conv_rtol = cfg->conv_rtol;
+  a.conv_eps = cfg->conv_eps;
+  a.eps0 = cfg->eps0;
+  if (launch_wide_invert(a, nfilt, s) != cudaSuccess) return VFISV_E_CUDA;
+  return VFISV_OK;
+}
+
 int invert_device(vfisv_handle* h, const DevInvert& d, int nfilt, int nlam,
                   const vfisv_line* line, const vfisv_config* cfg, int64_t npix,
                   const int64_t* npix_dev, cudaStream_t s) {
+  if (nfilt > 8) return invert_device_wide(h, d, nfilt, nlam, line, cfg, npix, npix_dev, s);
   int64_t nslots = 0;
   int grid = 0, block = h->lm_block;
   size_t smem = 0;
@@ -595,7 +649,7 @@ int vfisv_synth(vfisv_handle* h, const float* params, int64_t npix, const float*
                 float* stokes, void* stream) {
   if (!h || !params || !filters || !wl_mA || !stokes || !line_ok(line)) return VFISV_E_ARG;
   if (npix < 0 || nfilt < 1 || nlam < 1 || nlam > 4096) return VFISV_E_SIZE;
-  if (nfilt > 8) return VFISV_E_UNSUPPORTED;
+  if (nfilt > 8 && !wide_supported(nfilt, nlam)) return VFISV_E_UNSUPPORTED;
   if (npix == 0) return VFISV_OK;
   if (set_device(h)) return VFISV_E_CUDA;
   cudaStream_t s = (cudaStream_t)stream;
@@ -614,6 +668,16 @@ int vfisv_synth(vfisv_handle* h, const float* params, int64_t npix, const float*
   if (rc) return rc;
   char* ws = (char*)h->ws;
   float* table = (float*)(ws + L.table);
+  if (nfilt > 8) {  // many narrow instrument profiles: one pixel per warp
+    int* err = (int*)(ws + L.err);
+    if (launch_wide_pack((const float*)st.bufs[1].dev, nfilt, (const float*)st.bufs[2].dev, nlam,
+                         table, err, s) != cudaSuccess ||
+        launch_wide_synth((const float*)st.bufs[0].dev, npix, table, nfilt, nlam,
+                          (float*)st.bufs[3].dev, err, h->W, line_constants(line), s) !=
+            cudaSuccess)
+      return VFISV_E_CUDA;
+    return st.finish(s);
+  }
   if (launch_pack_table((const float*)st.bufs[1].dev, nfilt, (const float*)st.bufs[2].dev,
                         nlam, table, s) != cudaSuccess)
     return VFISV_E_CUDA;

@@ -185,6 +185,20 @@ cudaError_t launch_voigt_table(const Weideman& W, void* tab, cudaStream_t s);
 cudaError_t launch_voigt(int method, const Weideman& W, const void* tab, const float* a,
                          const float* u, int64_t n, float* H, float* F, cudaStream_t s);
 
+// wide.cu: inputs with many narrow instrument profiles (up to 128 samples
+// per Stokes parameter, bands of up to 32 fine points, up to 1024 fine
+// points), one pixel per warp.  The compacted table (wide_table_bytes) is
+// built by launch_wide_pack, which sets *err to VFISV_E_UNSUPPORTED when a
+// band is wider than the kernels take.
+bool wide_supported(int nf, int nlam);
+size_t wide_table_bytes(int nf, int nlam);
+cudaError_t launch_wide_pack(const float* filters, int nf, const float* wl, int nlam,
+                             float* table, int* err, cudaStream_t s);
+cudaError_t launch_wide_synth(const float* params, int64_t npix, const float* table, int nf,
+                              int nlam, float* stokes, int* err, const Weideman& W,
+                              const LineK& lk, cudaStream_t s);
+cudaError_t launch_wide_invert(const InvertArgs& a, int nf, cudaStream_t s);
+
 // prep.cu: initial models from the filtergrams (Sec. 6); `geom` is device
 // scratch of filter_geom_bytes()
 size_t filter_geom_bytes();

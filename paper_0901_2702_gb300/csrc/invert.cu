@@ -12,14 +12,11 @@
 
 #include "common.cuh"
 #include "dfloat.cuh"
+#include "solve.cuh"
 
 namespace vfisv {
 
 constexpr int kInvThreadsDefault = 128;  // pixel slots per CTA unless autotuned
-constexpr int kNP = 9;    // parameters taking part in the solve (alpha held)
-constexpr int kNPk = 45;  // packed lower triangle of a 9x9 matrix
-
-__device__ __forceinline__ int tri(int i, int j) { return i * (i + 1) / 2 + j; }  // i >= j
 
 // Compensated accumulation of a product: s + c tracks sum(a*b) to about
 // twice the working precision (TwoProduct via FMA, TwoSum).
@@ -36,156 +33,6 @@ struct Dot2 {
   }
   __device__ __forceinline__ float value() const { return s + c; }
 };
-
-// Table 2 (with the oracle's reading of its overlapping rows).
-__device__ __forceinline__ double eps_update(double e, bool success) {
-  double n;
-  if (success)
-    n = (e > 1e4) ? e / 100.0 : (e >= 1e-4 ? e / 10.0 : e / 2.0);
-  else
-    n = (e < 1e-4) ? e * 100.0 : (e <= 1e4 ? e * 2.0 : e * 10.0);
-  return fmax(n, 1e-9);  // floor: the scaled damped matrix keeps eigenvalues >= 1e-9
-}
-
-// Symmetric eigen-decomposition by cyclic Jacobi rotations, FP64; the
-// fallback when the Cholesky pivots show a (numerically) singular matrix.
-// Solves M y = b with eigenvalues below 1e-12 * max zeroed (truncated SVD
-// of a symmetric matrix), or, with b == nullptr, writes the truncated
-// pseudo-inverse into Minv.
-__device__ __noinline__ void jacobi_pinv(const double* Mp /*packed*/, const double* b,
-                                         double* y, double* Minv) {
-  double a[kNP][kNP], v[kNP][kNP];
-  for (int i = 0; i < kNP; ++i)
-    for (int j = 0; j < kNP; ++j) {
-      a[i][j] = (i >= j) ? Mp[tri(i, j)] : Mp[tri(j, i)];
-      v[i][j] = (i == j) ? 1.0 : 0.0;
-    }
-  for (int sweep = 0; sweep < 30; ++sweep) {
-    double off = 0.0, dia = 0.0;
-    for (int i = 0; i < kNP; ++i) {
-      dia += a[i][i] * a[i][i];
-      for (int j = i + 1; j < kNP; ++j) off += a[i][j] * a[i][j];
-    }
-    if (!(off > 1e-26 * dia)) break;  // off-diagonal below ~3e-13 of the diagonal
-    for (int p = 0; p < kNP - 1; ++p)
-      for (int q = p + 1; q < kNP; ++q) {
-        const double apq = a[p][q];
-        if (apq == 0.0) continue;
-        const double th = (a[q][q] - a[p][p]) / (2.0 * apq);
-        const double t = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
-        const double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
-        for (int k = 0; k < kNP; ++k) {
-          const double akp = a[k][p], akq = a[k][q];
-          a[k][p] = c * akp - s * akq;
-          a[k][q] = s * akp + c * akq;
-        }
-        for (int k = 0; k < kNP; ++k) {
-          const double apk = a[p][k], aqk = a[q][k];
-          a[p][k] = c * apk - s * aqk;
-          a[q][k] = s * apk + c * aqk;
-        }
-        for (int k = 0; k < kNP; ++k) {
-          const double vkp = v[k][p], vkq = v[k][q];
-          v[k][p] = c * vkp - s * vkq;
-          v[k][q] = s * vkp + c * vkq;
-        }
-      }
-  }
-  double lmax = 0.0;
-  for (int i = 0; i < kNP; ++i) lmax = fmax(lmax, fabs(a[i][i]));
-  double linv[kNP];
-  for (int i = 0; i < kNP; ++i) {
-    const double l = fabs(a[i][i]);
-    linv[i] = (l > 1e-12 * lmax && l > 0.0) ? 1.0 / a[i][i] : 0.0;
-  }
-  if (b) {
-    double t[kNP];
-    for (int i = 0; i < kNP; ++i) {
-      double s = 0.0;
-      for (int k = 0; k < kNP; ++k) s += v[k][i] * b[k];
-      t[i] = s * linv[i];
-    }
-    for (int k = 0; k < kNP; ++k) {
-      double s = 0.0;
-      for (int i = 0; i < kNP; ++i) s += v[k][i] * t[i];
-      y[k] = s;
-    }
-  } else {
-    for (int i = 0; i < kNP; ++i)
-      for (int j = 0; j <= i; ++j) {
-        double s = 0.0;
-        for (int k = 0; k < kNP; ++k) s += v[i][k] * linv[k] * v[j][k];
-        Minv[tri(i, j)] = s;
-      }
-  }
-}
-
-// In-place Cholesky of a packed 9x9 matrix; false if a pivot is not
-// comfortably positive (the matrix has unit-scale diagonal here).
-__device__ __forceinline__ bool cholesky9(double (&L)[kNPk], double (&ri)[kNP]) {
-#pragma unroll
-  for (int j = 0; j < kNP; ++j) {
-    double d = L[tri(j, j)];
-#pragma unroll
-    for (int k = 0; k < j; ++k) d = fma(-L[tri(j, k)], L[tri(j, k)], d);
-    if (!(d > 1e-10)) return false;
-    const double r = rsqrt(d);
-    ri[j] = r;
-    L[tri(j, j)] = d * r;
-#pragma unroll
-    for (int i = j + 1; i < kNP; ++i) {
-      double s = L[tri(i, j)];
-#pragma unroll
-      for (int k = 0; k < j; ++k) s = fma(-L[tri(i, k)], L[tri(j, k)], s);
-      L[tri(i, j)] = s * r;
-    }
-  }
-  return true;
-}
-
-// Forward and back substitution with the factor and its reciprocal pivots.
-__device__ __forceinline__ void chol_solve9(const double (&L)[kNPk], const double (&ri)[kNP],
-                                            double (&x)[kNP]) {
-#pragma unroll
-  for (int i = 0; i < kNP; ++i) {
-    double s = x[i];
-#pragma unroll
-    for (int k = 0; k < i; ++k) s = fma(-L[tri(i, k)], x[k], s);
-    x[i] = s * ri[i];
-  }
-#pragma unroll
-  for (int i = kNP - 1; i >= 0; --i) {
-    double s = x[i];
-#pragma unroll
-    for (int k = i + 1; k < kNP; ++k) s = fma(-L[tri(k, i)], x[k], s);
-    x[i] = s * ri[i];
-  }
-}
-
-// Jacobi-scaled matrix of the stored normal equations: returns the scale
-// s_i = diag^-1/2 (0 for held parameters) and fills Mx = D^-1/2 A D^-1/2 +
-// eps I on free parameters, identity rows/columns on held ones.
-__device__ __forceinline__ void scaled_system(const float* scr, int64_t ns, uint32_t free_mask,
-                                              double eps, double (&Mx)[kNPk],
-                                              double (&sc)[kNP], bool (&held)[kNP]) {
-#pragma unroll
-  for (int i = 0; i < kNP; ++i) {
-    const double d = (double)scr[(int64_t)tri(i, i) * ns];
-    held[i] = !((free_mask >> i) & 1u) || !(d > 0.0) || !isfinite(d);
-    sc[i] = held[i] ? 0.0 : rsqrt(d);
-  }
-#pragma unroll
-  for (int i = 0; i < kNP; ++i)
-#pragma unroll
-    for (int j = 0; j <= i; ++j) {
-      double m;
-      if (i == j)
-        m = held[i] ? 1.0 : 1.0 + eps;
-      else
-        m = (held[i] || held[j]) ? 0.0 : (double)scr[(int64_t)tri(i, j) * ns] * sc[i] * sc[j];
-      Mx[tri(i, j)] = m;
-    }
-}
 
 // The same factorisation and solve in double-float arithmetic (the fast
 // path of the damped step; FP64 is kept for the rare singular fallback).
@@ -226,66 +73,6 @@ __device__ __forceinline__ void chol_solve9_df(const dfl (&L)[kNPk], const dfl (
     for (int k = i + 1; k < kNP; ++k) t = df_fma(df_neg(L[tri(k, i)]), x[k], t);
     x[i] = df_mul(t, ri[i]);
   }
-}
-
-// Eq. 5 with the Marquardt diagonal (Eq. 4): delta = (A + eps diag A)^-1 g,
-// Jacobi-scaled, in FP64 (the default precision of the solve).
-__device__ __noinline__ void damped_step_fp64(const float* scr, int64_t ns, uint32_t free_mask, double eps,
-                            double (&delta)[kNP]) {
-  double L[kNPk], sc[kNP];
-  bool held[kNP];
-  scaled_system(scr, ns, free_mask, eps, L, sc, held);
-  double y[kNP];
-#pragma unroll
-  for (int i = 0; i < kNP; ++i)
-    y[i] = held[i] ? 0.0 : (double)scr[(int64_t)(kNPk + i) * ns] * sc[i];
-  double ri[kNP];
-  if (cholesky9(L, ri)) {
-    chol_solve9(L, ri, y);
-  } else {
-    // rebuild the scaled matrix (the factorisation overwrote it)
-    scaled_system(scr, ns, free_mask, eps, L, sc, held);
-    double b[kNP];
-#pragma unroll
-    for (int i = 0; i < kNP; ++i) b[i] = y[i];
-    jacobi_pinv(L, b, y, nullptr);
-  }
-#pragma unroll
-  for (int i = 0; i < kNP; ++i) delta[i] = held[i] ? 0.0 : sc[i] * y[i];
-}
-
-// Covariance (J^T W J)^+ at the final model, in parameter units, from the
-// packed J^T W J at scr[e * ns].  Reads everything before writing `out`, so
-// `out` may hold the packed matrix itself.  With try_only, returns false
-// without writing when the Cholesky factorisation fails (the caller then
-// runs the eigen-decomposition path for that pixel).
-__device__ __noinline__ bool covariance_fp64(const float* scr, int64_t ns, uint32_t free_mask,
-                                        float* out, bool try_only) {
-  double L[kNPk], sc[kNP];
-  bool held[kNP];
-  scaled_system(scr, ns, free_mask, 0.0, L, sc, held);
-  double P[kNPk], ri[kNP];
-  if (cholesky9(L, ri)) {
-    for (int j = 0; j < kNP; ++j) {
-      double x[kNP];
-#pragma unroll
-      for (int i = 0; i < kNP; ++i) x[i] = (i == j) ? 1.0 : 0.0;
-      chol_solve9(L, ri, x);
-      for (int i = j; i < kNP; ++i) P[tri(i, j)] = x[i];
-    }
-  } else {
-    if (try_only) return false;
-    scaled_system(scr, ns, free_mask, 0.0, L, sc, held);
-    jacobi_pinv(L, nullptr, nullptr, P);
-  }
-  for (int i = 0; i < 10; ++i)
-    for (int j = 0; j < 10; ++j) {
-      float v = 0.0f;
-      if (i < kNP && j < kNP && !held[i] && !held[j])
-        v = (float)(sc[i] * sc[j] * ((i >= j) ? P[tri(i, j)] : P[tri(j, i)]));
-      out[i * 10 + j] = v;
-    }
-  return true;
 }
 
 // The same step in double-float (the fast_solve option); the result is

@@ -18,6 +18,12 @@ Workloads (all parameters in the C-ABI parameter order, see ``PARAM_NAMES``):
   smoothly varying inclination and azimuth).
 * ``noise`` -- Gaussian noise of sigma = rel * I_c per observable, where the
   continuum I_c = S0 + mu*S1 of the generating model is passed in.
+* ``serving_maps`` / ``serving_map_params`` -- the uneven serving mix: map
+  sides log-uniform in [32, 2048], noise log-uniform in [3e-4, 3e-3] I_c,
+  each map a disk with the full-disk distributions; half of the maps are
+  spectrograph-shaped (``spectrograph_grid``, ``spectrograph_instrument``:
+  112 samples 21.5 mA apart, Gaussian instrument FWHM 25 mA, synthesis grid
+  4x finer, Fe I 6302.5 A).
 
 The HMI-like instrument: 149 wavelength samples at 10 mA spacing over
 +-740 mA about line centre (HMI tunes over the Fe I 6173 A line, paper
@@ -203,3 +209,40 @@ def serving_maps(seed: int, nmaps: int = 64, side_min: int = 32, side_max: int =
     sides = np.exp(g.uniform(np.log(side_min), np.log(side_max), nmaps)).astype(int)
     sig = np.exp(g.uniform(np.log(3e-4), np.log(3e-3), nmaps))
     return sides, sig
+
+
+# Spectrograph-shaped inputs of the serving mix: the Fe I 6302.5 A line
+# sampled at 112 points 21.5 mA apart, each sample a Gaussian instrument
+# profile of FWHM 25 mA over a synthesis grid four times finer.
+SPEC_NSAMP, SPEC_STEP_mA, SPEC_FINE = 112, 21.5, 4
+
+
+def spectrograph_grid(nsamp: int = SPEC_NSAMP, step_mA: float = SPEC_STEP_mA,
+                      fine: int = SPEC_FINE):
+    """(fine synthesis grid [nsamp*fine], sample centres [nsamp]) in mA."""
+    n = nsamp * fine
+    x = (np.arange(n, dtype=np.float64) - (n - 1) / 2.0) * (step_mA / fine)
+    c = (np.arange(nsamp, dtype=np.float64) - (nsamp - 1) / 2.0) * step_mA
+    return x, c
+
+
+def spectrograph_instrument(x_mA, centres_mA, fwhm_mA: float = 25.0, cut_fwhm: float = 3.0):
+    """Gaussian instrument profiles [nsamp, nfine], truncated at cut_fwhm
+    FWHM from each centre (tail mass < 1e-11), unit sum."""
+    x = np.asarray(x_mA, dtype=np.float64)
+    rows = []
+    for c in centres_mA:
+        d = x - c
+        t = np.exp(-4.0 * np.log(2.0) * d * d / (fwhm_mA * fwhm_mA))
+        t[np.abs(d) > cut_fwhm * fwhm_mA] = 0.0
+        rows.append(t / t.sum())
+    return np.stack(rows)
+
+
+def serving_map_params(side: int, seed: int):
+    """Parameters of one serving-mix map: a disk of diameter ~side with the
+    full-disk distributions (quiet Sun and active-region blobs)."""
+    side = max(int(side), 8)
+    p, _ = full_disk_params(seed, side=side, radius=0.5 * side - 0.5,
+                            active_fraction=0.10)
+    return p
