@@ -175,6 +175,26 @@ const char* vfisv_strerror(int code);
 int vfisv_voigt(vfisv_handle* h, const float* a, const float* u, int64_t n, int32_t method,
                 float* H, float* F, void* stream);
 
+/* Many maps in one persistent launch (the uneven serving mix): the pixels of
+ * nmaps maps concatenated in obs [npix][4][nfilt], map m holding pixels
+ * map_off[m] .. map_off[m+1]-1 (map_off: host int64 [nmaps+1], map_off[0] =
+ * 0, non-decreasing, npix = map_off[nmaps]); weights [nmaps][4][nfilt] are
+ * per map (w^2/sigma^2 shared by the map's pixels).  Any nfilt vfisv_invert
+ * takes (6 filter positions, or the wide instrument path).  Outputs as
+ * vfisv_invert, plus latency_ms [nmaps] (optional): for each map, the time
+ * from the start of this call's first kernel to the retirement of the map's
+ * last pixel by the LM kernel, read from the GPU's global timer (the
+ * covariance pass that follows is not included; an empty map reads 0).
+ * The offsets are copied into a pinned buffer of the handle, which a
+ * captured graph keeps reading on every replay: a later batch call on the
+ * same handle changes what the replays see.  Host or device buffers. */
+int vfisv_invert_batch(vfisv_handle* h, const float* obs, const float* weights,
+                       const int64_t* map_off, int32_t nmaps, const float* filters,
+                       int32_t nfilt, const float* wl_mA, int32_t nlam, const vfisv_line* line,
+                       const float* init, const vfisv_config* cfg, float* params_out,
+                       float* chi2_out, int32_t* iters_out, int32_t* status_out, float* cov_out,
+                       float* latency_ms, void* stream);
+
 /* Initial models from the filtergrams (Sec. 6; the paper's methods are
  * cited, not printed -- this is one reading of them).  For each pixel of
  * obs [npix][4][nfilt] (3 <= nfilt <= 8; filters [nfilt][nlam] on wl_mA, any

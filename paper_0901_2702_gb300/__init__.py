@@ -20,7 +20,8 @@ __all__ = [
     "vfisv_strerror", "vfisv_config_default", "vfisv_nn_init", "vfisv_nn_train",
     "vfisv_nn_grad", "vfisv_nn_infer", "vfisv_invert_nn", "vfisv_graph_begin", "vfisv_graph_end",
     "vfisv_graph_launch", "vfisv_graph_destroy", "vfisv_autotune", "vfisv_voigt",
-    "vfisv_limb_weights", "vfisv_restart_models", "vfisv_init_models", "VfisvError",
+    "vfisv_limb_weights", "vfisv_restart_models", "vfisv_init_models", "vfisv_invert_batch",
+    "VfisvError",
     "library_path",
     "load",
     "NN_NBLOB", "NN_NTRAIN",
@@ -113,6 +114,10 @@ def load():
     lib.vfisv_voigt.restype = ctypes.c_int
     lib.vfisv_limb_weights.argtypes = [P, P, P, I64, I32, ctypes.c_float, P, P, P]
     lib.vfisv_limb_weights.restype = ctypes.c_int
+    lib.vfisv_invert_batch.argtypes = [P, P, P, P, I32, P, I32, P, I32,
+                                       ctypes.POINTER(vfisv_line), P, ctypes.POINTER(vfisv_config),
+                                       P, P, P, P, P, P, P]
+    lib.vfisv_invert_batch.restype = ctypes.c_int
     lib.vfisv_init_models.argtypes = [P, P, I64, P, I32, P, I32, ctypes.POINTER(vfisv_line), P,
                                       P, P]
     lib.vfisv_init_models.restype = ctypes.c_int
@@ -514,4 +519,44 @@ def vfisv_init_models(h: Handle, obs, filters, wl_mA, line, want_pol: bool = Tru
         dst = out.get(key)
         if dst is not None and not _is_torch(dst) and k is not dst:
             dst[...] = k
+    return out
+
+
+def vfisv_invert_batch(h: Handle, obs, weights, map_off, filters, wl_mA, line, init=None,
+                       config=None, want_cov=True, want_latency=True, out=None, stream=None):
+    """Inversion of many concatenated maps in one launch.
+
+    obs [npix, 4*nfilt]; weights [nmaps, 4*nfilt] per map; map_off host
+    int64 [nmaps+1] prefix offsets.  Returns vfisv_invert's outputs plus
+    latency_ms [nmaps] (per-map completion time from the call's start)."""
+    off = np.ascontiguousarray(np.asarray(map_off, dtype=np.int64))
+    nmaps = int(off.size - 1)
+    npix = int(off[-1])
+    nfilt, nlam = int(filters.shape[0]), int(filters.shape[1])
+    cfg = config if isinstance(config, vfisv_config) else vfisv_config_default(**(config or {}))
+    if out is None:
+        out = {"params": _empty(obs, (npix, 10), np.float32),
+               "chi2": _empty(obs, (npix,), np.float32),
+               "iters": _empty(obs, (npix,), np.int32),
+               "status": _empty(obs, (npix,), np.int32),
+               "cov": _empty(obs, (npix, 10, 10), np.float32) if want_cov else None,
+               "latency_ms": _empty(obs, (nmaps,), np.float32) if want_latency else None}
+    op, k1 = _ptr(obs, np.float32)
+    wp, k2 = _ptr(weights, np.float32)
+    fp, k3 = _ptr(filters, np.float32)
+    lp, k4 = _ptr(wl_mA, np.float32)
+    ip, k5 = _ptr(init, np.float32)
+    keys = ("params", "chi2", "iters", "status", "cov", "latency_ms")
+    dts = (np.float32, np.float32, np.int32, np.int32, np.float32, np.float32)
+    ptrs = [_ptr(out.get(k), dt) for k, dt in zip(keys, dts)]
+    ln = _line(line)
+    _check(load().vfisv_invert_batch(h.ptr, op, wp, off.ctypes.data, nmaps, fp, nfilt, lp, nlam,
+                                     ctypes.byref(ln), ip, ctypes.byref(cfg),
+                                     *[p for p, _ in ptrs],
+                                     ctypes.c_void_p(_stream(obs, stream))),
+           "vfisv_invert_batch")
+    for k, (_, kk) in zip(keys, ptrs):
+        dst = out.get(k)
+        if dst is not None and not _is_torch(dst) and kk is not dst:
+            dst[...] = kk
     return out

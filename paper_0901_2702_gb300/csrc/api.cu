@@ -29,6 +29,10 @@ struct vfisv_handle {
   size_t geom_bytes = 0;
   void* wfinit = nullptr;  // weak-field initial models of an inversion without init
   size_t wfinit_bytes = 0;
+  void* mapws = nullptr;   // batched maps: offsets, counters, stamps (device)
+  size_t mapws_bytes = 0;
+  int64_t* mapoff_host = nullptr;  // pinned copy of the caller's map offsets
+  size_t mapoff_host_bytes = 0;
   bool capturing = false;  // between vfisv_graph_begin and vfisv_graph_end
 };
 
@@ -233,6 +237,10 @@ struct DevInvert {
   int64_t w_stride = 0;
   float *params = nullptr, *chi2 = nullptr, *cov = nullptr;
   int32_t *iters = nullptr, *status = nullptr;
+  // batched maps (vfisv_invert_batch)
+  const int64_t* map_off = nullptr;
+  int nmaps = 0;
+  unsigned long long *map_done = nullptr, *map_t = nullptr;
 };
 
 // Pack the filter table, zero the work queue, run the persistent LM kernel
@@ -281,6 +289,10 @@ int invert_device_wide(vfisv_handle* h, const DevInvert& d, int nfilt, int nlam,
   a.conv_rtol = cfg->conv_rtol;
   a.conv_eps = cfg->conv_eps;
   a.eps0 = cfg->eps0;
+  a.map_off = d.map_off;
+  a.nmaps = d.nmaps;
+  a.map_done = d.map_done;
+  a.map_t = d.map_t;
   if (launch_wide_invert(a, nfilt, s) != cudaSuccess) return VFISV_E_CUDA;
   return VFISV_OK;
 }
@@ -348,6 +360,10 @@ int invert_device(vfisv_handle* h, const DevInvert& d, int nfilt, int nlam,
   a.conv_rtol = cfg->conv_rtol;
   a.conv_eps = cfg->conv_eps;
   a.eps0 = cfg->eps0;
+  a.map_off = d.map_off;
+  a.nmaps = d.nmaps;
+  a.map_done = d.map_done;
+  a.map_t = d.map_t;
   a.restarts = cfg->restarts;
   a.seed = cfg->seed;
   a.hess_reuse = cfg->hess_reuse;
@@ -427,6 +443,8 @@ void vfisv_destroy(vfisv_handle* h) {
   if (h->vtab) cudaFree(h->vtab);
   if (h->geom) cudaFree(h->geom);
   if (h->wfinit) cudaFree(h->wfinit);
+  if (h->mapws) cudaFree(h->mapws);
+  if (h->mapoff_host) cudaFreeHost(h->mapoff_host);
   delete h;
 }
 
@@ -822,6 +840,87 @@ int vfisv_nn_infer(vfisv_handle* h, const float* blob, const float* obs, int64_t
                    (const float*)st.bufs[1].dev, npix, (float)line->mu,
                    (float*)st.bufs[2].dev, (float*)st.bufs[3].dev, (float*)st.bufs[4].dev,
                    s) != cudaSuccess)
+    return VFISV_E_CUDA;
+  return st.finish(s);
+}
+
+int vfisv_invert_batch(vfisv_handle* h, const float* obs, const float* weights,
+                       const int64_t* map_off, int32_t nmaps, const float* filters,
+                       int32_t nfilt, const float* wl_mA, int32_t nlam, const vfisv_line* line,
+                       const float* init, const vfisv_config* cfg, float* params_out,
+                       float* chi2_out, int32_t* iters_out, int32_t* status_out, float* cov_out,
+                       float* latency_ms, void* stream) {
+  if (!map_off || nmaps < 1) return VFISV_E_ARG;
+  if (map_off[0] != 0) return VFISV_E_ARG;
+  for (int m = 0; m < nmaps; ++m)
+    if (map_off[m + 1] < map_off[m]) return VFISV_E_ARG;
+  const int64_t npix = map_off[nmaps];
+  int rc = check_invert_args(h, obs, weights, filters, nfilt, wl_mA, nlam, line, cfg, npix,
+                             params_out, chi2_out, iters_out, status_out);
+  if (rc) return rc;
+  if (set_device(h)) return VFISV_E_CUDA;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int nobs = 4 * nfilt;
+  // device: offsets [nmaps+1], completion counters [nmaps], stamps [nmaps], start stamp
+  const size_t b_off = up((size_t)(nmaps + 1) * 8), b_cnt = up((size_t)nmaps * 8);
+  if ((rc = grow(&h->mapws, &h->mapws_bytes, b_off + 2 * b_cnt + 256))) return rc;
+  const size_t hbytes = (size_t)(nmaps + 1) * 8;
+  if (h->mapoff_host_bytes < hbytes) {
+    if (t_capturing) return VFISV_E_CAPTURE;
+    if (h->mapoff_host) cudaFreeHost(h->mapoff_host);
+    h->mapoff_host = nullptr;
+    h->mapoff_host_bytes = 0;
+    if (cudaMallocHost((void**)&h->mapoff_host, hbytes) != cudaSuccess) return VFISV_E_NOMEM;
+    h->mapoff_host_bytes = hbytes;
+  }
+  // the pinned copy is read by the copy below (and by every replay of a
+  // captured graph), so the caller's array need not outlive the call; an
+  // earlier call's copy from it must be complete before it is rewritten
+  if (!t_capturing && cudaStreamSynchronize(s) != cudaSuccess) return VFISV_E_CUDA;
+  memcpy(h->mapoff_host, map_off, hbytes);
+  char* mw = (char*)h->mapws;
+  int64_t* off_d = (int64_t*)mw;
+  unsigned long long* done = (unsigned long long*)(mw + b_off);
+  unsigned long long* tdone = (unsigned long long*)(mw + b_off + b_cnt);
+  unsigned long long* t0 = (unsigned long long*)(mw + b_off + 2 * b_cnt);
+  if (cudaMemcpyAsync(off_d, h->mapoff_host, hbytes, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemsetAsync(done, 0, b_cnt, s) != cudaSuccess ||
+      cudaMemsetAsync(tdone, 0, b_cnt, s) != cudaSuccess)
+    return VFISV_E_CUDA;
+  if (npix == 0) return VFISV_OK;
+  Staging st;
+  st.add(obs, (size_t)npix * nobs * sizeof(float), false);
+  st.add(weights, (size_t)nmaps * nobs * sizeof(float), false);
+  st.add(filters, (size_t)nfilt * nlam * sizeof(float), false);
+  st.add(wl_mA, (size_t)nlam * sizeof(float), false);
+  st.add(init, init ? (size_t)npix * 10 * sizeof(float) : 0, false);
+  st.add(params_out, (size_t)npix * 10 * sizeof(float), true);
+  st.add(chi2_out, (size_t)npix * sizeof(float), true);
+  st.add(iters_out, (size_t)npix * sizeof(int32_t), true);
+  st.add(status_out, (size_t)npix * sizeof(int32_t), true);
+  st.add(cov_out, cov_out ? (size_t)npix * 100 * sizeof(float) : 0, true);
+  st.add(latency_ms, latency_ms ? (size_t)nmaps * sizeof(float) : 0, true);
+  if ((rc = st.prepare(h, s))) return rc;
+  if (launch_stamp(t0, s) != cudaSuccess) return VFISV_E_CUDA;
+  DevInvert d;
+  d.obs = (const float*)st.bufs[0].dev;
+  d.w = (const float*)st.bufs[1].dev;
+  d.w_stride = 0;
+  d.filters = (const float*)st.bufs[2].dev;
+  d.wl = (const float*)st.bufs[3].dev;
+  d.init = (const float*)st.bufs[4].dev;
+  d.params = (float*)st.bufs[5].dev;
+  d.chi2 = (float*)st.bufs[6].dev;
+  d.iters = (int32_t*)st.bufs[7].dev;
+  d.status = (int32_t*)st.bufs[8].dev;
+  d.cov = (float*)st.bufs[9].dev;
+  d.map_off = off_d;
+  d.nmaps = nmaps;
+  d.map_done = done;
+  d.map_t = tdone;
+  if ((rc = invert_device(h, d, nfilt, nlam, line, cfg, npix, nullptr, s))) return rc;
+  if (latency_ms && launch_map_latency(tdone, t0, nmaps, (float*)st.bufs[10].dev, s) !=
+                        cudaSuccess)
     return VFISV_E_CUDA;
   return st.finish(s);
 }

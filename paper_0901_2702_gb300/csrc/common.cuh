@@ -136,12 +136,50 @@ struct InvertArgs {
   double eps0;
   double hess_reuse = 0.0;   // Hessian reuse threshold (Sec. 4.4), 0 = off
   int fast_solve = 0;        // 1: double-float solve, compensated FP32 chi2
+  // batched maps (the serving mix): map m holds pixels map_off[m] ..
+  // map_off[m+1]-1 and its weight row w + m * nobs; each map's completion
+  // (global timer, ns) goes to map_t[m] when its last pixel retires
+  const int64_t* map_off = nullptr;
+  int nmaps = 0;
+  unsigned long long* map_done = nullptr;
+  unsigned long long* map_t = nullptr;
   int restarts = 0;          // randomised restarts (Sec. 4.2): trigger bit mask, 0 = off
   uint64_t seed = 0;         // key of the restart perturbations
   char* rs_state = nullptr;  // restarts: per-slot state, layout RestartState
 };
 
 constexpr int kScratchPerSlot = 45 + 9;  // packed J^T W J and J^T W r
+
+// Map of a pixel in a batch (binary search over the prefix offsets).
+__device__ __forceinline__ int map_of(const int64_t* off, int nmaps, int64_t pix) {
+  int lo = 0, hi = nmaps;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (__ldg(off + mid) <= pix) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ const float* weight_row(const InvertArgs& A, int64_t pix, int nobs) {
+  if (A.map_off) return A.w + (int64_t)map_of(A.map_off, A.nmaps, pix) * nobs;
+  return A.w + pix * A.w_stride;
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Count a retired pixel of a batch; the map's last one stamps its time.
+__device__ __forceinline__ void map_retired(const InvertArgs& A, int64_t pix) {
+  if (!A.map_done) return;
+  const int m = map_of(A.map_off, A.nmaps, pix);
+  const unsigned long long size =
+      (unsigned long long)(__ldg(A.map_off + m + 1) - __ldg(A.map_off + m));
+  if (atomicAdd(A.map_done + m, 1ull) + 1ull == size) A.map_t[m] = global_ns();
+}
 
 // Per-slot state of the randomised restarts, structure of arrays over the
 // slots: FP64 [2][ns] (best chi2, initial chi2), FP32 [64][ns] (J^T W J,
@@ -206,6 +244,11 @@ cudaError_t launch_weak_field(const float* obs, int64_t npix, const int64_t* npi
                               const float* filters, int nf, const float* wl, int nlam,
                               const LineK& lk, int mode, float pol_thr, void* geom, float* init,
                               float* pol_out, cudaStream_t s);
+// prep.cu: batched maps -- a call's start stamp (global timer, ns) and the
+// per-map latency in ms from it
+cudaError_t launch_stamp(unsigned long long* t, cudaStream_t s);
+cudaError_t launch_map_latency(const unsigned long long* t_done, const unsigned long long* t0,
+                               int nmaps, float* ms, cudaStream_t s);
 // prep.cu: Eq. 14-15 weights
 cudaError_t launch_limb_weights(const float* obs, const float* mu, int64_t npix, int nf,
                                 float ic0, const float* sigma4, float* w, cudaStream_t s);

@@ -326,7 +326,7 @@ __global__ void __launch_bounds__(BS, 1) invert_kernel(InvertArgs A) {
         fresh = true;
         sPix[tid] = pix;
         const float* o = A.obs + pix * NOBS;
-        const float* wv = A.w + pix * A.w_stride;
+        const float* wv = weight_row(A, pix, NOBS);
         bool bad = false;
         float wsum = 0.0f, ic = -INFINITY;
 #pragma unroll
@@ -361,6 +361,7 @@ __global__ void __launch_bounds__(BS, 1) invert_kernel(InvertArgs A) {
           A.status_out[pix] = VFISV_PIX_BAD_INPUT;
           if (A.cov_out)
             for (int j = 0; j < 100; ++j) A.cov_out[pix * 100 + j] = 0.0f;
+          map_retired(A, pix);
           sPix[tid] = -1;
           continue;
         }
@@ -416,7 +417,7 @@ __global__ void __launch_bounds__(BS, 1) invert_kernel(InvertArgs A) {
 
     const long long pix = sPix[tid];
     const float* o = A.obs + pix * NOBS;
-    const float* wv = A.w + pix * A.w_stride;
+    const float* wv = weight_row(A, pix, NOBS);
 
     // ---- model, residual and chi-square (Eq. 1, FP64) ----
     float c2p, s2p;
@@ -638,6 +639,7 @@ __global__ void __launch_bounds__(BS, 1) invert_kernel(InvertArgs A) {
           }
         }
       }
+      map_retired(A, pix);
       sPix[tid] = -1;
     }
   }

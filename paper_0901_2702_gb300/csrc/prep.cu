@@ -195,6 +195,29 @@ __global__ void weak_field_kernel(const float* __restrict__ obs, int64_t npix,
   for (int j = 0; j < 10; ++j) init[p * 10 + j] = m[j];
 }
 
+// Batched maps: the start stamp of a call and each map's latency from it.
+__global__ void stamp_kernel(unsigned long long* t) { *t = global_ns(); }
+
+__global__ void map_latency_kernel(const unsigned long long* __restrict__ t_done,
+                                   const unsigned long long* __restrict__ t0, int nmaps,
+                                   float* __restrict__ ms) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= nmaps) return;
+  const unsigned long long t = t_done[m];
+  ms[m] = (t >= *t0) ? (float)((double)(t - *t0) * 1e-6) : 0.0f;  // empty maps: 0
+}
+
+cudaError_t launch_stamp(unsigned long long* t, cudaStream_t s) {
+  stamp_kernel<<<1, 1, 0, s>>>(t);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_map_latency(const unsigned long long* t_done, const unsigned long long* t0,
+                               int nmaps, float* ms, cudaStream_t s) {
+  map_latency_kernel<<<(nmaps + 127) / 128, 128, 0, s>>>(t_done, t0, nmaps, ms);
+  return cudaGetLastError();
+}
+
 size_t filter_geom_bytes() { return sizeof(FilterGeom); }
 
 cudaError_t launch_weak_field(const float* obs, int64_t npix, const int64_t* npix_dev,

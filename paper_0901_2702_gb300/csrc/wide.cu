@@ -242,7 +242,7 @@ __global__ void __launch_bounds__(32 * kWWarps, 1) wide_invert_kernel(InvertArgs
       if (pix >= npix) break;
       fresh = true;
       const float* o = A.obs + pix * nobs;
-      const float* wv = A.w + pix * A.w_stride;
+      const float* wv = weight_row(A, pix, nobs);
       bool bad = false;
       float wsum = 0.0f, ic = -INFINITY;
       for (int j = lane; j < nobs; j += 32) {
@@ -285,6 +285,7 @@ __global__ void __launch_bounds__(32 * kWWarps, 1) wide_invert_kernel(InvertArgs
           A.chi2_out[pix] = 0.0f;
           A.iters_out[pix] = 0;
           A.status_out[pix] = VFISV_PIX_BAD_INPUT;
+          map_retired(A, pix);
         }
         if (A.cov_out)
           for (int j = lane; j < 100; j += 32) A.cov_out[pix * 100 + j] = 0.0f;
@@ -314,7 +315,7 @@ __global__ void __launch_bounds__(32 * kWWarps, 1) wide_invert_kernel(InvertArgs
                     A.nlam, vbuf, lane, acc);
     const long long pix = S.pix;
     const float* o = A.obs + pix * nobs;
-    const float* wv = A.w + pix * A.w_stride;
+    const float* wv = weight_row(A, pix, nobs);
     float c2p, s2p;
     sincosf(2.0f * Mt[2] * kDeg, &s2p, &c2p);
     const float mus1 = mu * Mt[8];
@@ -450,6 +451,7 @@ __global__ void __launch_bounds__(32 * kWWarps, 1) wide_invert_kernel(InvertArgs
             covariance_fp64(S.A, 1, A.free_mask, cv, false);
           }
         }
+        map_retired(A, pix);
         S.pix = -1;
       }
       __syncwarp();
