@@ -334,10 +334,12 @@ def vfisv_nn_grad(h: Handle, blob, obs, params, stream=None):
     return loss, grad
 
 
-def vfisv_nn_infer(h: Handle, blob, obs, line, want_conf=True, want_raw=False, stream=None):
-    """Initial models [npix, 10] (and confidence / raw outputs) from the network."""
+def vfisv_nn_infer(h: Handle, blob, obs, line, want_conf=True, want_raw=False, init=None,
+                   stream=None):
+    """Initial models [npix, 10] (and confidence / raw outputs) from the network;
+    ``init`` may be a preallocated output (needed inside a graph capture)."""
     n = int(obs.shape[0])
-    init = _empty(obs, (n, 10), np.float32)
+    init = _empty(obs, (n, 10), np.float32) if init is None else init
     conf = _empty(obs, (n,), np.float32) if want_conf else None
     raw = _empty(obs, (n, NN_NOUT), np.float32) if want_raw else None
     bp, kb = _ptr(blob, np.float32)
@@ -348,6 +350,9 @@ def vfisv_nn_infer(h: Handle, blob, obs, line, want_conf=True, want_raw=False, s
     ln = _line(line)
     _check(load().vfisv_nn_infer(h.ptr, bp, op, n, ctypes.byref(ln), ip, cp, rp,
                                  ctypes.c_void_p(_stream(obs, stream))), "vfisv_nn_infer")
+    for dst, k in ((init, ki), (conf, kc), (raw, kr)):
+        if dst is not None and not _is_torch(dst) and k is not dst:
+            dst[...] = k
     return {"init": init, "conf": conf, "raw": raw}
 
 

@@ -246,7 +246,7 @@ struct DevInvert {
 // Pack the filter table, zero the work queue, run the persistent LM kernel
 // and the batched covariance, all on stream s.
 // Many narrow instrument profiles (spectrograph-shaped inputs): the
-// warp-per-pixel kernel, which also writes the covariance.
+// warp-per-pixel kernel, then the batched covariance.
 int invert_device_wide(vfisv_handle* h, const DevInvert& d, int nfilt, int nlam,
                        const vfisv_line* line, const vfisv_config* cfg, int64_t npix,
                        const int64_t* npix_dev, cudaStream_t s) {
@@ -294,6 +294,10 @@ int invert_device_wide(vfisv_handle* h, const DevInvert& d, int nfilt, int nlam,
   a.map_done = d.map_done;
   a.map_t = d.map_t;
   if (launch_wide_invert(a, nfilt, s) != cudaSuccess) return VFISV_E_CUDA;
+  // the kernel parks each pixel's J^T W J in its covariance row
+  if (d.cov && launch_covariance(d.cov, d.status, npix, npix_dev, cfg->free_mask, 0, s) !=
+                   cudaSuccess)
+    return VFISV_E_CUDA;
   return VFISV_OK;
 }
 

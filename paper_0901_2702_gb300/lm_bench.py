@@ -7,6 +7,7 @@ synthesised by the library itself.  Prints one JSON line with the time of
 the timed inversion (CUDA events, after --warmup untimed ones).
 
     python -m paper_0901_2702_gb300.lm_bench --npix 262144 --no-cov [--fast-solve]
+    python -m paper_0901_2702_gb300.lm_bench --npix 16384 --no-cov --spectrograph
 """
 from __future__ import annotations
 
@@ -27,6 +28,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=1)
     ap.add_argument("--max-iter", type=int, default=50)
     ap.add_argument("--fast-solve", action="store_true", help="double-float solve (fast_solve=1)")
+    ap.add_argument("--spectrograph", action="store_true",
+                    help="spectrograph-shaped inputs (112 samples x 4 Stokes, Fe I 6302.5 A)")
     args = ap.parse_args()
 
     import numpy as np
@@ -37,16 +40,22 @@ def main():
 
     dev = torch.device("cuda:0")
     h = v.vfisv_create(0)
-    line = W.FE6173
-    x = W.wavelength_grid()
     t32 = lambda a: torch.tensor(np.asarray(a, dtype=np.float32), device=dev)  # noqa: E731
-    tf, tx = t32(W.hmi_filters(x)), t32(x)
+    if args.spectrograph:
+        line = W.FE6302
+        x, c = W.spectrograph_grid()
+        tf, tx = t32(W.spectrograph_instrument(x, c)), t32(x)
+    else:
+        line = W.FE6173
+        x = W.wavelength_grid()
+        tf, tx = t32(W.hmi_filters(x)), t32(x)
+    nobs = 4 * tf.shape[0]
     n = args.npix
     p = t32(W.quiet_and_active_params(n, args.seed))
-    syn = v.vfisv_synth(h, p, tf, tx, line).reshape(n, 24)
+    syn = v.vfisv_synth(h, p, tf, tx, line).reshape(n, nobs)
     sig = 1e-3 * (p[:, 7] + p[:, 8])[:, None]
-    obs = (syn + sig * t32(W.noise(n, 24, args.seed))).contiguous()
-    w = (1.0 / (sig * sig)).expand(n, 24).contiguous()
+    obs = (syn + sig * t32(W.noise(n, nobs, args.seed))).contiguous()
+    w = (1.0 / (sig * sig)).expand(n, nobs).contiguous()
     cfg = {"max_iter": args.max_iter, "fast_solve": int(args.fast_solve)}
     for _ in range(args.warmup):
         v.vfisv_invert(h, obs, w, tf, tx, line, config=cfg, want_cov=not args.no_cov)
@@ -60,7 +69,7 @@ def main():
     v.vfisv_check(h)
     st = r["status"]
     print(json.dumps({"npix": n, "ms": e0.elapsed_time(e1), "cov": not args.no_cov,
-                      "fast_solve": bool(args.fast_solve),
+                      "fast_solve": bool(args.fast_solve), "spectrograph": args.spectrograph,
                       "mean_iters": r["iters"].float().mean().item(),
                       "passes": int(r["iters"].sum().item()) + n,
                       "converged": ((st == 0) | (st == 2)).float().mean().item()}))
