@@ -39,7 +39,10 @@ Readings of points the paper leaves open or prints garbled:
 * Bounds after each step: B < 0 -> (-B, 180 - gamma); gamma reflected into
   [0, 180] (the profiles depend on sin^2 gamma and cos gamma only);
   psi mod 180; B <= 6000 G; eta0 in [0.01, 500]; dlambdaD in [5, 150] mA;
-  a in [0, 5]; |v| <= 20 km/s; S0, S1 in [0, 2].
+  a in [0, 5]; |v| <= 20 km/s; S0, S1 in [0, 2]; alpha in [0, 1].
+* The filling factor alpha (Sec. 2) is held at 1 unless bit 9 of
+  ``free_mask`` is set; free, it joins the solve with the column
+  S_mag - S_mag(B=0) (the other columns mixed alpha : 1 - alpha).
 * Covariance: (J^T W J)^+ at the final model (eps = 0), computed in the
   Jacobi-scaled form with the same SVD truncation, zero for held
   parameters.
@@ -127,6 +130,7 @@ def apply_bounds(m):
     m[:, me.VLOS] = np.clip(m[:, me.VLOS], -20.0, 20.0)
     m[:, me.S0] = np.clip(m[:, me.S0], 0.0, 2.0)
     m[:, me.S1] = np.clip(m[:, me.S1], 0.0, 2.0)
+    m[:, me.ALPHA] = np.clip(m[:, me.ALPHA], 0.0, 1.0)
     return m
 
 
@@ -246,13 +250,14 @@ def invert(obs, w, filters, x, line, init=None, max_iter=50, conv_rtol=1e-4,
         m = np.asarray(init, dtype=np.float64).copy()
         bad |= ~np.isfinite(m).all(1)
         m = np.where(np.isfinite(m), m, STANDARD_GUESS[None, :])
-    m[:, me.ALPHA] = 1.0
+    if not free[me.ALPHA]:
+        m[:, me.ALPHA] = 1.0          # the filling factor held at 1
     m = apply_bounds(m)
     obs_s = np.where(bad[:, None], 0.0, obs)
     w_s = np.where(bad[:, None], 0.0, w)
 
     def model(mm, jac):
-        out = me.synth(mm, filters, x, line, jacobian=jac)
+        out = me.synth(mm, filters, x, line, jacobian=jac, alpha_jacobian=bool(free[me.ALPHA]))
         if jac:
             s, J = out
             return s.reshape(len(mm), -1), J.reshape(len(mm), n_obs, NPAR)

@@ -173,19 +173,22 @@ def _magnetic_unit(p, x, line, with_derivs):
     return y, dy
 
 
-def synth(params, filters, x, line, jacobian: bool = False):
+def synth(params, filters, x, line, jacobian: bool = False, alpha_jacobian: bool = False):
     """Filtered Stokes vector [npix, 4, nfilt] (and Jacobian [npix, 4, nfilt, 10]).
 
     S(x) = alpha * S_mag(x) + (1 - alpha) * S_mag(x; B=0) with
     S_mag = S0 e0 + mu S1 K^{-1} e0, then the filter convolution
     S_jk = sum_i T_k(x_i) S_j(x_i) (the instrument's 6 tuning positions).
+    The B = 0 profile is computed when some alpha differs from 1, or with
+    ``alpha_jacobian`` (the alpha column, S_mag - S_mag(B=0), needs it at
+    alpha = 1 too); otherwise the alpha column is not meaningful.
     """
     p = np.atleast_2d(np.asarray(params, dtype=np.float64))
     T = np.asarray(filters, dtype=np.float64)
     mu = float(line.get("mu", 1.0))
     al = p[:, ALPHA]
     y, dy = _magnetic_unit(p, x, line, jacobian)
-    needs_nm = np.any(al != 1.0)
+    needs_nm = np.any(al != 1.0) or (jacobian and alpha_jacobian)
     if needs_nm:
         pn = p.copy()
         pn[:, B] = 0.0

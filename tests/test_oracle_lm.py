@@ -191,3 +191,31 @@ def test_hessian_reuse_off_and_on():
     # with a stale matrix the last steps converge linearly, not quadratically,
     # so the stopping test (1e-9 per step) can end a few steps apart
     np.testing.assert_allclose(d["chi2"][both], c["chi2"][both], rtol=1e-5)
+
+
+def test_free_filling_factor_round_trip():
+    """alpha free (free_mask bit 9): noise-free strong-field profiles with
+    alpha in [0.4, 0.9] are recovered from a perturbed start, and freeing
+    alpha never ends above the held-alpha fit of data made with alpha = 1."""
+    n = 16
+    p = W.quiet_and_active_params(n, 30)
+    g = np.random.default_rng(30)
+    p[:, 0] = g.uniform(1200, 2800, n)
+    p[:, 1] = g.uniform(30, 150, n)
+    p[:, 9] = g.uniform(0.4, 0.9, n)
+    s = me.synth(p, T, X, LINE).reshape(n, -1)
+    o, w = W.observe(s, p, np.zeros_like(s))
+    init = p.copy()
+    init[:, 9] = np.clip(p[:, 9] + 0.15, 0, 1)
+    init[:, 0] *= 0.95
+    r = lm.invert(o, w, T, X, LINE, init=init, max_iter=200, conv_rtol=1e-12, free_mask=0x3FF)
+    good = r["chi2"] < 1e-8
+    assert good.mean() > 0.8
+    np.testing.assert_allclose(r["params"][good, 9], p[good, 9], atol=1e-4)
+    np.testing.assert_allclose(r["params"][good, 0], p[good, 0], rtol=1e-4)
+    p1, s1, o1, w1 = _obs(24, 31)
+    held = lm.invert(o1, w1, T, X, LINE, init=p1, max_iter=60, conv_rtol=1e-8)
+    free = lm.invert(o1, w1, T, X, LINE, init=held["params"], max_iter=60, conv_rtol=1e-8,
+                     free_mask=0x3FF)
+    assert np.all(free["chi2"] <= held["chi2"] * (1 + 1e-9) * (24 - 9) / (24 - 10) + 1e-12)
+    assert np.all((free["params"][:, 9] >= 0) & (free["params"][:, 9] <= 1))
