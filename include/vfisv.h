@@ -97,8 +97,12 @@ typedef struct {
 /* Levenberg-Marquardt controls (Sec. 4.2).
  *   max_iter   cap on trial steps (solves) per pixel; the paper runs a fixed
  *              count (30) -- here a pixel also stops when converged.
- *   free_mask  bit p set = parameter p is free; bit 9 (alpha) must be clear
- *              (the filling factor is held at 1 in the inversion).
+ *   free_mask  bit p set = parameter p is free.  Bit 9 frees the filling
+ *              factor alpha (Sec. 2; default held at 1): the model mixes the
+ *              magnetic and the non-magnetic (B = 0) profile, alpha in
+ *              [0, 1], 10 parameters in the solve and the covariance; taken
+ *              by the 6-filter path with the FP64 solve and no restarts
+ *              (else VFISV_E_UNSUPPORTED), not by vfisv_invert_noalloc.
  *   conv_rtol  converged when a successful step lowers chi2 by less than
  *              conv_rtol relative while the damping used was <= conv_eps.
  *   eps0       initial damping.

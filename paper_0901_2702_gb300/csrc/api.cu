@@ -185,12 +185,13 @@ struct WsLayout {
   size_t err = 0, queue = 64, table = 256, scratch = 0, rs = 0, total = 0;
 };
 
-WsLayout layout(int nf, int nlam, int64_t nslots, bool restarts) {
+WsLayout layout(int nf, int nlam, int64_t nslots, bool restarts, bool alpha_free = false) {
   WsLayout L;
   size_t tb = (size_t)table_floats(nf, nlam) * sizeof(float);
   if (nf > 8 && wide_table_bytes(nf, nlam) > tb) tb = wide_table_bytes(nf, nlam);
   L.scratch = L.table + up(tb);
-  L.rs = L.scratch + up((size_t)kScratchPerSlot * (size_t)nslots * sizeof(float));
+  const size_t per = alpha_free ? kScratchPerSlotAlpha : kScratchPerSlot;
+  L.rs = L.scratch + up(per * (size_t)nslots * sizeof(float));
   L.total = L.rs + (restarts ? up(kRsBytesPerSlot * (size_t)nslots) : 0);
   return L;
 }
@@ -203,9 +204,11 @@ int set_device(vfisv_handle* h) {
 
 int check_config(const vfisv_config* cfg, int nfilt) {
   if (!cfg) return VFISV_E_ARG;
-  if (cfg->max_iter < 0 || (cfg->free_mask & ~0x1FFu) || !(cfg->conv_rtol >= 0) ||
+  if (cfg->max_iter < 0 || (cfg->free_mask & ~0x3FFu) || !(cfg->conv_rtol >= 0) ||
       !(cfg->conv_eps >= 0) || !(cfg->eps0 > 0) || !isfinite(cfg->eps0))
     return VFISV_E_ARG;
+  // the filling factor free (bit 9): the FP64 solve without restarts
+  if ((cfg->free_mask >> 9) & 1u && (cfg->restarts || cfg->fast_solve)) return VFISV_E_UNSUPPORTED;
   // restart counters are 20 bits wide (each restart costs an iteration)
   if ((cfg->restarts & ~7) || (cfg->restarts && cfg->max_iter >= (1 << 20))) return VFISV_E_ARG;
   if (!(cfg->hess_reuse >= 0) || !isfinite(cfg->hess_reuse)) return VFISV_E_ARG;
@@ -226,7 +229,8 @@ int check_invert_args(vfisv_handle* h, const float* obs, const float* weights,
   if (npix < 0 || nfilt < 1 || nlam < 1 || nlam > 4096) return VFISV_E_SIZE;
   if (nfilt != 6 && !(nfilt > 8 && wide_supported(nfilt, nlam))) return VFISV_E_UNSUPPORTED;
   if (nfilt > 8 && cfg &&
-      (cfg->restarts || cfg->hess_reuse != 0.0 || cfg->wfa_pol != 0.0 || cfg->fast_solve))
+      (cfg->restarts || cfg->hess_reuse != 0.0 || cfg->wfa_pol != 0.0 || cfg->fast_solve ||
+       ((cfg->free_mask >> 9) & 1u)))
     return VFISV_E_UNSUPPORTED;  // options of the filter-position kernel only
   return check_config(cfg, nfilt);
 }
@@ -308,13 +312,14 @@ int invert_device(vfisv_handle* h, const DevInvert& d, int nfilt, int nlam,
   int64_t nslots = 0;
   int grid = 0, block = h->lm_block;
   size_t smem = 0;
-  if (invert_slots(nfilt, nlam, npix, cfg->restarts, cfg->fast_solve, &nslots, &grid, &block,
-                   &smem) !=
+  const bool alpha_free = (cfg->free_mask >> 9) & 1u;
+  if (invert_slots(nfilt, nlam, npix, cfg->restarts, cfg->fast_solve, alpha_free, &nslots, &grid,
+                   &block, &smem) !=
       cudaSuccess) {
     cudaGetLastError();
     return VFISV_E_CUDA;
   }
-  WsLayout L = layout(nfilt, nlam, nslots, cfg->restarts != 0);
+  WsLayout L = layout(nfilt, nlam, nslots, cfg->restarts != 0, alpha_free);
   if (h->ws_bytes < L.total) {
     int rc = grow(&h->ws, &h->ws_bytes, L.total);
     if (rc) return rc;

@@ -149,6 +149,7 @@ struct InvertArgs {
 };
 
 constexpr int kScratchPerSlot = 45 + 9;  // packed J^T W J and J^T W r
+constexpr int kScratchPerSlotAlpha = 55 + 10;  // the same with the filling factor free
 
 // Map of a pixel in a batch (binary search over the prefix offsets).
 __device__ __forceinline__ int map_of(const int64_t* off, int nmaps, int64_t pix) {
@@ -205,7 +206,7 @@ cudaError_t launch_synth(const SynthArgs& a, int nf, cudaStream_t s);
 // slots per CTA (64, 128 or 256; anything else selects 128 and is written
 // back), and the number of resident slots (the scratch it needs).
 cudaError_t invert_slots(int nf, int nlam, int64_t npix, int restarts, int fast_solve,
-                         int64_t* nslots, int* grid, int* block, size_t* smem);
+                         int alpha_free, int64_t* nslots, int* grid, int* block, size_t* smem);
 cudaError_t launch_restart_perturb(const float* in, int64_t n, int64_t pix0, int k,
                                    uint32_t free_mask, uint64_t seed, float* out, cudaStream_t s);
 // Upload the Weideman coefficients to the LM kernel's constant bank on the

@@ -242,22 +242,27 @@ __constant__ Weideman c_W;
 // The fused pass over the wavelength grid, kept out of line so that its
 // 168 accumulators get the whole register file; results go to the
 // thread's column of `dump`.
-template <int NF>
+template <int NF, bool NM = false>
 __device__ __noinline__ void fused_pass(const PixK P, const float* __restrict__ tab, int nlam,
                                         float* __restrict__ dump, int nt) {
   constexpr int S = ((NF + 1) + 3) & ~3;
   float acc[kRows][4][NF];
+  float accn[NM ? kNmRows : 1][NF];
 #pragma unroll
   for (int r = 0; r < kRows; ++r)
 #pragma unroll
     for (int s = 0; s < 4; ++s)
 #pragma unroll
       for (int k = 0; k < NF; ++k) acc[r][s][k] = 0.0f;
+#pragma unroll
+  for (int r = 0; r < (NM ? kNmRows : 1); ++r)
+#pragma unroll
+    for (int k = 0; k < NF; ++k) accn[r][k] = 0.0f;
 #pragma unroll 1
   for (int i = 0; i < nlam; ++i) {
     float T[NF];
     const float x = load_row<NF>(tab + (size_t)i * S, T);
-    lambda_step<NF, true>(c_W, P, x, T, acc);
+    lambda_step<NF, true, NM>(c_W, P, x, T, acc, accn);
   }
 #pragma unroll
   for (int r = 0; r < kRows; ++r)
@@ -265,6 +270,13 @@ __device__ __noinline__ void fused_pass(const PixK P, const float* __restrict__ 
     for (int s = 0; s < 4; ++s)
 #pragma unroll
       for (int k = 0; k < NF; ++k) dump[((r * 4 + s) * NF + k) * nt] = acc[r][s][k];
+  if constexpr (NM) {
+    // the non-magnetic rows follow the magnetic ones
+#pragma unroll
+    for (int r = 0; r < kNmRows; ++r)
+#pragma unroll
+      for (int k = 0; k < NF; ++k) dump[(kRows * 4 * NF + r * NF + k) * nt] = accn[r][k];
+  }
 }
 
 // Per-slot LM state kept in shared memory (structure of arrays, one column
@@ -277,11 +289,15 @@ __host__ __device__ constexpr size_t invert_smem_bytes(int tabf, int nacc, int n
 
 // RS: randomised restarts compiled in (A.restarts != 0).  DF: the damped
 // solve in double-float and chi2 by a compensated FP32 sum (fast_solve);
-// otherwise both in FP64.
-template <int NF, int BS, bool RS, bool DF>
+// otherwise both in FP64.  AF: the filling factor alpha free (Sec. 2): the
+// model mixes the magnetic and the non-magnetic (B = 0) profile, and the
+// solve takes 10 parameters.
+template <int NF, int BS, bool RS, bool DF, bool AF = false>
 __global__ void __launch_bounds__(BS, 1) invert_kernel(InvertArgs A) {
   constexpr int NOBS = 4 * NF;
-  constexpr int NACC = kRows * 4 * NF;
+  constexpr int NACC = kRows * 4 * NF + (AF ? kNmRows * NF : 0);
+  constexpr int NP = AF ? 10 : kNP;        // parameters in the solve
+  constexpr int NPK = NP * (NP + 1) / 2;   // packed J^T W J
   extern __shared__ __align__(16) float smem[];
   const int S = table_stride(NF);
   const int tabf = table_floats(NF, A.nlam);
@@ -352,8 +368,9 @@ __global__ void __launch_bounds__(BS, 1) invert_kernel(InvertArgs A) {
           Mt[7] = 0.25f * ic;
           Mt[8] = 0.75f * ic / A.lk.mu;
         }
-        Mt[9] = 1.0f;
+        if (!AF || !A.init) Mt[9] = 1.0f;
         apply_bounds(Mt);
+        Mt[9] = fminf(fmaxf(Mt[9], 0.0f), 1.0f);
         if (bad) {
           for (int j = 0; j < 10; ++j) A.params_out[pix * 10 + j] = Mt[j];
           A.chi2_out[pix] = 0.0f;
@@ -397,12 +414,15 @@ __global__ void __launch_bounds__(BS, 1) invert_kernel(InvertArgs A) {
             Mt[j] = t.hi + (t.lo + d[j].lo);  // the FP32 model nearest M + delta
           }
         } else {
-          double d[kNP];
-          damped_step_fp64(scr, ns, A.free_mask, sEps[tid], d);
+          double d[NP];
+          damped_step_fp64<NP>(scr, ns, A.free_mask, sEps[tid], d);
 #pragma unroll
-          for (int j = 0; j < kNP; ++j) Mt[j] = (float)((double)ST(sM, j) + d[j]);
+          for (int j = 0; j < NP; ++j) Mt[j] = (float)((double)ST(sM, j) + d[j]);
         }
-        Mt[9] = 1.0f;
+        if constexpr (AF)
+          Mt[9] = fminf(fmaxf(Mt[9], 0.0f), 1.0f);
+        else
+          Mt[9] = 1.0f;
         apply_bounds(Mt);
 #pragma unroll
         for (int j = 0; j < 10; ++j) ST(sMt, j) = Mt[j];
@@ -410,10 +430,13 @@ __global__ void __launch_bounds__(BS, 1) invert_kernel(InvertArgs A) {
     }
 
     // ---- fused synthesis + Jacobian at the trial model (Secs. 3 and 4.4) ----
-    fused_pass<NF>(make_pixk(A.lk, ST(sMt, 0), ST(sMt, 1), ST(sMt, 3), ST(sMt, 4),
-                             ST(sMt, 5), ST(sMt, 6)),
-                   tab, A.nlam, dump + tid, nt);
+    fused_pass<NF, AF>(make_pixk(A.lk, ST(sMt, 0), ST(sMt, 1), ST(sMt, 3), ST(sMt, 4),
+                                 ST(sMt, 5), ST(sMt, 6)),
+                       tab, A.nlam, dump + tid, nt);
     auto D = [&](int r, int s, int k) { return dump[((r * 4 + s) * NF + k) * nt + tid]; };
+    // non-magnetic Stokes I rows (AF): value, then the E, D, A, V rows
+    auto N = [&](int r, int k) { return dump[(kRows * 4 * NF + r * NF + k) * nt + tid]; };
+    const float alf = AF ? ST(sMt, 9) : 1.0f;
 
     const long long pix = sPix[tid];
     const float* o = A.obs + pix * NOBS;
@@ -427,11 +450,13 @@ __global__ void __launch_bounds__(BS, 1) invert_kernel(InvertArgs A) {
     float syn[NOBS];
 #pragma unroll
     for (int k = 0; k < NF; ++k) {
-      const float q0 = D(0, 1, k), u0 = D(0, 2, k);
-      syn[k] = fmaf(s0, tau[k], mus1 * D(0, 0, k));
+      // with alpha free: alpha x magnetic + (1 - alpha) x non-magnetic
+      const float q0 = alf * D(0, 1, k), u0 = alf * D(0, 2, k);
+      const float yI = AF ? fmaf(alf, D(0, 0, k) - N(0, k), N(0, k)) : D(0, 0, k);
+      syn[k] = fmaf(s0, tau[k], mus1 * yI);
       syn[NF + k] = mus1 * fmaf(c2p, q0, -s2p * u0);
       syn[2 * NF + k] = mus1 * fmaf(s2p, q0, c2p * u0);
-      syn[3 * NF + k] = mus1 * D(0, 3, k);
+      syn[3 * NF + k] = mus1 * (alf * D(0, 3, k));
     }
     double c2;
     if constexpr (DF) {
@@ -523,12 +548,14 @@ __global__ void __launch_bounds__(BS, 1) invert_kernel(InvertArgs A) {
 #pragma unroll
       for (int j = 0; j < 10; ++j) ST(sM, j) = ST(sMt, j);
       sChi[tid] = c2;
-      Dot2 a[kNPk], g[kNP];
+      Dot2 a[NPK], g[NP];
 #pragma unroll
-      for (int i = 0; i < kNPk; ++i) a[i] = Dot2{0.0f, 0.0f};
+      for (int i = 0; i < NPK; ++i) a[i] = Dot2{0.0f, 0.0f};
 #pragma unroll
-      for (int i = 0; i < kNP; ++i) g[i] = Dot2{0.0f, 0.0f};
-      constexpr int rowOf[kNP] = {kRowB, kRowG, -1, kRowE, kRowD, kRowA, kRowV, -1, -1};
+      for (int i = 0; i < NP; ++i) g[i] = Dot2{0.0f, 0.0f};
+      constexpr int rowOf[10] = {kRowB, kRowG, -1, kRowE, kRowD, kRowA, kRowV, -1, -1, -1};
+      // rows of the non-magnetic profile for eta0, dlambdaD, a, v (AF)
+      constexpr int nmRowOf[10] = {-1, -1, -1, 1, 2, 3, 4, -1, -1, -1};
       const float mu = A.lk.mu;
       const RowScale R = row_scale(A.lk, ST(sMt, 3), ST(sMt, 4));
       // Hessian reuse (Sec. 4.4): this and the previous accepted step both
@@ -542,7 +569,7 @@ __global__ void __launch_bounds__(BS, 1) invert_kernel(InvertArgs A) {
       // fmaf(cA, D(r, sa, k), cB * D(r, sb, k)), the psi rotation of Q0/U0.
 #pragma unroll 1
       for (int k = 0; k < NF; ++k) {
-        const float q0 = D(0, 1, k), u0 = D(0, 2, k);
+        const float q0 = alf * D(0, 1, k), u0 = alf * D(0, 2, k);
         const float Qk = mus1 * fmaf(c2p, q0, -s2p * u0);
         const float Uk = mus1 * fmaf(s2p, q0, c2p * u0);
 #pragma unroll 1
@@ -551,22 +578,28 @@ __global__ void __launch_bounds__(BS, 1) invert_kernel(InvertArgs A) {
           const int sb = (s == 0) ? 0 : (s == 3 ? 3 : 2);
           const float cA = (s == 1) ? c2p : (s == 2 ? s2p : 1.0f);
           const float cB = (s == 1) ? -s2p : (s == 2 ? c2p : 0.0f);
-          float J[kNP];
+          float J[NP];
 #pragma unroll
-          for (int p = 0; p < kNP; ++p)
-            if (rowOf[p] >= 0)
-              J[p] = (mus1 * R.s[rowOf[p]]) *
+          for (int p = 0; p < NP; ++p)
+            if (rowOf[p] >= 0) {
+              J[p] = (alf * mus1 * R.s[rowOf[p]]) *
                      fmaf(cA, D(rowOf[p], sa, k), cB * D(rowOf[p], sb, k));
+              if (AF && nmRowOf[p] > 0 && s == 0)
+                J[p] = fmaf((1.0f - alf) * mus1 * R.s[rowOf[p]], N(nmRowOf[p], k), J[p]);
+            }
           J[2] = (s == 1) ? -2.0f * kDeg * Uk : (s == 2 ? 2.0f * kDeg * Qk : 0.0f);
           J[7] = (s == 0) ? tau[k] : 0.0f;
-          const float lin = fmaf(cA, D(0, sa, k), cB * D(0, sb, k));
+          const float linm = fmaf(cA, D(0, sa, k), cB * D(0, sb, k));  // magnetic
+          const float lin = AF ? ((s == 0) ? fmaf(alf, linm - N(0, k), N(0, k)) : alf * linm)
+                               : linm;
           J[8] = mu * lin;
+          if constexpr (AF) J[NP - 1] = mus1 * ((s == 0) ? linm - N(0, k) : linm);
           const float sv = (s == 0) ? fmaf(s0, tau[k], mus1 * lin) : mus1 * lin;
           const int ob = s * NF + k;
           const float ww = wv[ob];
           const float rr = o[ob] - sv;
 #pragma unroll
-          for (int p = 0; p < kNP; ++p) {
+          for (int p = 0; p < NP; ++p) {
             const float wj = ww * J[p];
             g[p].add(wj, rr);
             if (!keepA) {
@@ -578,10 +611,10 @@ __global__ void __launch_bounds__(BS, 1) invert_kernel(InvertArgs A) {
       }
       if (!keepA) {
 #pragma unroll
-        for (int i = 0; i < kNPk; ++i) scr[(int64_t)i * ns] = a[i].value();
+        for (int i = 0; i < NPK; ++i) scr[(int64_t)i * ns] = a[i].value();
       }
 #pragma unroll
-      for (int i = 0; i < kNP; ++i) scr[(int64_t)(kNPk + i) * ns] = g[i].value();
+      for (int i = 0; i < NP; ++i) scr[(int64_t)(NPK + i) * ns] = g[i].value();
       if (RS && c2 < *rsBest) {
         // a new best over all segments: keep it with its normal equations
         *rsBest = c2;
@@ -624,18 +657,18 @@ __global__ void __launch_bounds__(BS, 1) invert_kernel(InvertArgs A) {
         } else {
           // all 45 loads first (one retiring lane runs this while its warp
           // waits), then 400-byte-aligned vector stores into the row
-          float v[48];
+          constexpr int NPK4 = (NPK + 3) & ~3;
+          float v[NPK4];
 #pragma unroll
-          for (int j = 0; j < kNPk; ++j) v[j] = src[(int64_t)j * ns];
-          v[45] = v[46] = v[47] = 0.0f;
+          for (int j = 0; j < NPK4; ++j) v[j] = (j < NPK) ? src[(int64_t)j * ns] : 0.0f;
           if ((reinterpret_cast<uintptr_t>(A.cov_out) & 15u) == 0) {  // rows are 400 B
             float4* c4 = reinterpret_cast<float4*>(cv);
 #pragma unroll
-            for (int j = 0; j < 12; ++j)
+            for (int j = 0; j < NPK4 / 4; ++j)
               c4[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
           } else {
 #pragma unroll
-            for (int j = 0; j < kNPk; ++j) cv[j] = v[j];
+            for (int j = 0; j < NPK; ++j) cv[j] = v[j];
           }
         }
       }
@@ -654,7 +687,7 @@ __global__ void __launch_bounds__(BS, 1) invert_kernel(InvertArgs A) {
 // warp that happens to hold one such pixel.
 constexpr int kCovThreads = 128;
 constexpr int kCovQueue = 2 * kCovThreads;
-template <bool DF>
+template <bool DF, int NPAR = kNP>
 __global__ void __launch_bounds__(kCovThreads) covariance_kernel(float* cov,
                                                                  const int32_t* status,
                                                                  int64_t npix_max,
@@ -673,7 +706,8 @@ __global__ void __launch_bounds__(kCovThreads) covariance_kernel(float* cov,
       const int st = status[p];
       if (st == VFISV_PIX_CONVERGED || st == VFISV_PIX_MAXITER || st == VFISV_PIX_STALLED) {
         const bool ok = DF ? covariance_df(cov + p * 100, 1, free_mask, cov + p * 100, true)
-                           : covariance_fp64(cov + p * 100, 1, free_mask, cov + p * 100, true);
+                           : covariance_fp64<NPAR>(cov + p * 100, 1, free_mask, cov + p * 100,
+                                                   true);
         if (!ok) {
           const int slot = atomicAdd(&qn, 1);
           queue[slot] = p;  // slot < kCovQueue: drained below before it can fill
@@ -688,7 +722,7 @@ __global__ void __launch_bounds__(kCovThreads) covariance_kernel(float* cov,
         if (DF)
           covariance_df(cov + queue[i] * 100, 1, free_mask, cov + queue[i] * 100, false);
         else
-          covariance_fp64(cov + queue[i] * 100, 1, free_mask, cov + queue[i] * 100, false);
+          covariance_fp64<NPAR>(cov + queue[i] * 100, 1, free_mask, cov + queue[i] * 100, false);
       __syncthreads();
       if (threadIdx.x == 0) qn = 0;
     }
@@ -708,15 +742,19 @@ cudaError_t launch_covariance(float* cov, const int32_t* status, int64_t npix,
   if (grid < 1) grid = 1;
   if (fast_solve)
     covariance_kernel<true><<<(int)grid, kCovThreads, 0, s>>>(cov, status, npix, npix_dev, free_mask);
+  else if (free_mask & (1u << 9))  // the filling factor free: 10 parameters
+    covariance_kernel<false, 10><<<(int)grid, kCovThreads, 0, s>>>(cov, status, npix, npix_dev,
+                                                                    free_mask);
   else
     covariance_kernel<false><<<(int)grid, kCovThreads, 0, s>>>(cov, status, npix, npix_dev, free_mask);
   return cudaGetLastError();
 }
 
-template <int BS, bool RS, bool DF>
+template <int BS, bool RS, bool DF, bool AF = false>
 static cudaError_t slots_for(int nlam, int64_t npix, int64_t* nslots, int* grid, size_t* smem) {
-  auto kern = invert_kernel<6, BS, RS, DF>;
-  const size_t sm = invert_smem_bytes(table_floats(6, nlam), kRows * 4 * 6, BS);
+  auto kern = invert_kernel<6, BS, RS, DF, AF>;
+  const size_t sm =
+      invert_smem_bytes(table_floats(6, nlam), kRows * 4 * 6 + (AF ? kNmRows * 6 : 0), BS);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   int dev = 0, nsm = 0, per = 0;
@@ -752,8 +790,13 @@ static cudaError_t invert_slots_t(int nlam, int64_t npix, int restarts, int64_t*
 }
 
 cudaError_t invert_slots(int nf, int nlam, int64_t npix, int restarts, int fast_solve,
-                         int64_t* nslots, int* grid, int* block, size_t* smem) {
+                         int alpha_free, int64_t* nslots, int* grid, int* block, size_t* smem) {
   if (nf != 6) return cudaErrorInvalidValue;
+  if (alpha_free) {  // compiled for the default slot count, FP64 solve, no restarts
+    if (restarts || fast_solve) return cudaErrorInvalidValue;
+    *block = kInvThreadsDefault;
+    return slots_for<kInvThreadsDefault, false, false, true>(nlam, npix, nslots, grid, smem);
+  }
   return fast_solve ? invert_slots_t<true>(nlam, npix, restarts, nslots, grid, block, smem)
                     : invert_slots_t<false>(nlam, npix, restarts, nslots, grid, block, smem);
 }
@@ -782,6 +825,11 @@ static cudaError_t launch_invert_t(const InvertArgs& a, int grid, int block, siz
 cudaError_t launch_invert(const InvertArgs& a, int nf, int grid, int block, size_t smem,
                           cudaStream_t s) {
   if (nf != 6) return cudaErrorInvalidValue;
+  if (a.free_mask & (1u << 9)) {
+    if (a.restarts || a.fast_solve || block != kInvThreadsDefault) return cudaErrorInvalidValue;
+    invert_kernel<6, kInvThreadsDefault, false, false, true><<<grid, block, smem, s>>>(a);
+    return cudaGetLastError();
+  }
   return a.fast_solve ? launch_invert_t<true>(a, grid, block, smem, s)
                       : launch_invert_t<false>(a, grid, block, smem, s);
 }

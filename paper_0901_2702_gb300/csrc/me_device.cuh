@@ -164,10 +164,16 @@ constexpr int kRowB = 1, kRowG = 2, kRowE = 3, kRowD = 4, kRowA = 5, kRowV = 6;
 
 // One wavelength point: synthesis (and, if DERIV, the Jacobian rows),
 // accumulated into acc[row][stokes][k] += T_k * value.
-template <int NF, bool DERIV>
+// Rows of the non-magnetic (B = 0) Stokes I profile used when the filling
+// factor is free: value, then eta0 d/d eta0, u d/du, d/da, d/du (the scale
+// factors of the magnetic rows E, D, A, V apply to them alike).
+constexpr int kNmRows = 5;
+
+template <int NF, bool DERIV, bool NM = false>
 __device__ __forceinline__ void lambda_step(const Weideman& W, const PixK& P, float x,
                                             const float (&T)[NF],
-                                            float (&acc)[DERIV ? kRows : 1][4][NF]) {
+                                            float (&acc)[DERIV ? kRows : 1][4][NF],
+                                            float (*accn)[NF] = nullptr) {
   const float up = fmaf(x, P.invD, -P.uv);
   const float ub = up + P.uB, ur = up - P.uB;
   float Hp, Fp, Hb, Fb, Hr, Fr;
@@ -281,6 +287,19 @@ __device__ __forceinline__ void lambda_step(const Weideman& W, const PixK& P, fl
     stokes(3, fmaf(-yV, dDe, -e2 * eV), fmaf(-yV, dDq, -rV * rL),
            fmaf(-yV, dDv, -fmaf(rV, rV, eI2)), fmaf(-yV, dDr, -rV * eL),
            fmaf(-yV, dDt, -fmaf(rV, eV, Pi)));
+    if constexpr (NM) {
+      // B = 0: the three components coincide with the pi one, eta_I =
+      // 1 + eta0 H_p, no polarisation, I = 1 / eta_I (unit S1)
+      const float eta0 = fmaf(2.0f, P.c2, P.c1);
+      const float yn = rcp_fast(fmaf(eta0, Hp, 1.0f));
+      const float ny2 = -eta0 * yn * yn;
+      const float nU = ny2 * bep;  // d/du_p
+      const float nv[kNmRows] = {yn, ny2 * Hp, up * nU, ny2 * alp, nU};
+#pragma unroll
+      for (int k = 0; k < NF; ++k)
+#pragma unroll
+        for (int r = 0; r < kNmRows; ++r) accn[r][k] = fmaf(T[k], nv[r], accn[r][k]);
+    }
   }
 }
 

@@ -110,7 +110,7 @@ extern "C" int vfisv_invert_noalloc(const float* obs, const float* weights,
   int64_t nslots = 0;
   int grid = 0, block = 128;
   size_t smem = 0;
-  if (invert_slots(nfilt, nlam, npix, 0, cfg->fast_solve, &nslots, &grid, &block, &smem) !=
+  if (invert_slots(nfilt, nlam, npix, 0, cfg->fast_solve, 0, &nslots, &grid, &block, &smem) !=
       cudaSuccess) {
     cudaGetLastError();
     return VFISV_E_CUDA;

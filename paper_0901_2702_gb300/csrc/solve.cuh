@@ -13,6 +13,8 @@ namespace vfisv {
 
 constexpr int kNP = 9;    // parameters taking part in the solve (alpha held)
 constexpr int kNPk = 45;  // packed lower triangle of a 9x9 matrix
+// With the filling factor free the solve takes N = 10 parameters; the
+// functions below are templates on N (default 9).
 
 __device__ __forceinline__ int tri(int i, int j) { return i * (i + 1) / 2 + j; }  // i >= j
 
@@ -31,39 +33,40 @@ __device__ __forceinline__ double eps_update(double e, bool success) {
 // Solves M y = b with eigenvalues below 1e-12 * max zeroed (truncated SVD
 // of a symmetric matrix), or, with b == nullptr, writes the truncated
 // pseudo-inverse into Minv.
+template <int N = kNP>
 static __device__ __noinline__ void jacobi_pinv(const double* Mp /*packed*/, const double* b,
                                          double* y, double* Minv) {
-  double a[kNP][kNP], v[kNP][kNP];
-  for (int i = 0; i < kNP; ++i)
-    for (int j = 0; j < kNP; ++j) {
+  double a[N][N], v[N][N];
+  for (int i = 0; i < N; ++i)
+    for (int j = 0; j < N; ++j) {
       a[i][j] = (i >= j) ? Mp[tri(i, j)] : Mp[tri(j, i)];
       v[i][j] = (i == j) ? 1.0 : 0.0;
     }
   for (int sweep = 0; sweep < 30; ++sweep) {
     double off = 0.0, dia = 0.0;
-    for (int i = 0; i < kNP; ++i) {
+    for (int i = 0; i < N; ++i) {
       dia += a[i][i] * a[i][i];
-      for (int j = i + 1; j < kNP; ++j) off += a[i][j] * a[i][j];
+      for (int j = i + 1; j < N; ++j) off += a[i][j] * a[i][j];
     }
     if (!(off > 1e-26 * dia)) break;  // off-diagonal below ~3e-13 of the diagonal
-    for (int p = 0; p < kNP - 1; ++p)
-      for (int q = p + 1; q < kNP; ++q) {
+    for (int p = 0; p < N - 1; ++p)
+      for (int q = p + 1; q < N; ++q) {
         const double apq = a[p][q];
         if (apq == 0.0) continue;
         const double th = (a[q][q] - a[p][p]) / (2.0 * apq);
         const double t = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
         const double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
-        for (int k = 0; k < kNP; ++k) {
+        for (int k = 0; k < N; ++k) {
           const double akp = a[k][p], akq = a[k][q];
           a[k][p] = c * akp - s * akq;
           a[k][q] = s * akp + c * akq;
         }
-        for (int k = 0; k < kNP; ++k) {
+        for (int k = 0; k < N; ++k) {
           const double apk = a[p][k], aqk = a[q][k];
           a[p][k] = c * apk - s * aqk;
           a[q][k] = s * apk + c * aqk;
         }
-        for (int k = 0; k < kNP; ++k) {
+        for (int k = 0; k < N; ++k) {
           const double vkp = v[k][p], vkq = v[k][q];
           v[k][p] = c * vkp - s * vkq;
           v[k][q] = s * vkp + c * vkq;
@@ -71,29 +74,29 @@ static __device__ __noinline__ void jacobi_pinv(const double* Mp /*packed*/, con
       }
   }
   double lmax = 0.0;
-  for (int i = 0; i < kNP; ++i) lmax = fmax(lmax, fabs(a[i][i]));
-  double linv[kNP];
-  for (int i = 0; i < kNP; ++i) {
+  for (int i = 0; i < N; ++i) lmax = fmax(lmax, fabs(a[i][i]));
+  double linv[N];
+  for (int i = 0; i < N; ++i) {
     const double l = fabs(a[i][i]);
     linv[i] = (l > 1e-12 * lmax && l > 0.0) ? 1.0 / a[i][i] : 0.0;
   }
   if (b) {
-    double t[kNP];
-    for (int i = 0; i < kNP; ++i) {
+    double t[N];
+    for (int i = 0; i < N; ++i) {
       double s = 0.0;
-      for (int k = 0; k < kNP; ++k) s += v[k][i] * b[k];
+      for (int k = 0; k < N; ++k) s += v[k][i] * b[k];
       t[i] = s * linv[i];
     }
-    for (int k = 0; k < kNP; ++k) {
+    for (int k = 0; k < N; ++k) {
       double s = 0.0;
-      for (int i = 0; i < kNP; ++i) s += v[k][i] * t[i];
+      for (int i = 0; i < N; ++i) s += v[k][i] * t[i];
       y[k] = s;
     }
   } else {
-    for (int i = 0; i < kNP; ++i)
+    for (int i = 0; i < N; ++i)
       for (int j = 0; j <= i; ++j) {
         double s = 0.0;
-        for (int k = 0; k < kNP; ++k) s += v[i][k] * linv[k] * v[j][k];
+        for (int k = 0; k < N; ++k) s += v[i][k] * linv[k] * v[j][k];
         Minv[tri(i, j)] = s;
       }
   }
@@ -101,9 +104,10 @@ static __device__ __noinline__ void jacobi_pinv(const double* Mp /*packed*/, con
 
 // In-place Cholesky of a packed 9x9 matrix; false if a pivot is not
 // comfortably positive (the matrix has unit-scale diagonal here).
-__device__ __forceinline__ bool cholesky9(double (&L)[kNPk], double (&ri)[kNP]) {
+template <int N = kNP>
+__device__ __forceinline__ bool cholesky9(double (&L)[(N * (N + 1) / 2)], double (&ri)[N]) {
 #pragma unroll
-  for (int j = 0; j < kNP; ++j) {
+  for (int j = 0; j < N; ++j) {
     double d = L[tri(j, j)];
 #pragma unroll
     for (int k = 0; k < j; ++k) d = fma(-L[tri(j, k)], L[tri(j, k)], d);
@@ -112,7 +116,7 @@ __device__ __forceinline__ bool cholesky9(double (&L)[kNPk], double (&ri)[kNP]) 
     ri[j] = r;
     L[tri(j, j)] = d * r;
 #pragma unroll
-    for (int i = j + 1; i < kNP; ++i) {
+    for (int i = j + 1; i < N; ++i) {
       double s = L[tri(i, j)];
 #pragma unroll
       for (int k = 0; k < j; ++k) s = fma(-L[tri(i, k)], L[tri(j, k)], s);
@@ -123,20 +127,21 @@ __device__ __forceinline__ bool cholesky9(double (&L)[kNPk], double (&ri)[kNP]) 
 }
 
 // Forward and back substitution with the factor and its reciprocal pivots.
-__device__ __forceinline__ void chol_solve9(const double (&L)[kNPk], const double (&ri)[kNP],
-                                            double (&x)[kNP]) {
+template <int N = kNP>
+__device__ __forceinline__ void chol_solve9(const double (&L)[(N * (N + 1) / 2)], const double (&ri)[N],
+                                            double (&x)[N]) {
 #pragma unroll
-  for (int i = 0; i < kNP; ++i) {
+  for (int i = 0; i < N; ++i) {
     double s = x[i];
 #pragma unroll
     for (int k = 0; k < i; ++k) s = fma(-L[tri(i, k)], x[k], s);
     x[i] = s * ri[i];
   }
 #pragma unroll
-  for (int i = kNP - 1; i >= 0; --i) {
+  for (int i = N - 1; i >= 0; --i) {
     double s = x[i];
 #pragma unroll
-    for (int k = i + 1; k < kNP; ++k) s = fma(-L[tri(k, i)], x[k], s);
+    for (int k = i + 1; k < N; ++k) s = fma(-L[tri(k, i)], x[k], s);
     x[i] = s * ri[i];
   }
 }
@@ -144,17 +149,18 @@ __device__ __forceinline__ void chol_solve9(const double (&L)[kNPk], const doubl
 // Jacobi-scaled matrix of the stored normal equations: returns the scale
 // s_i = diag^-1/2 (0 for held parameters) and fills Mx = D^-1/2 A D^-1/2 +
 // eps I on free parameters, identity rows/columns on held ones.
+template <int N = kNP>
 __device__ __forceinline__ void scaled_system(const float* scr, int64_t ns, uint32_t free_mask,
-                                              double eps, double (&Mx)[kNPk],
-                                              double (&sc)[kNP], bool (&held)[kNP]) {
+                                              double eps, double (&Mx)[(N * (N + 1) / 2)],
+                                              double (&sc)[N], bool (&held)[N]) {
 #pragma unroll
-  for (int i = 0; i < kNP; ++i) {
+  for (int i = 0; i < N; ++i) {
     const double d = (double)scr[(int64_t)tri(i, i) * ns];
     held[i] = !((free_mask >> i) & 1u) || !(d > 0.0) || !isfinite(d);
     sc[i] = held[i] ? 0.0 : rsqrt(d);
   }
 #pragma unroll
-  for (int i = 0; i < kNP; ++i)
+  for (int i = 0; i < N; ++i)
 #pragma unroll
     for (int j = 0; j <= i; ++j) {
       double m;
@@ -168,28 +174,29 @@ __device__ __forceinline__ void scaled_system(const float* scr, int64_t ns, uint
 
 // Eq. 5 with the Marquardt diagonal (Eq. 4): delta = (A + eps diag A)^-1 g,
 // Jacobi-scaled, in FP64 (the default precision of the solve).
+template <int N = kNP>
 static __device__ __noinline__ void damped_step_fp64(const float* scr, int64_t ns, uint32_t free_mask, double eps,
-                            double (&delta)[kNP]) {
-  double L[kNPk], sc[kNP];
-  bool held[kNP];
-  scaled_system(scr, ns, free_mask, eps, L, sc, held);
-  double y[kNP];
+                            double (&delta)[N]) {
+  double L[(N * (N + 1) / 2)], sc[N];
+  bool held[N];
+  scaled_system<N>(scr, ns, free_mask, eps, L, sc, held);
+  double y[N];
 #pragma unroll
-  for (int i = 0; i < kNP; ++i)
-    y[i] = held[i] ? 0.0 : (double)scr[(int64_t)(kNPk + i) * ns] * sc[i];
-  double ri[kNP];
-  if (cholesky9(L, ri)) {
-    chol_solve9(L, ri, y);
+  for (int i = 0; i < N; ++i)
+    y[i] = held[i] ? 0.0 : (double)scr[(int64_t)((N * (N + 1) / 2) + i) * ns] * sc[i];
+  double ri[N];
+  if (cholesky9<N>(L, ri)) {
+    chol_solve9<N>(L, ri, y);
   } else {
     // rebuild the scaled matrix (the factorisation overwrote it)
-    scaled_system(scr, ns, free_mask, eps, L, sc, held);
-    double b[kNP];
+    scaled_system<N>(scr, ns, free_mask, eps, L, sc, held);
+    double b[N];
 #pragma unroll
-    for (int i = 0; i < kNP; ++i) b[i] = y[i];
-    jacobi_pinv(L, b, y, nullptr);
+    for (int i = 0; i < N; ++i) b[i] = y[i];
+    jacobi_pinv<N>(L, b, y, nullptr);
   }
 #pragma unroll
-  for (int i = 0; i < kNP; ++i) delta[i] = held[i] ? 0.0 : sc[i] * y[i];
+  for (int i = 0; i < N; ++i) delta[i] = held[i] ? 0.0 : sc[i] * y[i];
 }
 
 // Covariance (J^T W J)^+ at the final model, in parameter units, from the
@@ -197,29 +204,30 @@ static __device__ __noinline__ void damped_step_fp64(const float* scr, int64_t n
 // `out` may hold the packed matrix itself.  With try_only, returns false
 // without writing when the Cholesky factorisation fails (the caller then
 // runs the eigen-decomposition path for that pixel).
+template <int N = kNP>
 static __device__ __noinline__ bool covariance_fp64(const float* scr, int64_t ns, uint32_t free_mask,
                                         float* out, bool try_only) {
-  double L[kNPk], sc[kNP];
-  bool held[kNP];
-  scaled_system(scr, ns, free_mask, 0.0, L, sc, held);
-  double P[kNPk], ri[kNP];
-  if (cholesky9(L, ri)) {
-    for (int j = 0; j < kNP; ++j) {
-      double x[kNP];
+  double L[(N * (N + 1) / 2)], sc[N];
+  bool held[N];
+  scaled_system<N>(scr, ns, free_mask, 0.0, L, sc, held);
+  double P[(N * (N + 1) / 2)], ri[N];
+  if (cholesky9<N>(L, ri)) {
+    for (int j = 0; j < N; ++j) {
+      double x[N];
 #pragma unroll
-      for (int i = 0; i < kNP; ++i) x[i] = (i == j) ? 1.0 : 0.0;
-      chol_solve9(L, ri, x);
-      for (int i = j; i < kNP; ++i) P[tri(i, j)] = x[i];
+      for (int i = 0; i < N; ++i) x[i] = (i == j) ? 1.0 : 0.0;
+      chol_solve9<N>(L, ri, x);
+      for (int i = j; i < N; ++i) P[tri(i, j)] = x[i];
     }
   } else {
     if (try_only) return false;
-    scaled_system(scr, ns, free_mask, 0.0, L, sc, held);
-    jacobi_pinv(L, nullptr, nullptr, P);
+    scaled_system<N>(scr, ns, free_mask, 0.0, L, sc, held);
+    jacobi_pinv<N>(L, nullptr, nullptr, P);
   }
   for (int i = 0; i < 10; ++i)
     for (int j = 0; j < 10; ++j) {
       float v = 0.0f;
-      if (i < kNP && j < kNP && !held[i] && !held[j])
+      if (i < N && j < N && !held[i] && !held[j])
         v = (float)(sc[i] * sc[j] * ((i >= j) ? P[tri(i, j)] : P[tri(j, i)]));
       out[i * 10 + j] = v;
     }
