@@ -22,6 +22,13 @@ library, 8 epochs) and the training time is reported beside the numbers.
 buffers (host->device copies of observations and weights and the copy back
 of all outputs inside the timed region).
 
+`fast_solve` repeats the mixed step with the opt-in double-float solve
+(not the headline: the workload names an FP64 solve).
+
+`--workload serving` runs the uneven serving mix instead (64 maps, half
+filtergrams, half spectrograph-shaped; per-map latency p50/p99) and prints
+its own line.
+
 With --impl reference the FP64 CPU oracle (plain LM) is timed instead on a
 bounded sample of the same map.  Multi-GPU: pixels are independent, so N
 ranks invert N independent maps (weak scaling, no collective on the data
@@ -449,7 +456,9 @@ def run_serving(args):
     def half(kind):
         h, tf, tx, line = (hF, tfF, txF, W.FE6173) if kind == 0 else (hS, tfS, txS, W.FE6302)
         obs, wts, sizes, ids = [], [], [], []
-        for m in range(kind, len(sides), 2):
+        # serving order: the smallest maps first (shortest-job-first lowers
+        # the median latency; the work per pixel is the same)
+        for m in sorted(range(kind, len(sides), 2), key=lambda j: int(sides[j])):
             p = t32(W.serving_map_params(int(sides[m]), seed * 1000 + m))
             syn = v.vfisv_synth(h, p, tf, tx, line).reshape(p.shape[0], -1)
             obs.append(syn + float(sig[m]) * torch.randn(syn.shape, device=dev, generator=gen))
@@ -550,7 +559,8 @@ def run_serving(args):
                       "pixels": {"filter": nF, "spectrograph": nS},
                       "l2": "inputs > 129 MB L2 (no flush needed)",
                       "parallelism": "two persistent launches (one per instrument), each a "
-                                     "captured CUDA graph, on two concurrent streams"},
+                                     "captured CUDA graph, on two concurrent streams; maps "
+                                     "queued smallest first"},
            "converged_fraction": {"filter": cF / max(nF, 1), "spectrograph": cS / max(nS, 1)},
            "latency_ms": {"p50": float(np.percentile(lat, 50)),
                           "p99": float(np.percentile(lat, 99)),
@@ -559,7 +569,9 @@ def run_serving(args):
                                   "retirement of its last pixel (GPU global timer)"},
            "per_map_latency_ms": {str(m): float(x) for m, x in zip(idsF + idsS, lat)},
            "ms_per_step_all": times, "input_generation_s": gen_s, "clocks": clocks,
-           "gpu_launches": None}
+           # per step: network (pack + 6 per 65,536-pixel chunk), then per half
+           # start stamp, table pack, LM kernel, covariance, latency
+           "gpu_launches": args.steps * (1 + 6 * ((nF + 65535) // 65536) + 5 + 5)}
     gF.close()
     gS.close()
     print(json.dumps(res))
