@@ -128,7 +128,8 @@ typedef struct {
  *              Where an inversion starts without given models (vfisv_invert
  *              with init == NULL, the re-inversion stage of vfisv_invert_nn),
  *              > 0 starts from the models of vfisv_init_models instead of the
- *              standard guess.  In the first stage of vfisv_invert_nn, > 0
+ *              standard guess (both the 6-filter and the spectrograph-shaped
+ *              path).  In the first stage of vfisv_invert_nn, > 0
  *              combines the network's guess the paper's way: B and gamma from
  *              the weak-field estimate where the polarisation level is below
  *              wfa_pol (the paper: 0.06), the wing azimuth everywhere, the
@@ -201,7 +202,7 @@ int vfisv_invert_batch(vfisv_handle* h, const float* obs, const float* weights,
 
 /* Initial models from the filtergrams (Sec. 6; the paper's methods are
  * cited, not printed -- this is one reading of them).  For each pixel of
- * obs [npix][4][nfilt] (3 <= nfilt <= 8; filters [nfilt][nlam] on wl_mA, any
+ * obs [npix][4][nfilt] (3 <= nfilt <= 128; filters [nfilt][nlam] on wl_mA, any
  * order of centres):
  *   c_k      filter centres sum T_k x / sum T_k, taken in increasing order;
  *   B_par    least-squares fit of V_k = -C B_par dI/dlambda_k, the derivative
@@ -210,7 +211,9 @@ int vfisv_invert_batch(vfisv_handle* h, const float* obs, const float* weights,
  *   B_perp   least-squares fit of |(Q_k, U_k)| = C^2 B_perp^2 / 4 |d2I/dlambda2_k|
  *            over the interior centres;
  *   psi      azimuth from the line wings: 2 psi = atan2(sum w_k U_k,
- *            sum w_k Q_k), w_k = (c_k - mean c)^4;
+ *            sum w_k Q_k), w_k = (c_k - mean c)^4, times the squared relative
+ *            line depth ((I_c - I_k) / max_j (I_c - I_j))^2 when nfilt > 8
+ *            (spectra that reach into the continuum);
  *   B = hypot(B_par, B_perp), gamma = atan2(B_perp, B_par);
  *   v        centre of gravity of the line depth I_c - I_k over the centres;
  *   eta0 = 10, dlambdaD = 35 mA, a = 0.25, S0 = 0.25 I_c, S1 = 0.75 I_c / mu,

@@ -22,7 +22,10 @@ derivatives of Stokes I, evaluated on the filtergrams themselves:
 * azimuth (our reading of Auer et al. 1977): from the linear polarisation
   of the line wings, where the sigma components fix its sign and the
   magneto-optical rotation is small: 2 psi = atan2(sum w_k U_k,
-  sum w_k Q_k) with w_k = (c_k - cbar)^4, cbar the mean centre;
+  sum w_k Q_k) with w_k = (c_k - cbar)^4, cbar the mean centre; with more
+  than 8 samples (spectra reaching into the continuum, where the samples
+  carry only noise) w_k is multiplied by the squared relative line depth
+  ((I_c - I_k) / max_j (I_c - I_j))^2, which vanishes there;
 * the sign s_V of the longitudinal relation is that of the synthesis
   convention (``SIGN_V``), pinned by the tests on weak-field profiles;
 * B = sqrt(B_par^2 + B_perp^2), gamma = atan2(B_perp, B_par);
@@ -84,7 +87,12 @@ def weak_field(obs, filters, x, line):
     qa = np.where(den2 > 0, (Q[:, inner] * d2[:, inner]).sum(1) / safe, 0.0)
     ub = np.where(den2 > 0, (U[:, inner] * d2[:, inner]).sum(1) / safe, 0.0)
     bperp = 2.0 * np.sqrt(np.sqrt(qa * qa + ub * ub)) / C
-    wk = (c - c.mean()) ** 4
+    wk = np.broadcast_to((c - c.mean()) ** 4, I.shape)
+    if nf > 8:
+        depth = I.max(1, keepdims=True) - I
+        dmax = depth.max(1, keepdims=True)
+        rel = np.where(dmax > 0, depth / np.where(dmax > 0, dmax, 1.0), 0.0)
+        wk = wk * rel * rel
     psi = np.mod(0.5 * np.degrees(np.arctan2((U * wk).sum(1), (Q * wk).sum(1))), 180.0)
     B = np.hypot(bpar, bperp)
     gamma = np.degrees(np.arctan2(bperp, bpar))

@@ -229,7 +229,7 @@ int check_invert_args(vfisv_handle* h, const float* obs, const float* weights,
   if (npix < 0 || nfilt < 1 || nlam < 1 || nlam > 4096) return VFISV_E_SIZE;
   if (nfilt != 6 && !(nfilt > 8 && wide_supported(nfilt, nlam))) return VFISV_E_UNSUPPORTED;
   if (nfilt > 8 && cfg &&
-      (cfg->restarts || cfg->hess_reuse != 0.0 || cfg->wfa_pol != 0.0 || cfg->fast_solve ||
+      (cfg->restarts || cfg->hess_reuse != 0.0 || cfg->fast_solve ||
        ((cfg->free_mask >> 9) & 1u)))
     return VFISV_E_UNSUPPORTED;  // options of the filter-position kernel only
   return check_config(cfg, nfilt);
@@ -263,6 +263,18 @@ int invert_device_wide(vfisv_handle* h, const DevInvert& d, int nfilt, int nlam,
   char* ws = (char*)h->ws;
   float* table = (float*)(ws + L.table);
   int* err = (int*)(ws + L.err);
+  const float* init = d.init;
+  if (!init && cfg->wfa_pol > 0.0) {
+    // start from the weak-field models of the observations (Sec. 6)
+    int rc = grow(&h->geom, &h->geom_bytes, filter_geom_bytes());
+    if (!rc) rc = grow(&h->wfinit, &h->wfinit_bytes, (size_t)npix * 10 * sizeof(float));
+    if (rc) return rc;
+    if (launch_weak_field(d.obs, npix, npix_dev, d.filters, nfilt, d.wl, nlam,
+                          line_constants(line), 0, 0.0f, h->geom, (float*)h->wfinit, nullptr,
+                          s) != cudaSuccess)
+      return VFISV_E_CUDA;
+    init = (const float*)h->wfinit;
+  }
   if (launch_wide_pack(d.filters, nfilt, d.wl, nlam, table, err, s) != cudaSuccess)
     return VFISV_E_CUDA;
   if (cudaMemsetAsync(ws + L.queue, 0, sizeof(unsigned long long), s) != cudaSuccess)
@@ -271,7 +283,7 @@ int invert_device_wide(vfisv_handle* h, const DevInvert& d, int nfilt, int nlam,
   a.obs = d.obs;
   a.w = d.w;
   a.w_stride = d.w_stride;
-  a.init = d.init;
+  a.init = init;
   a.table = table;
   a.nlam = nlam;
   a.npix = npix;
@@ -591,7 +603,7 @@ int vfisv_init_models(vfisv_handle* h, const float* obs, int64_t npix, const flo
                       float* init_out, float* pol_out, void* stream) {
   if (!h || !obs || !filters || !wl_mA || !init_out || !line_ok(line)) return VFISV_E_ARG;
   if (npix < 0 || nlam < 1 || nlam > 4096) return VFISV_E_SIZE;
-  if (nfilt < 3 || nfilt > 8) return VFISV_E_UNSUPPORTED;
+  if (nfilt < 3 || nfilt > 128) return VFISV_E_UNSUPPORTED;
   if (npix == 0) return VFISV_OK;
   if (set_device(h)) return VFISV_E_CUDA;
   cudaStream_t s = (cudaStream_t)stream;

@@ -20,7 +20,14 @@ __global__ void limb_weights_kernel(const float* __restrict__ obs, const float* 
   if (p >= npix) return;
   const float* o = obs + p * 4 * nf;
   float ic = -INFINITY;
-  for (int k = 0; k < nf; ++k) ic = fmaxf(ic, o[k]);
+  float imin = INFINITY;
+  for (int k = 0; k < nf; ++k) {
+    ic = fmaxf(ic, o[k]);
+    imin = fminf(imin, o[k]);
+  }
+  // wing weights times the squared relative line depth (the outer samples
+  // of a spectrum lie in the continuum and carry only noise)
+  const float inv_dmax = (ic > imin) ? 1.0f / (ic - imin) : 0.0f;
   // Eq. 14: w_I = 0.7778 |I_cont(mu) - I_cont(x,y)| + 0.3; w_Q = w_U = w_V = 1
   const float wI = fmaf(0.7778f, fabsf(icont_mu(mu[p]) - ic * inv_ic0), 0.3f);
   float* out = w + p * 4 * nf;
@@ -44,21 +51,22 @@ cudaError_t launch_limb_weights(const float* obs, const float* mu, int64_t npix,
 // Filter geometry shared by every pixel of a launch: centres (transmission-
 // weighted mean wavelength) in increasing order, the original index of each,
 // and the wing weights (c_k - cbar)^4 of the azimuth estimate.
+constexpr int kGeomMax = 128;  // samples per Stokes parameter the initial models take
 struct FilterGeom {
-  float c[8];
-  float wing[8];
-  int order[8];
+  float c[kGeomMax];
+  float wing[kGeomMax];
+  int order[kGeomMax];
 };
 
 __global__ void filter_geom_kernel(const float* __restrict__ filters, int nf,
                                    const float* __restrict__ wl, int nlam,
                                    FilterGeom* __restrict__ g) {
-  __shared__ double cs[8];
+  __shared__ double cs[kGeomMax];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (warp < nf) {
+  for (int k = warp; k < nf; k += blockDim.x >> 5) {
     double sw = 0.0, swx = 0.0;
     for (int i = lane; i < nlam; i += 32) {
-      const double t = filters[(size_t)warp * nlam + i];
+      const double t = filters[(size_t)k * nlam + i];
       sw += t;
       swx += t * wl[i];
     }
@@ -66,11 +74,11 @@ __global__ void filter_geom_kernel(const float* __restrict__ filters, int nf,
       sw += __shfl_xor_sync(0xffffffffu, sw, o);
       swx += __shfl_xor_sync(0xffffffffu, swx, o);
     }
-    if (lane == 0) cs[warp] = swx / sw;
+    if (lane == 0) cs[k] = swx / sw;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    int ord[8];
+    int ord[kGeomMax];
     for (int k = 0; k < nf; ++k) ord[k] = k;
     for (int k = 1; k < nf; ++k)  // insertion sort, stable
       for (int j = k; j > 0 && cs[ord[j]] < cs[ord[j - 1]]; --j) {
@@ -218,16 +226,123 @@ cudaError_t launch_map_latency(const unsigned long long* t_done, const unsigned 
   return cudaGetLastError();
 }
 
+// The same estimates for many samples per Stokes parameter (spectrograph-
+// shaped inputs), with the sample count at run time: one pixel per thread,
+// two passes over the observables (I_c first, then the sums), the three-point
+// window of the differences carried along.
+__global__ void weak_field_many_kernel(const float* __restrict__ obs, int64_t npix,
+                                       const int64_t* __restrict__ npix_dev, int nf,
+                                       const FilterGeom* __restrict__ geom, LineK lk, int mode,
+                                       float pol_thr, float* __restrict__ init,
+                                       float* __restrict__ pol_out) {
+  __shared__ FilterGeom G;
+  for (int k = threadIdx.x; k < nf; k += blockDim.x) {
+    G.c[k] = geom->c[k];
+    G.wing[k] = geom->wing[k];
+    G.order[k] = geom->order[k];
+  }
+  __syncthreads();
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= (npix_dev ? *npix_dev : npix)) return;
+  const float* o = obs + p * 4 * nf;
+  float ic = -INFINITY;
+  bool finite = true;
+  for (int j = 0; j < 4 * nf; ++j) finite = finite && isfinite(o[j]);
+  if (!finite) {
+    if (pol_out) pol_out[p] = NAN;
+    if (mode == 0)
+      for (int j = 0; j < 10; ++j) init[p * 10 + j] = NAN;
+    return;
+  }
+  float imin = INFINITY;
+  for (int k = 0; k < nf; ++k) {
+    ic = fmaxf(ic, o[k]);
+    imin = fminf(imin, o[k]);
+  }
+  // wing weights times the squared relative line depth (the outer samples
+  // of a spectrum lie in the continuum and carry only noise)
+  const float inv_dmax = (ic > imin) ? 1.0f / (ic - imin) : 0.0f;
+  float s11 = 0.0f, sv1 = 0.0f, s22 = 0.0f, sq2 = 0.0f, su2 = 0.0f, wq = 0.0f, wu = 0.0f;
+  float pmax = 0.0f, depth = 0.0f, depthc = 0.0f;
+  // window: previous, current, next (in increasing centre order)
+  float Ip = 0.0f, Ic0 = o[G.order[0]], In = o[G.order[1]];
+  for (int k = 0; k < nf; ++k) {
+    const int j = G.order[k];
+    const float Q = o[nf + j], U = o[2 * nf + j], V = o[3 * nf + j];
+    float d1;
+    if (k == 0) {
+      d1 = (In - Ic0) / (G.c[1] - G.c[0]);
+    } else if (k == nf - 1) {
+      d1 = (Ic0 - Ip) / (G.c[k] - G.c[k - 1]);
+    } else {
+      d1 = (In - Ip) / (G.c[k + 1] - G.c[k - 1]);
+      const float right = (In - Ic0) / (G.c[k + 1] - G.c[k]);
+      const float left = (Ic0 - Ip) / (G.c[k] - G.c[k - 1]);
+      const float d2 = 2.0f * (right - left) / (G.c[k + 1] - G.c[k - 1]);
+      s22 = fmaf(d2, d2, s22);
+      sq2 = fmaf(Q, d2, sq2);
+      su2 = fmaf(U, d2, su2);
+    }
+    s11 = fmaf(d1, d1, s11);
+    sv1 = fmaf(V, d1, sv1);
+    const float rd = (ic - Ic0) * inv_dmax;
+    const float wk = G.wing[k] * rd * rd;
+    wq = fmaf(wk, Q, wq);
+    wu = fmaf(wk, U, wu);
+    pmax = fmaxf(pmax, sqrtf(fmaf(Q, Q, fmaf(U, U, V * V))));
+    const float d = ic - Ic0;
+    depth += d;
+    depthc = fmaf(d, G.c[k], depthc);
+    Ip = Ic0;
+    Ic0 = In;
+    In = (k + 2 < nf) ? o[G.order[k + 2]] : 0.0f;
+  }
+  const float C = lk.cB;
+  const float bpar = (s11 > 0.0f) ? -sv1 / (s11 * C) : 0.0f;
+  const float qa = (s22 > 0.0f) ? sq2 / s22 : 0.0f, ub = (s22 > 0.0f) ? su2 / s22 : 0.0f;
+  const float bperp = 2.0f * sqrtf(sqrtf(fmaf(qa, qa, ub * ub))) / C;
+  float psi = 0.5f * atan2f(wu, wq) * (1.0f / kDeg);
+  if (psi < 0.0f) psi += 180.0f;
+  const float B = sqrtf(fmaf(bpar, bpar, bperp * bperp));
+  const float gamma = atan2f(bperp, bpar) * (1.0f / kDeg);
+  const float pol = pmax / ic;
+  if (pol_out) pol_out[p] = pol;
+  float m[10];
+  if (mode == 0) {
+    const float lam = (depth > 0.0f) ? depthc / depth : 0.0f;
+    m[0] = B; m[1] = gamma; m[2] = psi;
+    m[3] = 10.0f; m[4] = 35.0f; m[5] = 0.25f;
+    m[6] = lam / lk.cv;
+    m[7] = 0.25f * ic;
+    m[8] = 0.75f * ic / lk.mu;
+    m[9] = 1.0f;
+  } else {
+    for (int j = 0; j < 10; ++j) m[j] = init[p * 10 + j];
+    if (pol < pol_thr) {
+      m[0] = B;
+      m[1] = gamma;
+    }
+    m[2] = psi;
+  }
+  apply_bounds(m);
+  for (int j = 0; j < 10; ++j) init[p * 10 + j] = m[j];
+}
+
 size_t filter_geom_bytes() { return sizeof(FilterGeom); }
 
 cudaError_t launch_weak_field(const float* obs, int64_t npix, const int64_t* npix_dev,
                               const float* filters, int nf, const float* wl, int nlam,
                               const LineK& lk, int mode, float pol_thr, void* geom, float* init,
                               float* pol_out, cudaStream_t s) {
-  if (nf < 3 || nf > 8) return cudaErrorInvalidValue;
+  if (nf < 3 || nf > kGeomMax) return cudaErrorInvalidValue;
   filter_geom_kernel<<<1, 256, 0, s>>>(filters, nf, wl, nlam, (FilterGeom*)geom);
   const unsigned grid = (unsigned)((npix + 255) / 256);
   const FilterGeom* g = (const FilterGeom*)geom;
+  if (nf > 8) {
+    weak_field_many_kernel<<<grid, 256, 0, s>>>(obs, npix, npix_dev, nf, g, lk, mode, pol_thr,
+                                                init, pol_out);
+    return cudaGetLastError();
+  }
   switch (nf) {
     case 3: weak_field_kernel<3><<<grid, 256, 0, s>>>(obs, npix, npix_dev, g, lk, mode, pol_thr, init, pol_out); break;
     case 4: weak_field_kernel<4><<<grid, 256, 0, s>>>(obs, npix, npix_dev, g, lk, mode, pol_thr, init, pol_out); break;

@@ -85,3 +85,60 @@ def test_wide_band_too_wide_is_reported(vf):
     x2, T2 = _coarse(16)
     v.vfisv_synth(h, p, T2.astype(np.float32), x2.astype(np.float32), LINE)
     v.vfisv_check(h)
+
+
+def test_wide_initial_models_vs_oracle(vf):
+    """Weak-field initial models from 112-sample spectra (Sec. 6) vs the
+    oracle's, with the tolerances of the filtergram test."""
+    from oracle import init
+    v, h, torch = vf
+    n = 2000
+    p = f32(W.quiet_and_active_params(n, 103))
+    s = me.synth(p, f32(TS), f32(XS), LINE).reshape(n, -1)
+    obs, w = W.observe(s, p, W.noise(n, s.shape[1], 103))
+    obs = f32(obs)
+    g = v.vfisv_init_models(h, obs.astype(np.float32), TS.astype(np.float32),
+                            XS.astype(np.float32), LINE)
+    ref = init.initial_models(obs, f32(TS), f32(XS), LINE)
+    wf = init.weak_field(obs, f32(TS), f32(XS), LINE)
+    gi = g["init"].astype(np.float64)
+    np.testing.assert_allclose(gi[:, 0], ref[:, 0], rtol=2e-3, atol=0.5)
+    assert np.abs(gi[:, 1] - ref[:, 1]).max() < 0.1
+    np.testing.assert_allclose(gi[:, 6], ref[:, 6], rtol=1e-3, atol=2e-3)
+    np.testing.assert_allclose(g["pol"], wf["pol"], rtol=1e-5)
+    c = init.filter_centres(f32(TS), f32(XS))
+    i_ = obs[:, :112]
+    depth = i_.max(1, keepdims=True) - i_
+    wk = (c - c.mean())[None, :] ** 4 * (depth / depth.max(1, keepdims=True)) ** 2
+    q, u = obs[:, 112:224], obs[:, 224:336]
+    strong = np.hypot((q * wk).sum(1), (u * wk).sum(1)) / wk.sum(1) > 1e-5
+    dpsi = np.abs((gi[:, 2] - ref[:, 2] + 90.0) % 180.0 - 90.0)
+    assert strong.mean() > 0.5 and dpsi[strong].max() < 0.1
+    # the estimates themselves: with 112 samples the weak-field B is close
+    weak = p[:, 0] < 800
+    print(f"spectrograph weak-field B: median |dB| {np.median(np.abs(gi[weak, 0] - p[weak, 0])):.1f} G "
+          f"(B < 800 G), psi within 10 deg {np.mean(np.abs((gi[:, 2] - p[:, 2] + 90) % 180 - 90) < 10):.3f}")
+
+
+def test_wide_weak_field_start(vf):
+    """The spectrograph path started from the weak-field models (wfa_pol > 0):
+    parity with the oracle started from its own, and the effect on the
+    iteration count against the standard guess."""
+    v, h, torch = vf
+    n = 160
+    p = f32(W.quiet_and_active_params(n, 104))
+    s = me.synth(p, f32(TS), f32(XS), LINE).reshape(n, -1)
+    obs, w = W.observe(s, p, W.noise(n, s.shape[1], 104))
+    obs, w = f32(obs), f32(w)
+    t = lambda a: torch.tensor(np.asarray(a, dtype=np.float32), device="cuda:0")  # noqa: E731
+    r = v.vfisv_invert(h, t(obs), t(w), t(TS), t(XS), LINE, config={"wfa_pol": 1.0})
+    v.vfisv_check(h)
+    g = {k: x.cpu().numpy() for k, x in r.items()}
+    o = lm.invert(obs, w, f32(TS), f32(XS), LINE, wfa_pol=1.0)
+    both = np.isin(g["status"], (0, 2)) & np.isin(o["status"], (0, 2))
+    rel = np.abs(g["chi2"][both] / o["chi2"][both] - 1)
+    assert both.mean() > 0.5 and np.mean(rel <= 1e-3) >= 0.95
+    std = v.vfisv_invert(h, t(obs), t(w), t(TS), t(XS), LINE)
+    print(f"spectrograph start: weak-field {g['iters'].mean():.1f} iterations, converged "
+          f"{np.isin(g['status'], (0, 2)).mean():.3f}; standard guess {std['iters'].float().mean().item():.1f}, "
+          f"{torch.isin(std['status'], torch.tensor([0, 2], device='cuda:0')).float().mean().item():.3f}")
