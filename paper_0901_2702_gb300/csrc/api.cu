@@ -908,7 +908,15 @@ int vfisv_invert_batch(vfisv_handle* h, const float* obs, const float* weights,
       cudaMemsetAsync(done, 0, b_cnt, s) != cudaSuccess ||
       cudaMemsetAsync(tdone, 0, b_cnt, s) != cudaSuccess)
     return VFISV_E_CUDA;
-  if (npix == 0) return VFISV_OK;
+  if (npix == 0) {  // every map empty: latencies 0
+    if (!latency_ms) return VFISV_OK;
+    if (is_device_ptr(latency_ms))
+      return cudaMemsetAsync(latency_ms, 0, (size_t)nmaps * sizeof(float), s) == cudaSuccess
+                 ? VFISV_OK
+                 : VFISV_E_CUDA;
+    memset(latency_ms, 0, (size_t)nmaps * sizeof(float));
+    return VFISV_OK;
+  }
   Staging st;
   st.add(obs, (size_t)npix * nobs * sizeof(float), false);
   st.add(weights, (size_t)nmaps * nobs * sizeof(float), false);
