@@ -38,12 +38,28 @@ def gelu_grad(x):
     return cdf + x * pdf
 
 
-def forward(weights, x):
-    """weights = [(W0,b0),...,(W3,b3)]; returns (y, cache)."""
+def round_bf16(x):
+    """Round to the nearest bfloat16 value (8 significant bits, the FP32
+    exponent range), ties to even: x = m 2^e with 1/2 <= |m| < 1, and m 2^8
+    rounded to an integer.  Values far outside the network's range (FP32
+    overflow, subnormals) are not handled."""
+    m, e = np.frexp(np.asarray(x, dtype=np.float64))
+    return np.ldexp(np.round(m * 256.0), e - 8)
+
+
+def forward(weights, x, operand_round=None):
+    """weights = [(W0,b0),...,(W3,b3)]; returns (y, cache).
+
+    ``operand_round`` (e.g. ``round_bf16``) is applied to every layer's input
+    and weight matrix before the product, which is then formed exactly in
+    FP64 -- the arithmetic of a tensor-core layer with rounded operands and a
+    wide accumulator (biases and activations unrounded)."""
     h = np.asarray(x, dtype=np.float64)
     cache = []
     nl = len(weights)
     for l, (W, b) in enumerate(weights):
+        if operand_round is not None:
+            h, W = operand_round(h), operand_round(W)
         z = h @ W + b
         cache.append((h, z))
         h = gelu(z) if l < nl - 1 else z

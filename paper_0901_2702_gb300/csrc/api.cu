@@ -105,6 +105,8 @@ int grow(void** buf, size_t* have, size_t need) {
     *buf = nullptr;
     return VFISV_E_NOMEM;
   }
+  // a workspace starts with the device error word: clear it
+  if (cudaMemset(*buf, 0, need < 256 ? need : 256) != cudaSuccess) return VFISV_E_CUDA;
   *have = need;
   return VFISV_OK;
 }
@@ -672,15 +674,19 @@ int vfisv_check(vfisv_handle* h, void* stream) {
   cudaStream_t s = (cudaStream_t)stream;
   if (cudaStreamSynchronize(s) != cudaSuccess) return VFISV_E_CUDA;
   if (cudaGetLastError() != cudaSuccess) return VFISV_E_CUDA;
-  if (!h->ws) return VFISV_OK;
-  int e = 0;
-  if (cudaMemcpy(&e, h->ws, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
-    return VFISV_E_CUDA;
-  if (e) {
-    cudaMemset(h->ws, 0, sizeof(int));
-    return VFISV_E_DEVICE;
+  // error words: the inversion workspace and the network workspace
+  int bad = 0;
+  for (void* w : {h->ws, h->nnws}) {
+    if (!w) continue;
+    int e = 0;
+    if (cudaMemcpy(&e, w, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+      return VFISV_E_CUDA;
+    if (e) {
+      cudaMemset(w, 0, sizeof(int));
+      bad = 1;
+    }
   }
-  return VFISV_OK;
+  return bad ? VFISV_E_DEVICE : VFISV_OK;
 }
 
 int vfisv_synth(vfisv_handle* h, const float* params, int64_t npix, const float* filters,
@@ -838,8 +844,6 @@ int vfisv_nn_grad(vfisv_handle* h, const float* blob, const float* obs, const fl
   return st.finish(s);
 }
 
-static constexpr int64_t kInferChunk = 65536;
-
 int vfisv_nn_infer(vfisv_handle* h, const float* blob, const float* obs, int64_t npix,
                    const vfisv_line* line, float* init_out, float* conf_out, float* raw_out,
                    void* stream) {
@@ -856,8 +860,8 @@ int vfisv_nn_infer(vfisv_handle* h, const float* blob, const float* obs, int64_t
   st.add(raw_out, raw_out ? (size_t)npix * nn::OUT * sizeof(float) : 0, true);
   int rc = st.prepare(h, s);
   if (rc) return rc;
-  if ((rc = grow(&h->nnws, &h->nnws_bytes, nn::workspace_bytes(kInferChunk)))) return rc;
-  if (nn::nn_infer(h->nnws, kInferChunk, (const float*)st.bufs[0].dev,
+  if ((rc = grow(&h->nnws, &h->nnws_bytes, nn::infer_workspace_bytes()))) return rc;
+  if (nn::nn_infer(h->nnws, (const float*)st.bufs[0].dev,
                    (const float*)st.bufs[1].dev, npix, (float)line->mu,
                    (float*)st.bufs[2].dev, (float*)st.bufs[3].dev, (float*)st.bufs[4].dev,
                    s) != cudaSuccess)
@@ -1003,10 +1007,10 @@ int vfisv_invert_nn(vfisv_handle* h, const float* blob, const float* obs, const 
                o_i = place((size_t)npix * 4), o_s = place((size_t)npix * 4),
                o_v = cov ? place((size_t)npix * 100 * 4) : 0;
   if ((rc = grow(&h->mixws, &h->mixws_bytes, off))) return rc;
-  if ((rc = grow(&h->nnws, &h->nnws_bytes, nn::workspace_bytes(kInferChunk)))) return rc;
+  if ((rc = grow(&h->nnws, &h->nnws_bytes, nn::infer_workspace_bytes()))) return rc;
   char* mw = (char*)h->mixws;
   float* init = (float*)(mw + o_init);
-  if (nn::nn_infer(h->nnws, kInferChunk, (const float*)st.bufs[4].dev, o, npix, (float)line->mu,
+  if (nn::nn_infer(h->nnws, (const float*)st.bufs[4].dev, o, npix, (float)line->mu,
                    init, nullptr, nullptr, s) != cudaSuccess)
     return VFISV_E_CUDA;
   if (cfg_nn->wfa_pol > 0.0) {

@@ -11,7 +11,7 @@
 namespace vfisv {
 
 // Device error codes written to the handle's error word.
-enum : int { kDevErrNone = 0, kDevErrTableWait = 1 };
+enum : int { kDevErrNone = 0, kDevErrTableWait = 1, kDevErrNnWait = 2 };
 
 // Filter table layout in global and shared memory: nlam rows of `stride`
 // floats {T_0(x_i), ..., T_{nf-1}(x_i), x_i, pad...}, then one row holding

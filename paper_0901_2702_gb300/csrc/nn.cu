@@ -13,6 +13,7 @@
 
 #include "common.cuh"
 #include "nn.cuh"
+#include "nn_device.cuh"
 
 namespace vfisv {
 namespace nn {
@@ -54,16 +55,6 @@ __device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], 
       "{%8,%9}, {%0,%1,%2,%3};"
       : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-
-// GELU(x) = x Phi(x) and its derivative Phi(x) + x phi(x).
-__device__ __forceinline__ float gelu(float x) {
-  return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f));
-}
-__device__ __forceinline__ float gelu_grad(float x) {
-  const float cdf = 0.5f * (1.0f + erff(x * 0.70710678118654752f));
-  const float pdf = 0.39894228040143268f * expf(-0.5f * x * x);
-  return fmaf(x, pdf, cdf);
 }
 
 // ---------------------------------------------------------------------------
@@ -229,13 +220,6 @@ static cudaError_t gemm(const GemmArgs& g, int splits, cudaStream_t s) {
 // mult < n, offset + m < 2n and n < 2^31 keep the product inside 64 bits.
 __device__ __forceinline__ int64_t sample_of(int64_t m, const Perm& p) {
   return (int64_t)((p.mult * (uint64_t)(p.offset + m) + p.add) % (uint64_t)p.n);
-}
-
-__device__ __forceinline__ float ic_of(const float* o) {
-  float ic = -INFINITY;
-#pragma unroll
-  for (int j = 0; j < 6; ++j) ic = fmaxf(ic, o[j]);
-  return fmaxf(ic, 1e-30f);
 }
 
 __global__ void features_kernel(const float* __restrict__ obs, int64_t rows, int64_t mpad,
@@ -482,35 +466,6 @@ __global__ void stats_final_kernel(const double* __restrict__ part, int nblocks,
   }
 }
 
-// Network outputs -> initial model (and confidence): inverse of the targets.
-__global__ void decode_kernel(const float* __restrict__ Y, const float* __restrict__ ic,
-                              const float* __restrict__ blob, int64_t n, float mu,
-                              float* __restrict__ init, float* __restrict__ conf,
-                              float* __restrict__ raw) {
-  const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (m >= n) return;
-  const float* y = Y + m * N3P;
-  float t[OUT - 1];
-#pragma unroll
-  for (int o = 0; o < OUT - 1; ++o) t[o] = fmaf(y[o], blob[OFF_OUTS + o], blob[OFF_OUTM + o]);
-  float* p = init + m * 10;
-  p[0] = fmaxf(t[0], 0.0f);
-  p[1] = acosf(fminf(fmaxf(t[1], -1.0f), 1.0f)) * 57.295779513082321f;
-  float ps = 0.5f * atan2f(t[2], t[3]) * 57.295779513082321f;
-  if (ps < 0.0f) ps += 180.0f;
-  p[2] = ps;
-  p[3] = expf(t[4]);
-  p[4] = t[5];
-  p[5] = t[6];
-  p[6] = t[7];
-  p[7] = t[8] * ic[m];
-  p[8] = t[9] * ic[m] / mu;
-  p[9] = 1.0f;
-  if (conf) conf[m] = y[OUT - 1];
-  if (raw)
-    for (int o = 0; o < OUT; ++o) raw[m * OUT + o] = y[o];
-}
-
 // ---------------------------------------------------------------------------
 // host side
 
@@ -530,6 +485,7 @@ static Bufs carve(void* ws, int64_t M, size_t* used = nullptr) {
     return r;
   };
   Bufs b;
+  take(infer_workspace_bytes());  // error word and packed inference weights
   b.X0 = (bf16*)take((size_t)M * K0P * 2);
   for (int i = 0; i < 3; ++i) {
     b.Z[i] = (float*)take((size_t)M * HID * 4);
@@ -728,27 +684,6 @@ cudaError_t nn_train(void* ws, float* blob, const float* obs, const float* param
     adam_kernel<<<(int)((NTRAIN + 255) / 256), 256, 0, s>>>(
         blob, b.grad, b.m, b.v, (int)NTRAIN, (float)lr, b1, b2, (float)(1.0 - p1),
         (float)(1.0 - p2), eps);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  }
-  return cudaSuccess;
-}
-
-cudaError_t nn_infer(void* ws, int64_t chunk_rows, const float* blob, const float* obs,
-                     int64_t n, float mu, float* init, float* conf, float* raw,
-                     cudaStream_t s) {
-  Bufs b = carve(ws, chunk_rows);
-  cudaError_t e;
-  if ((e = pack(blob, b.P, s)) != cudaSuccess) return e;
-  for (int64_t r0 = 0; r0 < n; r0 += chunk_rows) {
-    const int64_t rows = (n - r0 < chunk_rows) ? n - r0 : chunk_rows;
-    const int64_t M = round_up(rows, BM);
-    Perm id{1, 0, 0, rows};
-    features_kernel<<<(unsigned)((M + 255) / 256), 256, 0, s>>>(obs + r0 * IN, rows, M, id,
-                                                                blob, b.X0, b.ic);
-    if ((e = forward(blob, b, M, s)) != cudaSuccess) return e;
-    decode_kernel<<<(unsigned)((rows + 255) / 256), 256, 0, s>>>(
-        b.Y, b.ic, blob, rows, mu, init + r0 * 10, conf ? conf + r0 : nullptr,
-        raw ? raw + r0 * OUT : nullptr);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   return cudaSuccess;

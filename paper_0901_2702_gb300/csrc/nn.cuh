@@ -60,9 +60,14 @@ cudaError_t nn_grad(void* ws, const float* blob, const float* obs, const float* 
 cudaError_t nn_train(void* ws, float* blob, const float* obs, const float* params, int64_t n,
                      int batch, int epochs, float lr0, uint64_t seed, float* loss_hist,
                      cudaStream_t s);
-cudaError_t nn_infer(void* ws, int64_t chunk_rows, const float* blob, const float* obs,
-                     int64_t n, float mu, float* init, float* conf, float* raw,
-                     cudaStream_t s);
+// Inference (mlp_tc.cu): one fused tensor-core kernel from observations to
+// initial models.  The workspace holds the device error word (first
+// kNnErrBytes) and the packed BF16 weights (kTcPackBytes after it).
+constexpr size_t kNnErrBytes = 256;
+constexpr size_t kTcPackBytes = 286720;
+constexpr size_t infer_workspace_bytes() { return kNnErrBytes + kTcPackBytes; }
+cudaError_t nn_infer(void* ws, const float* blob, const float* obs, int64_t n, float mu,
+                     float* init, float* conf, float* raw, cudaStream_t s);
 // rows the gradient/forward paths pad a batch of n samples to
 int64_t padded_rows(int64_t n);
 

@@ -115,3 +115,42 @@ def test_blob_gradient_vs_finite_differences():
                                                mlp.targets(p, obs, st), c0)[0]
         fd = (f(bp) - f(bm)) / 2e-6
         assert abs(fd - g[o]) < 1e-6 * max(1.0, abs(fd)), (name, fd, g[o])
+
+
+def test_round_bf16_ties_and_library():
+    # ties go to the even neighbour; anything above a tie goes up
+    one = 1.0
+    assert mlp.round_bf16(one + 2.0 ** -8) == one                  # tie, 1.0 is even
+    assert mlp.round_bf16(one + 3 * 2.0 ** -8) == one + 2.0 ** -6  # tie, rounds up to even
+    assert mlp.round_bf16(one + 2.0 ** -8 + 2.0 ** -20) == one + 2.0 ** -7
+    assert mlp.round_bf16(-(one + 2.0 ** -8 + 2.0 ** -20)) == -(one + 2.0 ** -7)
+    assert mlp.round_bf16(0.0) == 0.0
+    assert mlp.round_bf16(3.0 * 2.0 ** 100) == 3.0 * 2.0 ** 100
+    # FP32 values against the library's float32 -> bfloat16 conversion
+    torch = __import__("pytest").importorskip("torch")
+    rng = np.random.default_rng(11)
+    x = (rng.standard_normal(20000) * np.exp(rng.uniform(-20, 20, 20000))).astype(np.float32)
+    ref = torch.from_numpy(x).to(torch.bfloat16).to(torch.float64).numpy()
+    np.testing.assert_array_equal(mlp.round_bf16(x.astype(np.float64)), ref)
+
+
+def test_forward_with_rounded_operands():
+    rng = np.random.default_rng(5)
+    net = _net(rng)
+    x = rng.normal(size=(7, 5))
+    y, _ = mlp.forward(net, x)
+    yr, cache = mlp.forward(net, x, operand_round=mlp.round_bf16)
+    # the same layers written out with rounded operands
+    h = x
+    for l, (W, b) in enumerate(net):
+        z = mlp.round_bf16(h) @ mlp.round_bf16(W) + b
+        h = mlp.gelu(z) if l < len(net) - 1 else z
+    np.testing.assert_allclose(yr, h, rtol=0, atol=1e-14)
+    # the rounding moves each operand by at most 2^-9 relative: a small change
+    assert 0 < np.abs(yr - y).max() < 0.05
+    # a single layer whose operands are already on the bfloat16 grid: the
+    # rounding is the identity
+    W, b = mlp.round_bf16(net[0][0]), net[0][1]
+    xg = mlp.round_bf16(x)
+    np.testing.assert_array_equal(mlp.forward([(W, b)], xg, operand_round=mlp.round_bf16)[0],
+                                  xg @ W + b)
