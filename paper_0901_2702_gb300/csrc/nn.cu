@@ -515,7 +515,7 @@ static Bufs carve(void* ws, int64_t M, size_t* used = nullptr) {
 size_t workspace_bytes(int64_t rows) {
   size_t used = 0;
   carve(nullptr, round_up(rows, BM), &used);
-  const size_t stats = (size_t)256 * 2 * (IN + OUT - 1) * sizeof(double);
+  const size_t stats = infer_workspace_bytes() + (size_t)256 * 2 * (IN + OUT - 1) * sizeof(double);
   return used > stats ? used : stats;
 }
 
@@ -619,7 +619,7 @@ cudaError_t nn_init(void* ws, float* blob, const float* obs, const float* params
                     uint64_t seed, cudaStream_t s) {
   init_weights_kernel<<<dim3(64, 4), 256, 0, s>>>(blob, seed);
   const int nb = 256;
-  double* part = (double*)ws;
+  double* part = (double*)((char*)ws + infer_workspace_bytes());  // after the error word
   stats_partial_kernel<<<nb, 256, 0, s>>>(obs, params, n, part);
   stats_final_kernel<<<1, 64, 0, s>>>(part, nb, n, blob);
   return cudaGetLastError();

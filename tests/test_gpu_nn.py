@@ -37,6 +37,7 @@ def test_init_statistics_match_oracle(vf):
     ref = mlp.statistics(obs, p)
     for k in ref:
         np.testing.assert_allclose(st[k], ref[k], rtol=2e-4, atol=1e-6)
+    v.vfisv_check(h)  # the device error words stay clear
     lay = mlp.blob_layout()
     W0 = blob[lay["W0"][0]:lay["W0"][0] + 24 * 256]
     assert np.abs(W0).max() <= np.sqrt(6 / 24) and abs(W0.mean()) < 0.02
@@ -87,6 +88,7 @@ def test_tensor_core_forward_vs_rounded_operand_oracle(vf, n):
     assert np.median(err) < 1e-5 and err.mean() < 2e-4 and err.max() < 3e-2, \
         (np.median(err), err.mean(), err.max())
     np.testing.assert_array_equal(r["conf"], r["raw"][:, 10])
+    v.vfisv_check(h)
     m = mlp.decode(r["raw"].astype(np.float64), obs, st)
     np.testing.assert_allclose(r["init"][:, [0, 3, 5, 6, 7, 8]], m[:, [0, 3, 5, 6, 7, 8]],
                                rtol=2e-5, atol=2e-3)
