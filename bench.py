@@ -382,10 +382,8 @@ def run_ours(args, rank, world):
                              f"{achieved / fp32_peak_tflops(sm_mhz):.3f}"},
         "clocks": clocks,
     }
-    # our kernel launches per mixed step: network (pack + per 65536-pixel chunk:
-    # features, 4 GEMMs, decode), 2 x (table pack, LM, covariance), flag, merge
-    chunks = (npix + 65535) // 65536
-    res["gpu_launches"] = args.steps * (1 + 6 * chunks + 2 * 3 + 2)
+    # our kernel launches in the timed region: the kernel nodes of the replayed graph
+    res["gpu_launches"] = args.steps * graph_mixed.kernels()
     graph_mixed.close()
     graph_plain.close()
     h.close()
@@ -573,10 +571,8 @@ def run_serving(args):
                                   "retirement of its last pixel (GPU global timer)"},
            "per_map_latency_ms": {str(m): float(x) for m, x in zip(idsF + idsS, lat)},
            "ms_per_step_all": times, "input_generation_s": gen_s, "clocks": clocks,
-           # per step: network (pack + 6 per 65,536-pixel chunk), then per half
-           # start stamp, table pack, LM kernel, covariance, latency, and the
-           # spectrograph half's filter geometry and weak-field models
-           "gpu_launches": args.steps * (1 + 6 * ((nF + 65535) // 65536) + 5 + 5 + 2)}
+           # kernel nodes of the two replayed graphs
+           "gpu_launches": args.steps * (gF.kernels() + gS.kernels())}
     gF.close()
     gS.close()
     print(json.dumps(res))

@@ -262,6 +262,10 @@ typedef struct vfisv_graph vfisv_graph;
 int vfisv_graph_begin(vfisv_handle* h, void* stream);
 int vfisv_graph_end(vfisv_handle* h, void* stream, vfisv_graph** out);
 int vfisv_graph_launch(vfisv_graph* g, void* stream);
+/* Number of kernel launches one replay of the graph performs (kernel nodes,
+ * child graphs included), written to *count.  VFISV_E_ARG for a null graph
+ * or count. */
+int vfisv_graph_kernels(const vfisv_graph* g, int64_t* count);
 void vfisv_graph_destroy(vfisv_graph* g);
 
 /* Autotuner: time the LM kernel with 64, 128 and 256 pixel slots per CTA on

@@ -19,7 +19,7 @@ __all__ = [
     "vfisv_create", "vfisv_destroy", "vfisv_synth", "vfisv_invert", "vfisv_check",
     "vfisv_strerror", "vfisv_config_default", "vfisv_nn_init", "vfisv_nn_train",
     "vfisv_nn_grad", "vfisv_nn_infer", "vfisv_invert_nn", "vfisv_graph_begin", "vfisv_graph_end",
-    "vfisv_graph_launch", "vfisv_graph_destroy", "vfisv_autotune", "vfisv_voigt",
+    "vfisv_graph_launch", "vfisv_graph_kernels", "vfisv_graph_destroy", "vfisv_autotune", "vfisv_voigt",
     "vfisv_limb_weights", "vfisv_restart_models", "vfisv_init_models", "vfisv_invert_batch",
     "VfisvError",
     "library_path",
@@ -104,6 +104,8 @@ def load():
     lib.vfisv_graph_end.restype = ctypes.c_int
     lib.vfisv_graph_launch.argtypes = [P, P]
     lib.vfisv_graph_launch.restype = ctypes.c_int
+    lib.vfisv_graph_kernels.argtypes = [P, ctypes.POINTER(I64)]
+    lib.vfisv_graph_kernels.restype = ctypes.c_int
     lib.vfisv_graph_destroy.argtypes = [P]
     lib.vfisv_graph_destroy.restype = None
     lib.vfisv_autotune.argtypes = [P, P, P, I32, P, I32, P, I32, ctypes.POINTER(vfisv_line),
@@ -403,6 +405,10 @@ class Graph:
     def launch(self, stream):
         vfisv_graph_launch(self, stream)
 
+    def kernels(self) -> int:
+        """Kernel launches one replay performs."""
+        return vfisv_graph_kernels(self)
+
     def close(self):
         if getattr(self, "ptr", None):
             load().vfisv_graph_destroy(self.ptr)
@@ -430,6 +436,12 @@ def vfisv_graph_end(h: Handle, stream) -> Graph:
 def vfisv_graph_launch(g: Graph, stream) -> None:
     _check(load().vfisv_graph_launch(g.ptr, ctypes.c_void_p(_stream(None, stream))),
            "vfisv_graph_launch")
+
+
+def vfisv_graph_kernels(g: Graph) -> int:
+    n = ctypes.c_int64(0)
+    _check(load().vfisv_graph_kernels(g.ptr, ctypes.byref(n)), "vfisv_graph_kernels")
+    return int(n.value)
 
 
 def vfisv_graph_destroy(g: Graph) -> None:

@@ -34,6 +34,12 @@ struct vfisv_handle {
   int64_t* mapoff_host = nullptr;  // pinned copy of the caller's map offsets
   size_t mapoff_host_bytes = 0;
   bool capturing = false;  // between vfisv_graph_begin and vfisv_graph_end
+  // host-buffer pipeline: two device slots, copy-in / copy-out streams and
+  // their events (created on first use)
+  void* pipe = nullptr;
+  size_t pipe_bytes = 0;
+  cudaStream_t pipe_in = nullptr, pipe_out = nullptr;
+  cudaEvent_t pipe_ev[7] = {};
 };
 
 struct vfisv_graph {
@@ -181,6 +187,100 @@ struct Staging {
     return VFISV_OK;
   }
 };
+
+// Host-buffer pipeline for per-pixel calls on large maps.  Rows [0, npix)
+// run in kPipeChunks chunks; each chunk's host inputs are copied in on one
+// stream and its host outputs copied back on another, through two device
+// slots, while the caller's stream computes the previous chunk -- so the
+// host<->device traffic hides behind the inversion.  Every per-pixel result
+// depends on that pixel alone, so the outputs equal those of one call over
+// the whole map.  Device pointers among the rows are used in place.
+constexpr int kPipeChunks = 4;
+constexpr int64_t kPipeMinRows = 1 << 20;
+
+struct RowArg {
+  const void* user;  // caller pointer (host or device) or null
+  size_t row_bytes;  // bytes per pixel
+  bool out;
+};
+
+template <class Run>
+int pipeline_rows(vfisv_handle* h, cudaStream_t s, int64_t npix, RowArg* args, int nargs,
+                  Run run) {
+  const int64_t chunk = (npix + kPipeChunks - 1) / kPipeChunks;
+  std::vector<bool> host(nargs);
+  size_t slot = 0;
+  for (int i = 0; i < nargs; ++i) {
+    host[i] = args[i].user && !is_device_ptr(args[i].user);
+    if (host[i]) slot += up((size_t)chunk * args[i].row_bytes);
+  }
+  int rc = grow(&h->pipe, &h->pipe_bytes, 2 * slot);
+  if (rc) return rc;
+  if (!h->pipe_in) {
+    if (cudaStreamCreateWithFlags(&h->pipe_in, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&h->pipe_out, cudaStreamNonBlocking) != cudaSuccess)
+      return VFISV_E_CUDA;
+    for (cudaEvent_t& e : h->pipe_ev)
+      if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return VFISV_E_CUDA;
+  }
+  cudaEvent_t* ev_in = h->pipe_ev + 1;    // chunk's inputs in slot j
+  cudaEvent_t* ev_done = h->pipe_ev + 3;  // chunk computed
+  cudaEvent_t* ev_free = h->pipe_ev + 5;  // slot j copied out
+  // the copies start after the work already queued on the caller's stream
+  if (cudaEventRecord(h->pipe_ev[0], s) != cudaSuccess ||
+      cudaStreamWaitEvent(h->pipe_in, h->pipe_ev[0], 0) != cudaSuccess ||
+      cudaStreamWaitEvent(h->pipe_out, h->pipe_ev[0], 0) != cudaSuccess)
+    return VFISV_E_CUDA;
+  std::vector<void*> dev(nargs);
+  for (int64_t k = 0; k * chunk < npix; ++k) {
+    const int j = (int)(k & 1);
+    const int64_t off = k * chunk, n = npix - off < chunk ? npix - off : chunk;
+    char* base = (char*)h->pipe + (size_t)j * slot;
+    for (int i = 0; i < nargs; ++i) {
+      if (!args[i].user) {
+        dev[i] = nullptr;
+      } else if (!host[i]) {
+        dev[i] = (char*)args[i].user + (size_t)off * args[i].row_bytes;
+      } else {
+        dev[i] = base;
+        base += up((size_t)chunk * args[i].row_bytes);
+      }
+    }
+    if (k >= 2 && cudaStreamWaitEvent(h->pipe_in, ev_free[j], 0) != cudaSuccess)
+      return VFISV_E_CUDA;
+    for (int i = 0; i < nargs; ++i)
+      if (host[i] && !args[i].out &&
+          cudaMemcpyAsync(dev[i], (const char*)args[i].user + (size_t)off * args[i].row_bytes,
+                          (size_t)n * args[i].row_bytes, cudaMemcpyHostToDevice,
+                          h->pipe_in) != cudaSuccess)
+        return VFISV_E_CUDA;
+    if (cudaEventRecord(ev_in[j], h->pipe_in) != cudaSuccess ||
+        cudaStreamWaitEvent(s, ev_in[j], 0) != cudaSuccess)
+      return VFISV_E_CUDA;
+    if ((rc = run(n, dev.data())) != VFISV_OK) return rc;
+    if (cudaEventRecord(ev_done[j], s) != cudaSuccess ||
+        cudaStreamWaitEvent(h->pipe_out, ev_done[j], 0) != cudaSuccess)
+      return VFISV_E_CUDA;
+    for (int i = 0; i < nargs; ++i)
+      if (host[i] && args[i].out &&
+          cudaMemcpyAsync((char*)args[i].user + (size_t)off * args[i].row_bytes, dev[i],
+                          (size_t)n * args[i].row_bytes, cudaMemcpyDeviceToHost,
+                          h->pipe_out) != cudaSuccess)
+        return VFISV_E_CUDA;
+    if (cudaEventRecord(ev_free[j], h->pipe_out) != cudaSuccess) return VFISV_E_CUDA;
+  }
+  if (cudaStreamSynchronize(h->pipe_out) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return VFISV_E_CUDA;
+  return VFISV_OK;
+}
+
+// Large maps in host memory take the pipeline (not while capturing a graph,
+// and not with restarts, whose random draws are keyed by the pixel's index
+// within the call).
+bool pipeline_host(const vfisv_handle* h, const void* obs, int64_t npix, bool no_restarts) {
+  return !h->capturing && no_restarts && npix >= kPipeMinRows && !is_device_ptr(obs);
+}
 
 // Workspace layout: [err int | queue u64 | pad] [table] [scratch] [restart state]
 struct WsLayout {
@@ -468,6 +568,11 @@ void vfisv_destroy(vfisv_handle* h) {
   if (h->wfinit) cudaFree(h->wfinit);
   if (h->mapws) cudaFree(h->mapws);
   if (h->mapoff_host) cudaFreeHost(h->mapoff_host);
+  if (h->pipe) cudaFree(h->pipe);
+  if (h->pipe_in) cudaStreamDestroy(h->pipe_in);
+  if (h->pipe_out) cudaStreamDestroy(h->pipe_out);
+  for (cudaEvent_t e : h->pipe_ev)
+    if (e) cudaEventDestroy(e);
   delete h;
 }
 
@@ -510,6 +615,32 @@ int vfisv_graph_end(vfisv_handle* h, void* stream, vfisv_graph** out) {
 int vfisv_graph_launch(vfisv_graph* g, void* stream) {
   if (!g || !g->exec) return VFISV_E_ARG;
   return cudaGraphLaunch(g->exec, (cudaStream_t)stream) == cudaSuccess ? VFISV_OK : VFISV_E_CUDA;
+}
+
+static int count_kernels(cudaGraph_t g, int64_t* count) {
+  size_t n = 0;
+  if (cudaGraphGetNodes(g, nullptr, &n) != cudaSuccess) return VFISV_E_CUDA;
+  std::vector<cudaGraphNode_t> nodes(n);
+  if (n && cudaGraphGetNodes(g, nodes.data(), &n) != cudaSuccess) return VFISV_E_CUDA;
+  for (cudaGraphNode_t node : nodes) {
+    cudaGraphNodeType t;
+    if (cudaGraphNodeGetType(node, &t) != cudaSuccess) return VFISV_E_CUDA;
+    if (t == cudaGraphNodeTypeKernel) {
+      ++*count;
+    } else if (t == cudaGraphNodeTypeGraph) {
+      cudaGraph_t child;
+      if (cudaGraphChildGraphNodeGetGraph(node, &child) != cudaSuccess) return VFISV_E_CUDA;
+      const int rc = count_kernels(child, count);
+      if (rc) return rc;
+    }
+  }
+  return VFISV_OK;
+}
+
+int vfisv_graph_kernels(const vfisv_graph* g, int64_t* count) {
+  if (!g || !g->graph || !count) return VFISV_E_ARG;
+  *count = 0;
+  return count_kernels(g->graph, count);
 }
 
 void vfisv_graph_destroy(vfisv_graph* g) {
@@ -750,6 +881,32 @@ int vfisv_invert(vfisv_handle* h, const float* obs, const float* weights,
   if (set_device(h)) return VFISV_E_CUDA;
   cudaStream_t s = (cudaStream_t)stream;
   const int nobs = 4 * nfilt;
+  if (pipeline_host(h, obs, npix, cfg->restarts == 0)) {
+    // shared inputs once, the per-pixel rows through the pipeline
+    Staging sh;
+    sh.add(filters, (size_t)nfilt * nlam * sizeof(float), false);
+    sh.add(wl_mA, (size_t)nlam * sizeof(float), false);
+    sh.add(weights_per_pixel ? nullptr : weights, (size_t)nobs * sizeof(float), false);
+    if ((rc = sh.prepare(h, s))) return rc;
+    const float* fd = (const float*)sh.bufs[0].dev;
+    const float* wd = (const float*)sh.bufs[1].dev;
+    const float* wsh = (const float*)sh.bufs[2].dev;
+    RowArg a[] = {{obs, nobs * sizeof(float), false},
+                  {weights_per_pixel ? weights : nullptr, nobs * sizeof(float), false},
+                  {init, 10 * sizeof(float), false},
+                  {params_out, 10 * sizeof(float), true},
+                  {chi2_out, sizeof(float), true},
+                  {iters_out, sizeof(int32_t), true},
+                  {status_out, sizeof(int32_t), true},
+                  {cov_out, 100 * sizeof(float), true}};
+    return pipeline_rows(h, s, npix, a, 8, [&](int64_t n, void** d) {
+      // every pointer is on the device: the call runs in place, without syncing
+      return vfisv_invert(h, (const float*)d[0], weights_per_pixel ? (const float*)d[1] : wsh,
+                          weights_per_pixel, fd, nfilt, wd, nlam, line, (const float*)d[2], cfg,
+                          n, (float*)d[3], (float*)d[4], (int32_t*)d[5], (int32_t*)d[6],
+                          (float*)d[7], s);
+    });
+  }
   Staging st;
   st.add(obs, (size_t)npix * nobs * sizeof(float), false);
   st.add(weights, (size_t)(weights_per_pixel ? npix : 1) * nobs * sizeof(float), false);
@@ -976,6 +1133,34 @@ int vfisv_invert_nn(vfisv_handle* h, const float* blob, const float* obs, const 
   if (set_device(h)) return VFISV_E_CUDA;
   cudaStream_t s = (cudaStream_t)stream;
   const int nobs = 4 * nfilt;
+  if (pipeline_host(h, obs, npix, cfg_nn->restarts == 0 && cfg_plain->restarts == 0)) {
+    Staging sh;
+    sh.add(filters, (size_t)nfilt * nlam * sizeof(float), false);
+    sh.add(wl_mA, (size_t)nlam * sizeof(float), false);
+    sh.add(blob, nn::NBLOB * sizeof(float), false);
+    sh.add(weights_per_pixel ? nullptr : weights, (size_t)nobs * sizeof(float), false);
+    if ((rc = sh.prepare(h, s))) return rc;
+    const float* fd = (const float*)sh.bufs[0].dev;
+    const float* wd = (const float*)sh.bufs[1].dev;
+    const float* bd = (const float*)sh.bufs[2].dev;
+    const float* wsh = (const float*)sh.bufs[3].dev;
+    RowArg a[] = {{obs, nobs * sizeof(float), false},
+                  {weights_per_pixel ? weights : nullptr, nobs * sizeof(float), false},
+                  {params_out, 10 * sizeof(float), true},
+                  {chi2_out, sizeof(float), true},
+                  {iters_out, sizeof(int32_t), true},
+                  {status_out, sizeof(int32_t), true},
+                  {cov_out, 100 * sizeof(float), true},
+                  {flagged_out, sizeof(int32_t), true}};
+    return pipeline_rows(h, s, npix, a, 8, [&](int64_t n, void** d) {
+      // every pointer is on the device: the call runs in place, without syncing
+      return vfisv_invert_nn(h, bd, (const float*)d[0],
+                             weights_per_pixel ? (const float*)d[1] : wsh, weights_per_pixel, fd,
+                             nfilt, wd, nlam, line, cfg_nn, cfg_plain, chi2_flag,
+                             flag_unconverged, n, (float*)d[2], (float*)d[3], (int32_t*)d[4],
+                             (int32_t*)d[5], (float*)d[6], (int32_t*)d[7], s);
+    });
+  }
   Staging st;
   st.add(obs, (size_t)npix * nobs * sizeof(float), false);
   st.add(weights, (size_t)(weights_per_pixel ? npix : 1) * nobs * sizeof(float), false);

@@ -38,6 +38,8 @@ def test_graph_replay_matches_direct_calls(vf):
         v.vfisv_graph_begin(h, s)
         v.vfisv_invert(h, src, w, tf, tx, LINE, out=out, stream=s)
         g = v.vfisv_graph_end(h, s)
+        # table pack, LM kernel, covariance (memsets are not kernels)
+        assert 2 <= g.kernels() <= 4, g.kernels()
         for data in (obs, obs2):
             src.copy_(data)
             g.launch(s)
