@@ -278,6 +278,17 @@ int vfisv_autotune(vfisv_handle* h, const float* obs, const float* weights,
                    const vfisv_config* cfg, int64_t npix, int32_t* best_block, float* ms_out,
                    void* stream);
 
+/* Host-buffer pipeline depth.  vfisv_invert and vfisv_invert_nn given host
+ * observations for 2^20 pixels or more (no restarts, not capturing) copy the
+ * per-pixel rows in and out in `chunks` chunks on two copy streams of the
+ * handle, double-buffered on the device, while the caller's stream inverts
+ * the previous chunk; the outputs are those of one call over the whole map.
+ * With 3 or more chunks the first and last hold an eighth of the rows of
+ * each middle chunk (only their copies are not hidden).  chunks = 0 stages
+ * the whole map before the inversion instead; default 3.
+ * VFISV_E_ARG for chunks < 0 or > 64. */
+int vfisv_set_pipeline_chunks(vfisv_handle* h, int32_t chunks);
+
 /* Synchronise `stream` and report any error a kernel of this handle flagged
  * on the device since the last check (VFISV_E_DEVICE) or a CUDA error. */
 int vfisv_check(vfisv_handle* h, void* stream);

@@ -19,7 +19,8 @@ __all__ = [
     "vfisv_create", "vfisv_destroy", "vfisv_synth", "vfisv_invert", "vfisv_check",
     "vfisv_strerror", "vfisv_config_default", "vfisv_nn_init", "vfisv_nn_train",
     "vfisv_nn_grad", "vfisv_nn_infer", "vfisv_invert_nn", "vfisv_graph_begin", "vfisv_graph_end",
-    "vfisv_graph_launch", "vfisv_graph_kernels", "vfisv_graph_destroy", "vfisv_autotune", "vfisv_voigt",
+    "vfisv_graph_launch", "vfisv_graph_kernels", "vfisv_graph_destroy", "vfisv_autotune",
+    "vfisv_set_pipeline_chunks", "vfisv_voigt",
     "vfisv_limb_weights", "vfisv_restart_models", "vfisv_init_models", "vfisv_invert_batch",
     "VfisvError",
     "library_path",
@@ -104,6 +105,8 @@ def load():
     lib.vfisv_graph_end.restype = ctypes.c_int
     lib.vfisv_graph_launch.argtypes = [P, P]
     lib.vfisv_graph_launch.restype = ctypes.c_int
+    lib.vfisv_set_pipeline_chunks.argtypes = [P, I32]
+    lib.vfisv_set_pipeline_chunks.restype = ctypes.c_int
     lib.vfisv_graph_kernels.argtypes = [P, ctypes.POINTER(I64)]
     lib.vfisv_graph_kernels.restype = ctypes.c_int
     lib.vfisv_graph_destroy.argtypes = [P]
@@ -436,6 +439,11 @@ def vfisv_graph_end(h: Handle, stream) -> Graph:
 def vfisv_graph_launch(g: Graph, stream) -> None:
     _check(load().vfisv_graph_launch(g.ptr, ctypes.c_void_p(_stream(None, stream))),
            "vfisv_graph_launch")
+
+
+def vfisv_set_pipeline_chunks(h: Handle, chunks: int) -> None:
+    """Host-buffer pipeline depth of this handle (0: stage the whole map)."""
+    _check(load().vfisv_set_pipeline_chunks(h.ptr, int(chunks)), "vfisv_set_pipeline_chunks")
 
 
 def vfisv_graph_kernels(g: Graph) -> int:

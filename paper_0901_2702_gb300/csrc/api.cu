@@ -40,6 +40,7 @@ struct vfisv_handle {
   size_t pipe_bytes = 0;
   cudaStream_t pipe_in = nullptr, pipe_out = nullptr;
   cudaEvent_t pipe_ev[7] = {};
+  int pipe_chunks = 3;     // vfisv_set_pipeline_chunks (0: stage the whole map)
 };
 
 struct vfisv_graph {
@@ -189,13 +190,14 @@ struct Staging {
 };
 
 // Host-buffer pipeline for per-pixel calls on large maps.  Rows [0, npix)
-// run in kPipeChunks chunks; each chunk's host inputs are copied in on one
+// run in h->pipe_chunks chunks; each chunk's host inputs are copied in on one
 // stream and its host outputs copied back on another, through two device
 // slots, while the caller's stream computes the previous chunk -- so the
-// host<->device traffic hides behind the inversion.  Every per-pixel result
-// depends on that pixel alone, so the outputs equal those of one call over
-// the whole map.  Device pointers among the rows are used in place.
-constexpr int kPipeChunks = 4;
+// host<->device traffic hides behind the inversion.  Only the first chunk's
+// copy-in and the last chunk's copy-out stay exposed, so with three or more
+// chunks those two are an eighth of the size of the others.  Every per-pixel
+// result depends on that pixel alone, so the outputs equal those of one call
+// over the whole map.  Device pointers among the rows are used in place.
 constexpr int64_t kPipeMinRows = 1 << 20;
 
 struct RowArg {
@@ -207,7 +209,17 @@ struct RowArg {
 template <class Run>
 int pipeline_rows(vfisv_handle* h, cudaStream_t s, int64_t npix, RowArg* args, int nargs,
                   Run run) {
-  const int64_t chunk = (npix + kPipeChunks - 1) / kPipeChunks;
+  // chunk boundaries: weights 1/8, 1, ..., 1, 1/8 (uniform below 3 chunks)
+  const int nc = h->pipe_chunks;
+  std::vector<int64_t> bound(nc + 1);
+  const double edge = nc >= 3 ? 0.125 : 1.0, total_w = 2 * edge + (nc - 2);
+  double acc = 0.0;
+  for (int k = 0; k <= nc; ++k) {
+    bound[k] = k == nc ? npix : (int64_t)((double)npix * acc / (nc == 1 ? 1.0 : total_w));
+    if (k < nc) acc += (k == 0 || k == nc - 1) ? (nc == 1 ? 1.0 : edge) : 1.0;
+  }
+  int64_t chunk = 0;
+  for (int k = 0; k < nc; ++k) chunk = bound[k + 1] - bound[k] > chunk ? bound[k + 1] - bound[k] : chunk;
   std::vector<bool> host(nargs);
   size_t slot = 0;
   for (int i = 0; i < nargs; ++i) {
@@ -232,9 +244,10 @@ int pipeline_rows(vfisv_handle* h, cudaStream_t s, int64_t npix, RowArg* args, i
       cudaStreamWaitEvent(h->pipe_out, h->pipe_ev[0], 0) != cudaSuccess)
     return VFISV_E_CUDA;
   std::vector<void*> dev(nargs);
-  for (int64_t k = 0; k * chunk < npix; ++k) {
-    const int j = (int)(k & 1);
-    const int64_t off = k * chunk, n = npix - off < chunk ? npix - off : chunk;
+  for (int k = 0; k < nc; ++k) {
+    const int j = k & 1;
+    const int64_t off = bound[k], n = bound[k + 1] - bound[k];
+    if (n == 0) continue;
     char* base = (char*)h->pipe + (size_t)j * slot;
     for (int i = 0; i < nargs; ++i) {
       if (!args[i].user) {
@@ -279,7 +292,8 @@ int pipeline_rows(vfisv_handle* h, cudaStream_t s, int64_t npix, RowArg* args, i
 // and not with restarts, whose random draws are keyed by the pixel's index
 // within the call).
 bool pipeline_host(const vfisv_handle* h, const void* obs, int64_t npix, bool no_restarts) {
-  return !h->capturing && no_restarts && npix >= kPipeMinRows && !is_device_ptr(obs);
+  return !h->capturing && no_restarts && h->pipe_chunks > 0 && npix >= kPipeMinRows &&
+         !is_device_ptr(obs);
 }
 
 // Workspace layout: [err int | queue u64 | pad] [table] [scratch] [restart state]
@@ -648,6 +662,12 @@ void vfisv_graph_destroy(vfisv_graph* g) {
   if (g->exec) cudaGraphExecDestroy(g->exec);
   if (g->graph) cudaGraphDestroy(g->graph);
   delete g;
+}
+
+int vfisv_set_pipeline_chunks(vfisv_handle* h, int32_t chunks) {
+  if (!h || chunks < 0 || chunks > 64) return VFISV_E_ARG;
+  h->pipe_chunks = chunks;
+  return VFISV_OK;
 }
 
 int vfisv_autotune(vfisv_handle* h, const float* obs, const float* weights,

@@ -37,16 +37,30 @@ def _same(host, dev):
         np.testing.assert_array_equal(a, dev[k].cpu().numpy(), err_msg=k)
 
 
-def test_plain_inversion_host_pipeline(vf):
+@pytest.mark.parametrize("chunks", [2, 3, 5])
+def test_plain_inversion_host_pipeline(vf, chunks):
+    """2 chunks: equal halves; 3 (the default) and 5: small first and last."""
     v, h, torch = vf
     obs, w, tf, tx, _ = _map(v, h, torch, 71)
     cfg = {"max_iter": 30}
     rd = v.vfisv_invert(h, obs, w, tf, tx, LINE, config=cfg, want_cov=True)
-    rh = v.vfisv_invert(h, _host(obs), _host(w), _host(tf), _host(tx), LINE, config=cfg,
-                        want_cov=True)
+    v.vfisv_set_pipeline_chunks(h, chunks)
+    try:
+        rh = v.vfisv_invert(h, _host(obs), _host(w), _host(tf), _host(tx), LINE, config=cfg,
+                            want_cov=True)
+    finally:
+        v.vfisv_set_pipeline_chunks(h, 3)
     assert isinstance(rh["params"], np.ndarray)
     _same(rh, rd)
     v.vfisv_check(h)
+
+
+def test_pipeline_depth_bounds(vf):
+    v, h, torch = vf
+    for bad in (-1, 65):
+        with pytest.raises(v.VfisvError):
+            v.vfisv_set_pipeline_chunks(h, bad)
+    v.vfisv_set_pipeline_chunks(h, 3)
 
 
 def test_mixed_inversion_host_pipeline(vf):
