@@ -16,8 +16,9 @@ A step is one full-map inversion with the observations resident in HBM:
               P(chi2_15/15 > 2.5) = 0.15 %).  1024x1024 map: LM cap 20, flag =
               not converged or chi2 > 3;
   plain_lm:   vfisv_invert from the standard guess (cap 50), covariance on.
-The network is trained before timing (4M profiles synthesised by the
-library, 16 epochs) and the training time is reported beside the numbers.
+The network is trained before timing (16.8 M profiles synthesised by the
+library, 32 epochs of batch 8192) and the training time is reported beside
+the numbers.
 `e2e` repeats the mixed step through the same public call with pinned host
 buffers (host->device copies of observations and weights and the copy back
 of all outputs inside the timed region).
@@ -57,7 +58,7 @@ METRIC = "converged pixels/s on 1 GB300 at oracle-matched chi2: NN-init mixed vs
 PLAIN_CAP = 50
 # (LM cap after the network's guess, chi2 flag, flag unconverged pixels too)
 MIXED = {"disk": (50, 2.5, False), "map1024": (20, 3.0, True)}
-TRAIN_N, TRAIN_EPOCHS, TRAIN_BATCH = 1 << 22, 16, 8192
+TRAIN_N, TRAIN_EPOCHS, TRAIN_BATCH = 1 << 24, 32, 8192
 
 # Algorithmic FP32 flops of one fused LM pass (synthesis + 6-column Jacobian
 # + filtering) per wavelength point, from the op count of the formulas in
