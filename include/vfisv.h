@@ -278,6 +278,14 @@ int vfisv_autotune(vfisv_handle* h, const float* obs, const float* weights,
                    const vfisv_config* cfg, int64_t npix, int32_t* best_block, float* ms_out,
                    void* stream);
 
+/* Persistent launches of this handle (the LM, wide, covariance and network
+ * kernels) use at most `nsm` SMs; 0 (the default) lets them take every SM.
+ * For two handles inverting side by side on concurrent streams: an LM CTA
+ * holds a whole SM's registers, so without a split the first launch takes
+ * the GPU and the other waits for it.  A graph captures the grids in force
+ * at capture time.  VFISV_E_ARG for nsm < 0. */
+int vfisv_set_sm_limit(vfisv_handle* h, int32_t nsm);
+
 /* Host-buffer pipeline depth.  vfisv_invert and vfisv_invert_nn given host
  * observations for 2^20 pixels or more (no restarts, not capturing) copy the
  * per-pixel rows in and out in `chunks` chunks on two copy streams of the

@@ -20,7 +20,7 @@ __all__ = [
     "vfisv_strerror", "vfisv_config_default", "vfisv_nn_init", "vfisv_nn_train",
     "vfisv_nn_grad", "vfisv_nn_infer", "vfisv_invert_nn", "vfisv_graph_begin", "vfisv_graph_end",
     "vfisv_graph_launch", "vfisv_graph_kernels", "vfisv_graph_destroy", "vfisv_autotune",
-    "vfisv_set_pipeline_chunks", "vfisv_voigt",
+    "vfisv_set_pipeline_chunks", "vfisv_set_sm_limit", "vfisv_voigt",
     "vfisv_limb_weights", "vfisv_restart_models", "vfisv_init_models", "vfisv_invert_batch",
     "VfisvError",
     "library_path",
@@ -105,6 +105,8 @@ def load():
     lib.vfisv_graph_end.restype = ctypes.c_int
     lib.vfisv_graph_launch.argtypes = [P, P]
     lib.vfisv_graph_launch.restype = ctypes.c_int
+    lib.vfisv_set_sm_limit.argtypes = [P, I32]
+    lib.vfisv_set_sm_limit.restype = ctypes.c_int
     lib.vfisv_set_pipeline_chunks.argtypes = [P, I32]
     lib.vfisv_set_pipeline_chunks.restype = ctypes.c_int
     lib.vfisv_graph_kernels.argtypes = [P, ctypes.POINTER(I64)]
@@ -439,6 +441,11 @@ def vfisv_graph_end(h: Handle, stream) -> Graph:
 def vfisv_graph_launch(g: Graph, stream) -> None:
     _check(load().vfisv_graph_launch(g.ptr, ctypes.c_void_p(_stream(None, stream))),
            "vfisv_graph_launch")
+
+
+def vfisv_set_sm_limit(h: Handle, nsm: int) -> None:
+    """At most `nsm` SMs for this handle's persistent launches (0: all)."""
+    _check(load().vfisv_set_sm_limit(h.ptr, int(nsm)), "vfisv_set_sm_limit")
 
 
 def vfisv_set_pipeline_chunks(h: Handle, chunks: int) -> None:

@@ -12,6 +12,10 @@
 
 using namespace vfisv;
 
+namespace vfisv {
+thread_local int t_sm_limit = 0;  // from the calling handle (set_device)
+}  // namespace vfisv
+
 struct vfisv_handle {
   int device = 0;
   Weideman W{};
@@ -41,6 +45,7 @@ struct vfisv_handle {
   cudaStream_t pipe_in = nullptr, pipe_out = nullptr;
   cudaEvent_t pipe_ev[7] = {};
   int pipe_chunks = 3;     // vfisv_set_pipeline_chunks (0: stage the whole map)
+  int sm_limit = 0;        // vfisv_set_sm_limit (0: every SM)
 };
 
 struct vfisv_graph {
@@ -314,6 +319,7 @@ WsLayout layout(int nf, int nlam, int64_t nslots, bool restarts, bool alpha_free
 
 int set_device(vfisv_handle* h) {
   t_capturing = h->capturing;
+  t_sm_limit = h->sm_limit;
   return cudaSetDevice(h->device) == cudaSuccess ? VFISV_OK : VFISV_E_CUDA;
 }
 
@@ -662,6 +668,12 @@ void vfisv_graph_destroy(vfisv_graph* g) {
   if (g->exec) cudaGraphExecDestroy(g->exec);
   if (g->graph) cudaGraphDestroy(g->graph);
   delete g;
+}
+
+int vfisv_set_sm_limit(vfisv_handle* h, int32_t nsm) {
+  if (!h || nsm < 0) return VFISV_E_ARG;
+  h->sm_limit = nsm;
+  return VFISV_OK;
 }
 
 int vfisv_set_pipeline_chunks(vfisv_handle* h, int32_t chunks) {

@@ -10,6 +10,11 @@
 
 namespace vfisv {
 
+// SMs the persistent launches of the calling handle may use (0: all); set
+// per call from the handle (vfisv_set_sm_limit), read by the grid sizing.
+extern thread_local int t_sm_limit;
+inline int sm_budget(int nsm) { return (t_sm_limit > 0 && t_sm_limit < nsm) ? t_sm_limit : nsm; }
+
 // Device error codes written to the handle's error word.
 enum : int { kDevErrNone = 0, kDevErrTableWait = 1, kDevErrNnWait = 2 };
 

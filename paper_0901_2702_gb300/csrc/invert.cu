@@ -147,22 +147,40 @@ __device__ __noinline__ bool covariance_df(const float* scr, int64_t ns, uint32_
                          ? df_from(0.0f)
                          : df_mul(df_mul(df_from(scr[(int64_t)tri(i, j) * ns]), sc[i]), sc[j]);
   if (cholesky9_df(L, ri)) {
-    // scr is no longer read: column j of S M^-1 S, S = diag(sc), straight to out
-#pragma unroll 1
-    for (int j = 0; j < kNP; ++j) {
-      dfl x[kNP];
+    // scr is no longer read.  In place: W = L^-1 (columns right to left,
+    // each from the already inverted trailing block), then M^-1 = W^T W
+    // (columns left to right) -- ~285 double-float FMAs instead of nine
+    // solves (~810); then S M^-1 S, S = diag(sc), straight to out.
 #pragma unroll
-      for (int i = 0; i < kNP; ++i) x[i] = (i == j) ? sc[i] : df_from(0.0f);
-      chol_solve9_df(L, ri, x);
-      const bool hj = (hmask >> j) & 1u;
+    for (int j = kNP - 1; j >= 0; --j) {
 #pragma unroll
-      for (int i = 0; i < kNP; ++i) {
-        if (i < j) continue;
-        const float v = (hj || ((hmask >> i) & 1u)) ? 0.0f : df_mul(x[i], sc[i]).hi;
+      for (int i = kNP - 1; i > j; --i) {
+        dfl t = df_from(0.0f);
+#pragma unroll
+        for (int k = j + 1; k <= i; ++k) t = df_fma(L[tri(i, k)], L[tri(k, j)], t);
+        L[tri(i, j)] = df_neg(df_mul(t, ri[j]));
+      }
+      L[tri(j, j)] = ri[j];
+    }
+#pragma unroll
+    for (int j = 0; j < kNP; ++j)
+#pragma unroll
+      for (int i = j; i < kNP; ++i) {
+        dfl t = df_from(0.0f);
+#pragma unroll
+        for (int k = i; k < kNP; ++k) t = df_fma(L[tri(k, i)], L[tri(k, j)], t);
+        L[tri(i, j)] = t;
+      }
+#pragma unroll
+    for (int j = 0; j < kNP; ++j)
+#pragma unroll
+      for (int i = j; i < kNP; ++i) {
+        const float v = (((hmask >> i) | (hmask >> j)) & 1u)
+                            ? 0.0f
+                            : df_mul(df_mul(L[tri(i, j)], sc[i]), sc[j]).hi;
         out[i * 10 + j] = v;
         out[j * 10 + i] = v;
       }
-    }
     for (int k = 0; k < 10; ++k) {
       out[90 + k] = 0.0f;
       out[k * 10 + 9] = 0.0f;
@@ -736,6 +754,7 @@ cudaError_t launch_covariance(float* cov, const int32_t* status, int64_t npix,
   int dev = 0, nsm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  nsm = sm_budget(nsm);
   // a few blocks per SM, each sweeping many pixels so its fallback queue fills
   int64_t grid = (npix + kCovThreads - 1) / kCovThreads;
   if (grid > (int64_t)nsm * 4) grid = (int64_t)nsm * 4;
@@ -760,6 +779,7 @@ static cudaError_t slots_for(int nlam, int64_t npix, int64_t* nslots, int* grid,
   int dev = 0, nsm = 0, per = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  nsm = sm_budget(nsm);
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, BS, sm);
   if (e != cudaSuccess) return e;
   if (per < 1) return cudaErrorLaunchOutOfResources;

@@ -484,6 +484,7 @@ cudaError_t nn_infer(void* ws, const float* blob, const float* obs, int64_t n, f
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
   if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
     return e;
+  nsm = sm_budget(nsm);
   if ((e = cudaFuncSetAttribute(mlp_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)kSmemBytes)) != cudaSuccess)
     return e;

@@ -641,6 +641,7 @@ static int wide_grid(const void* kern, size_t smem, int64_t npix) {
   int dev = 0, nsm = 0, per = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  nsm = sm_budget(nsm);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, 32 * kWWarps, smem);
   if (per < 1) per = 1;
   int64_t g = (int64_t)nsm * per;
