@@ -365,7 +365,9 @@ int vfisv_nn_train(vfisv_handle* h, float* blob, const float* obs, const float* 
 int vfisv_nn_grad(vfisv_handle* h, const float* blob, const float* obs, const float* params,
                   int64_t n, float* grad_out, float* loss_out, void* stream);
 
-/* Network initial guesses for npix pixels.
+/* Network initial guesses for npix pixels (Sec. 5), in one fused kernel:
+ * features, the four layers (BF16 operands rounded to nearest, FP32
+ * accumulation, FP32 bias and GELU), decoding.
  *   init_out  float32[npix][10] models decoded from the outputs (alpha = 1)
  *   conf_out  float32[npix] confidence output, or NULL
  *   raw_out   float32[npix][11] raw (standardised) outputs, or NULL */
