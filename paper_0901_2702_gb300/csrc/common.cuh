@@ -16,7 +16,7 @@ extern thread_local int t_sm_limit;
 inline int sm_budget(int nsm) { return (t_sm_limit > 0 && t_sm_limit < nsm) ? t_sm_limit : nsm; }
 
 // Device error codes written to the handle's error word.
-enum : int { kDevErrNone = 0, kDevErrTableWait = 1, kDevErrNnWait = 2 };
+enum : int { kDevErrNone = 0, kDevErrTableWait = 1, kDevErrNnWait = 2, kDevErrPoolWait = 3 };
 
 // Filter table layout in global and shared memory: nlam rows of `stride`
 // floats {T_0(x_i), ..., T_{nf-1}(x_i), x_i, pad...}, then one row holding

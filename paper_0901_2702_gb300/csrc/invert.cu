@@ -257,12 +257,57 @@ cudaError_t launch_restart_perturb(const float* in, int64_t n, int64_t pix0, int
 // Weideman coefficients of this translation unit (set by invert_set_constants).
 __constant__ Weideman c_W;
 
+// Pool of dump buffers in shared memory: a buffer is [NACC][32] floats, one
+// lane per column.  The filtered accumulators of a pass are needed only
+// from the end of its wavelength loop to the end of the normal-equation
+// build, a few per cent of an iteration, so a CTA keeps one buffer per
+// four warps (at least one) and a warp (or the part of it that arrives
+// together) takes one at the end of its loop.  The shared memory this
+// frees goes to the L1 cache that holds the kernel's spilled registers.  owner[b] counts the lanes still using
+// buffer b; each lane releases its own use, so divergence between the
+// acquire and the release is harmless.  A holder waits on nothing, so the
+// bounded wait below only covers the time other warps spend in their
+// builds.
+__host__ __device__ constexpr int dump_pool(int nt) { return nt >= 128 ? nt / 128 : 1; }
+
+__device__ __forceinline__ int pool_acquire(int* owner, int npool, int* err) {
+  const unsigned m = __activemask();
+  const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
+  int b = -1;
+  if (lane == leader) {
+    const int users = __popc(m);
+    const long long t0 = clock64();
+    for (int it = 0; b < 0 && it < (1 << 24); ++it) {
+      for (int i = 0; i < npool && b < 0; ++i)
+        if (atomicCAS(&owner[i], 0, users) == 0) b = i;
+      if (b < 0) {
+        if (clock64() - t0 > (1ll << 31)) break;  // ~1 s at 2 GHz
+        __nanosleep(32);
+      }
+    }
+    if (b < 0) {  // reported; the pass goes on in a shared buffer (results invalid)
+      atomicExch(err, kDevErrPoolWait);
+      b = (threadIdx.x >> 5) % npool;
+    }
+  }
+  b = __shfl_sync(m, b, leader);
+  __threadfence_block();
+  return b;
+}
+
+__device__ __forceinline__ void pool_release(int* owner, int b) {
+  __threadfence_block();  // this lane's reads of the buffer come first
+  atomicSub(&owner[b], 1);
+}
+
 // The fused pass over the wavelength grid, kept out of line so that its
-// 168 accumulators get the whole register file; results go to the
-// thread's column of `dump`.
+// 168 accumulators get the whole register file; results go to the lane's
+// column of a pooled dump buffer, whose index it returns.
 template <int NF, bool NM = false>
-__device__ __noinline__ void fused_pass(const PixK P, const float* __restrict__ tab, int nlam,
-                                        float* __restrict__ dump, int nt) {
+__device__ __noinline__ int fused_pass(const PixK P, const float* __restrict__ tab, int nlam,
+                                       float* __restrict__ pool, int* owner, int npool,
+                                       int* err) {
+  constexpr int NACC = kRows * 4 * NF + (NM ? kNmRows * NF : 0);
   constexpr int S = ((NF + 1) + 3) & ~3;
   float acc[kRows][4][NF];
   float accn[NM ? kNmRows : 1][NF];
@@ -282,27 +327,35 @@ __device__ __noinline__ void fused_pass(const PixK P, const float* __restrict__ 
     const float x = load_row<NF>(tab + (size_t)i * S, T);
     lambda_step<NF, true, NM>(c_W, P, x, T, acc, accn);
   }
+  const int b = pool_acquire(owner, npool, err);
+  float* dump = pool + (size_t)b * NACC * 32 + (threadIdx.x & 31);
 #pragma unroll
   for (int r = 0; r < kRows; ++r)
 #pragma unroll
     for (int s = 0; s < 4; ++s)
 #pragma unroll
-      for (int k = 0; k < NF; ++k) dump[((r * 4 + s) * NF + k) * nt] = acc[r][s][k];
+      for (int k = 0; k < NF; ++k) dump[((r * 4 + s) * NF + k) * 32] = acc[r][s][k];
   if constexpr (NM) {
     // the non-magnetic rows follow the magnetic ones
 #pragma unroll
     for (int r = 0; r < kNmRows; ++r)
 #pragma unroll
-      for (int k = 0; k < NF; ++k) dump[(kRows * 4 * NF + r * NF + k) * nt] = accn[r][k];
+      for (int k = 0; k < NF; ++k) dump[(kRows * 4 * NF + r * NF + k) * 32] = accn[r][k];
   }
+  return b;
 }
 
 // Per-slot LM state kept in shared memory (structure of arrays, one column
 // per thread) so that the registers of the wavelength loop hold only its
 // accumulators.
 constexpr int kStateWords = 10 + 10 + 2 + 2 + 2 + 1 + 1;  // M, Mt, chi2b, eps, pix, it, near
+// Layout: table | dump pool | state | pool owners (padded to 16 B) | mbarrier.
+__host__ __device__ constexpr size_t pool_owner_bytes(int nt) {
+  return ((size_t)dump_pool(nt) * 4 + 15) & ~(size_t)15;
+}
 __host__ __device__ constexpr size_t invert_smem_bytes(int tabf, int nacc, int nt) {
-  return (size_t)tabf * 4 + (size_t)nacc * nt * 4 + (size_t)kStateWords * nt * 4 + 16;
+  return (size_t)tabf * 4 + (size_t)dump_pool(nt) * nacc * 32 * 4 + (size_t)kStateWords * nt * 4 +
+         pool_owner_bytes(nt) + 16;
 }
 
 // RS: randomised restarts compiled in (A.restarts != 0).  DF: the damped
@@ -321,8 +374,9 @@ __global__ void __launch_bounds__(BS, 1) invert_kernel(InvertArgs A) {
   const int tabf = table_floats(NF, A.nlam);
   const int tid = threadIdx.x, nt = blockDim.x;
   float* tab = smem;
-  float* dump = smem + tabf;                      // [NACC][nt]
-  float* sM = dump + NACC * nt;                   // [10][nt] best model
+  const int npool = dump_pool(nt);
+  float* pool = smem + tabf;                      // [npool][NACC][32]
+  float* sM = pool + (size_t)npool * NACC * 32;   // [10][nt] best model
   float* sMt = sM + 10 * nt;                      // [10][nt] trial model
   double* sChi = reinterpret_cast<double*>(sMt + 10 * nt);  // [nt]
   double* sEps = sChi + nt;                       // [nt]
@@ -330,6 +384,8 @@ __global__ void __launch_bounds__(BS, 1) invert_kernel(InvertArgs A) {
   int* sIt = reinterpret_cast<int*>(sPix + nt);   // [nt]
   int* sNear = sIt + nt;  // [nt] last accepted step was close to the minimum (Hessian reuse)
   uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + (invert_smem_bytes(tabf, NACC, nt) - 16) / 4);
+  int* owner = reinterpret_cast<int*>(mbar) - pool_owner_bytes(nt) / 4;  // [npool]
+  if (tid < npool) owner[tid] = 0;  // published by the barrier inside the table load
   if (!tma_load_table(tab, A.table, (uint32_t)(tabf * sizeof(float)), mbar, A.err)) return;
   const float* tau = tab + (size_t)A.nlam * S;
   const int64_t slot = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -448,12 +504,13 @@ __global__ void __launch_bounds__(BS, 1) invert_kernel(InvertArgs A) {
     }
 
     // ---- fused synthesis + Jacobian at the trial model (Secs. 3 and 4.4) ----
-    fused_pass<NF, AF>(make_pixk(A.lk, ST(sMt, 0), ST(sMt, 1), ST(sMt, 3), ST(sMt, 4),
-                                 ST(sMt, 5), ST(sMt, 6)),
-                       tab, A.nlam, dump + tid, nt);
-    auto D = [&](int r, int s, int k) { return dump[((r * 4 + s) * NF + k) * nt + tid]; };
+    const int dbuf = fused_pass<NF, AF>(make_pixk(A.lk, ST(sMt, 0), ST(sMt, 1), ST(sMt, 3),
+                                                  ST(sMt, 4), ST(sMt, 5), ST(sMt, 6)),
+                                        tab, A.nlam, pool, owner, npool, A.err);
+    const float* dump = pool + (size_t)dbuf * NACC * 32 + (tid & 31);
+    auto D = [&](int r, int s, int k) { return dump[((r * 4 + s) * NF + k) * 32]; };
     // non-magnetic Stokes I rows (AF): value, then the E, D, A, V rows
-    auto N = [&](int r, int k) { return dump[(kRows * 4 * NF + r * NF + k) * nt + tid]; };
+    auto N = [&](int r, int k) { return dump[(kRows * 4 * NF + r * NF + k) * 32]; };
     const float alf = AF ? ST(sMt, 9) : 1.0f;
 
     const long long pix = sPix[tid];
@@ -642,6 +699,7 @@ __global__ void __launch_bounds__(BS, 1) invert_kernel(InvertArgs A) {
         for (int j = 0; j < 10; ++j) rsF[(kScratchPerSlot + j) * ns] = ST(sM, j);
       }
     }
+    pool_release(owner, dbuf);  // the filtered rows are not read past this point
     if (!retire && it >= A.max_iter) retire = true;  // status stays MAXITER
 
     if (retire) {
