@@ -71,11 +71,12 @@ FLOP_PER_LAMBDA = 4 + 3 * 135 + 16 + 32 + 48 + 28 + 14 + 4 + 6 + 63 + 4 * 132
 FLOP_PER_PASS_EXTRA = 60  # model and residual outside the wavelength loop
 # DRAM bytes (read + write) of one plain-LM launch without covariance (FP64
 # solve, the default), per pixel, from one ncu capture of invert_kernel on
-# 262,144 pixels of the 1024^2 distributions (54.0 MB read + 102.2 MB write;
-# profiles/invert_kernel_traffic.md); scaled by the pixels of a launch.
-# Algorithmic: 192 B read (observables, weights) + 52 B written (model,
-# chi2, counts); the extra writes are the FP64 solve's call-stack traffic.
-TRAFFIC_BYTES_PER_PIXEL = (54_013_696 + 102_230_784) / 262_144
+# 262,144 pixels of the 1024^2 distributions, 64 slots per CTA as autotuned
+# (54.6 MB read + 222.8 MB write; profiles/invert_kernel_traffic.md); scaled
+# by the pixels of a launch.  Algorithmic: 192 B read (observables, weights)
+# + 52 B written (model, chi2, counts); the extra writes are spilled
+# registers and the FP64 solve's call stack written back from L2.
+TRAFFIC_BYTES_PER_PIXEL = (54_599_680 + 222_795_264) / 262_144
 
 
 def fp32_peak_tflops(sm_mhz: float, nsm: int = 152) -> float:
@@ -366,9 +367,10 @@ def run_ours(args, rank, world):
                      "frac": achieved / peak,
                      "traffic": int(TRAFFIC_BYTES_PER_PIXEL * npix),
                      "traffic_note": "dram read+write bytes per launch, scaled by pixels from a "
-                                     "262,144-pixel ncu capture (596 B/px; algorithmic 244 B/px: "
-                                     "reads 206 vs 192, writes 390 B/px of which ~350 are the FP64 "
-                                     "solve's call-stack write-back)",
+                                     "262,144-pixel ncu capture (1,058 B/px; algorithmic 244 "
+                                     "B/px: reads 208 vs 192, writes 850 B/px of which ~800 are "
+                                     "spilled registers and the FP64 solve's call stack written "
+                                     "back from L2; ~5 GB/s over the launch)",
                      "kernel": "invert_kernel<6> (plain LM pass, no covariance)",
                      "kernel_ms": ms_lm,
                      "note": "peak = FP32 pipe, 152 SM x 128 lanes x 2 flop x 2070 MHz (no "
