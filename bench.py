@@ -524,7 +524,7 @@ def run_serving(args):
     torch.cuda.synchronize()
     v.vfisv_check(hF, sF)
     v.vfisv_check(hS, sS)
-    # An LM CTA holds a whole SM's registers, so the half launched first
+    # A persistent LM launch fills every SM's register file, so the half launched first
     # would take the GPU and the other would wait for it: split the SMs in
     # proportion to each half's time alone, so both halves (and the small
     # maps at the head of each queue) run from the start.

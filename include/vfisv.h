@@ -280,9 +280,9 @@ int vfisv_autotune(vfisv_handle* h, const float* obs, const float* weights,
 
 /* Persistent launches of this handle (the LM, wide, covariance and network
  * kernels) use at most `nsm` SMs; 0 (the default) lets them take every SM.
- * For two handles inverting side by side on concurrent streams: an LM CTA
- * holds a whole SM's registers, so without a split the first launch takes
- * the GPU and the other waits for it.  A graph captures the grids in force
+ * For two handles inverting side by side on concurrent streams: a
+ * persistent LM launch fills every SM's register file, so without a split
+ * the first launch takes the GPU and the other waits for it.  A graph captures the grids in force
  * at capture time.  VFISV_E_ARG for nsm < 0. */
 int vfisv_set_sm_limit(vfisv_handle* h, int32_t nsm);
 
