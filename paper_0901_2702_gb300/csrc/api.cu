@@ -212,8 +212,26 @@ struct RowArg {
 };
 
 template <class Run>
+int pipeline_rows_impl(vfisv_handle* h, cudaStream_t s, int64_t npix, RowArg* args, int nargs,
+                       Run run);
+
+// On an error the copies already queued still read and write the caller's
+// host buffers: let them finish before returning, so the caller may free them.
+template <class Run>
 int pipeline_rows(vfisv_handle* h, cudaStream_t s, int64_t npix, RowArg* args, int nargs,
                   Run run) {
+  const int rc = pipeline_rows_impl(h, s, npix, args, nargs, run);
+  if (rc != VFISV_OK) {
+    if (h->pipe_in) cudaStreamSynchronize(h->pipe_in);
+    if (h->pipe_out) cudaStreamSynchronize(h->pipe_out);
+    cudaStreamSynchronize(s);
+  }
+  return rc;
+}
+
+template <class Run>
+int pipeline_rows_impl(vfisv_handle* h, cudaStream_t s, int64_t npix, RowArg* args, int nargs,
+                       Run run) {
   // chunk boundaries: weights 1/8, 1, ..., 1, 1/8 (uniform below 3 chunks)
   const int nc = h->pipe_chunks;
   std::vector<int64_t> bound(nc + 1);
