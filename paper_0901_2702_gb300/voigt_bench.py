@@ -16,7 +16,6 @@ if __package__ in (None, ""):
 
 
 def main():
-    import numpy as np
     import torch
 
     import paper_0901_2702_gb300 as v

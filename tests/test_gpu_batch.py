@@ -8,7 +8,7 @@ import numpy as np
 import pytest
 
 import workloads as W
-from oracle import lm, me
+from oracle import lm
 from gpu_common import LINE, T, X, f32, vf  # noqa: F401
 
 pytestmark = pytest.mark.gpu
