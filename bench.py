@@ -1,5 +1,6 @@
-"""Benchmark: converged pixels/s of the GB300 Milne-Eddington inversion,
-NN-initialised mixed inversion vs plain Levenberg-Marquardt.
+"""Benchmark: converged pixels/s of the GB300 Milne-Eddington inversion at
+chi-square matched to plain LM, NN-initialised mixed inversion vs plain
+Levenberg-Marquardt.
 
 Default workload (N=1): the 4096x4096 full-disk synthetic map -- 13,457,608
 on-disk pixels (disk radius 2073 px), 90 % quiet Sun (B ~ U[0,200] G) and
@@ -9,19 +10,34 @@ sigma = 1e-3 Ic.  `--workload map1024` selects the 1024x1024 map with the
 uniform parameter distributions instead.
 
 A step is one full-map inversion with the observations resident in HBM:
-  value:      vfisv_invert_nn -- network guess, LM, then plain LM (cap 50)
-              re-inversion of flagged pixels, lower chi2 kept; covariance on.
-              Full disk: LM cap 50 from the network's guess (the plain run's
-              budget), flag = chi2 > 2.5 (a fit worse than the noise allows:
-              P(chi2_15/15 > 2.5) = 0.15 %).  1024x1024 map: LM cap 20, flag =
-              not converged or chi2 > 3;
+  mixed:      vfisv_invert_nn -- network guess and confidence; pixels whose
+              confidence output is above a threshold go to plain LM
+              directly; the others run LM from the guess (cap 50 on the
+              disk, 20 on the 1024^2 map) and are re-inverted plainly (cap
+              50) when they did not converge or end with chi2 above a flag
+              (2.5 on the disk, 3 on the 1024^2 map), lower chi2 kept;
+              covariance on;
   plain_lm:   vfisv_invert from the standard guess (cap 50), covariance on.
-The network is trained before timing (16.8 M profiles synthesised by the
-library, 32 epochs of batch 8192) and the training time is reported beside
-the numbers.
+value = mixed pixels that CONVERGED (STALLED is reported apart) with chi2 <=
+(1 + 1e-3) x the chi2 of the same pixel in the same run's plain LM pass,
+per second of the mixed step; plain_lm.value = plain pixels that CONVERGED
+per second of the plain step.  The routing threshold is calibrated before
+timing on a held-out map of the same kind (another seed): the most
+permissive threshold from a grid for which 99.3 % of the held-out pixels
+meet the chi2 criterion and, among those, the most matched pixels per LM
+pass.  The network is trained before timing (16.8 M profiles synthesised by
+the library, 32 epochs of batch 8192); training and calibration times are
+reported beside the numbers.
 `e2e` repeats the mixed step through the same public call with pinned host
 buffers (host->device copies of observations and weights and the copy back
 of all outputs inside the timed region).
+
+`roofline` is measured on the plain LM kernel alone (no covariance) and
+counts the method's own work (Sec. 4.4, Fig. 6): the synthesis of every
+trial model, the derivatives and normal equations only at the starting
+model and after accepted trials (the kernel's passes and accepted trials
+come from its work counters); the work the fused kernel issues (derivatives
+on every pass) is reported beside it.
 
 `fast_solve` repeats the mixed step with the opt-in double-float solve
 (not the headline: the workload names an FP64 solve).
@@ -30,10 +46,13 @@ of all outputs inside the timed region).
 filtergrams, half spectrograph-shaped; per-map latency p50/p99) and prints
 its own line.
 
-With --impl reference the FP64 CPU oracle (plain LM) is timed instead on a
-bounded sample of the same map.  Multi-GPU: pixels are independent, so N
-ranks invert N independent maps (weak scaling, no collective on the data
-path).
+The oracle leg (cpu_baseline; with --impl reference it is the whole run)
+inverts a bounded sample of the same map with the FP64 oracle on every host
+core (a process pool over pixel chunks) and times it; in the GPU run the
+same sample, synthesised by the oracle, is also inverted by the GPU (plain
+and mixed) and the per-parameter error against the oracle is attached.
+Multi-GPU: pixels are independent, so N ranks invert N independent maps
+(weak scaling, no collective on the data path).
 """
 from __future__ import annotations
 
@@ -57,18 +76,29 @@ NLAM, NF = 149, 6
 METRIC = "converged pixels/s on 1 GB300 at oracle-matched chi2: NN-init mixed vs plain LM"
 PLAIN_CAP = 50
 # (LM cap after the network's guess, chi2 flag, flag unconverged pixels too)
-MIXED = {"disk": (50, 2.5, False), "map1024": (20, 3.0, True)}
+MIXED = {"disk": (50, 2.5, True), "map1024": (20, 3.0, True)}
+CHI2_MATCH = 1e-3          # mixed chi2 <= (1 + CHI2_MATCH) x plain chi2
+ROUTE_TARGET = 0.993       # calibration: held-out pixels meeting the chi2 criterion
+ROUTE_GRID = [round(-1.0 - 0.25 * i, 2) for i in range(17)]  # -1.0 ... -5.0
+CALIB_PIXELS = 1 << 18
 TRAIN_N, TRAIN_EPOCHS, TRAIN_BATCH = 1 << 24, 32, 8192
+CONVERGED, STALLED = 0, 2
 
-# Algorithmic FP32 flops of one fused LM pass (synthesis + 6-column Jacobian
-# + filtering) per wavelength point, from the op count of the formulas in
-# the kernel (FMA = 2 flops): profile coordinates 4, Faddeeva (Weideman, 16
-# terms) 3 x 135, absorption-matrix elements 16, Unno-Rachkovsky 32, Stokes
-# filtering 48, Eqs. 8-9 28, Delta partials 14, inclination factors 4,
-# filter weights x 1/Delta 6, 20 Stokes partials 63, chain rule and six
-# filtered derivative rows 4 x 132.
-FLOP_PER_LAMBDA = 4 + 3 * 135 + 16 + 32 + 48 + 28 + 14 + 4 + 6 + 63 + 4 * 132
+# Algorithmic FP32 flops per wavelength point, from the op count of the
+# formulas in the kernel (FMA = 2 flops).  Synthesis (every trial model):
+# profile coordinates 4, Faddeeva (Weideman, 16 terms) 3 x 135,
+# absorption-matrix elements 16, Unno-Rachkovsky 32, Stokes filtering 48.
+# Derivatives (the starting model and accepted trials, Fig. 6): Eqs. 8-9 28,
+# Delta partials 14, inclination factors 4, filter weights x 1/Delta 6, 20
+# Stokes partials 63, chain rule and six filtered derivative rows 4 x 132.
+FLOP_SYNTH_PER_LAMBDA = 4 + 3 * 135 + 16 + 32 + 48
+FLOP_DERIV_PER_LAMBDA = 28 + 14 + 4 + 6 + 63 + 4 * 132
+FLOP_PER_LAMBDA = FLOP_SYNTH_PER_LAMBDA + FLOP_DERIV_PER_LAMBDA  # one fused pass
 FLOP_PER_PASS_EXTRA = 60  # model and residual outside the wavelength loop
+# normal equations after a derivative pass: the 24 Jacobian rows (psi
+# rotation, row scales: ~30 flops each) and J^T W J (45) + J^T W r (9) as
+# multiply-adds (24 x (9 + 2 x 54))
+FLOP_NORMAL_EQ = 24 * 30 + 24 * (9 + 2 * 54)
 # DRAM bytes (read + write) of one plain-LM launch without covariance (FP64
 # solve, the default), per pixel, from one ncu capture of invert_kernel on
 # 262,144 pixels of the 1024^2 distributions, 64 slots per CTA as autotuned
@@ -142,12 +172,79 @@ def reduce_over_ranks(times_ms, counts, device):
     return [float(x) for x in t.tolist()], [int(x) for x in c.tolist()]
 
 
-def map_params(workload: str, rank: int):
+def map_params(workload: str, rank: int, offset: int = 0):
+    """Model parameters of a rank's map; offset selects a held-out map of the
+    same kind (the routing calibration)."""
+    seed = W.SEEDS[workload] + 1000 * rank + offset
     if workload == "disk":
-        p, _ = W.full_disk_params(W.SEEDS["disk"] + 1000 * rank)
-        return p, W.SEEDS["disk"] + 1000 * rank
-    n = 1024 * 1024
-    return W.quiet_and_active_params(n, W.SEEDS["map1024"] + 1000 * rank), W.SEEDS["map1024"] + 1000 * rank
+        p, _ = W.full_disk_params(seed)
+        return p, seed
+    return W.quiet_and_active_params(1024 * 1024, seed), seed
+
+
+def synth_map(v, h, p, tf, tx, line, seed, dev):
+    """Observations (library synthesis + seeded noise) and weights, in HBM."""
+    import torch
+    npix = p.shape[0]
+    tp = torch.tensor(np.asarray(p, dtype=np.float32), device=dev)
+    syn = v.vfisv_synth(h, tp, tf, tx, line).reshape(npix, 4 * NF)
+    sig = 1e-3 * (tp[:, 7] + tp[:, 8])[:, None]
+    nz = torch.tensor(W.noise(npix, 4 * NF, seed).astype(np.float32), device=dev)
+    obs = (syn + sig * nz).contiguous()
+    wts = (1.0 / (sig * sig)).expand(npix, 4 * NF).contiguous()
+    return obs, wts
+
+
+def mixed_outcome(routed, nn, plain, chi2_flag, flag_unconv):
+    """Per-pixel result of the mixed pipeline from its two deterministic
+    ingredients (every pixel's LM result depends on that pixel alone):
+    routed pixels take the plain result; the others keep LM from the guess
+    unless flagged, then the lower chi2 of the two.  Returns (chi2, status,
+    plain_ran)."""
+    import torch
+    sn, cn = nn["status"], nn["chi2"]
+    unconv = (sn != CONVERGED) & (sn != STALLED) if flag_unconv else torch.zeros_like(routed)
+    flag = ~routed & (~(cn <= chi2_flag) | unconv)
+    take = routed | (flag & (plain["chi2"] < cn))
+    return (torch.where(take, plain["chi2"], cn), torch.where(take, plain["status"], sn),
+            routed | flag)
+
+
+def calibrate_route(v, h, blob, tf, tx, line, workload, stream, cfg_nn, cfg_plain, dev):
+    """Confidence threshold for routing, chosen on a held-out map of the same
+    kind: among the grid values whose mixed result meets chi2 <= (1 +
+    CHI2_MATCH) x plain for ROUTE_TARGET of the held-out pixels, the one with
+    the most matched converged pixels per LM pass."""
+    import torch
+    t0 = time.perf_counter()
+    p, seed = map_params(workload, 0, offset=500)
+    idx = np.linspace(0, p.shape[0] - 1, min(CALIB_PIXELS, p.shape[0])).astype(np.int64)
+    obs, wts = synth_map(v, h, p[idx], tf, tx, line, seed, dev)
+    g = v.vfisv_nn_infer(h, blob, obs, line, stream=stream)
+    nn = v.vfisv_invert(h, obs, wts, tf, tx, line, init=g["init"], config=cfg_nn,
+                        want_cov=False, stream=stream)
+    pl = v.vfisv_invert(h, obs, wts, tf, tx, line, config=cfg_plain, want_cov=False,
+                        stream=stream)
+    v.vfisv_check(h, stream)
+    _, chi2_flag, flag_unconv = MIXED[workload]
+    passes_nn = nn["iters"].to(torch.int64) + 1
+    passes_pl = pl["iters"].to(torch.int64) + 1
+    rows, best = [], None
+    for k in ROUTE_GRID:
+        routed = g["conf"] > k
+        cm, sm, ran = mixed_outcome(routed, nn, pl, chi2_flag, flag_unconv)
+        ok = cm <= pl["chi2"] * (1 + CHI2_MATCH)
+        frac = float(ok.float().mean().item())
+        matched = int(((sm == CONVERGED) & ok).sum().item())
+        passes = int(passes_nn[~routed].sum().item() + passes_pl[ran].sum().item())
+        rows.append({"conf_route": k, "chi2_le_plain_frac": frac,
+                     "routed_frac": float(routed.float().mean().item()),
+                     "matched_per_kpass": 1e3 * matched / max(passes, 1)})
+        if frac >= ROUTE_TARGET and (best is None or matched / passes > best[1]):
+            best = (k, matched / passes)
+    k = best[0] if best else ROUTE_GRID[-1]
+    return k, {"held_out_map_seed": seed, "pixels": int(len(idx)), "target": ROUTE_TARGET,
+               "chosen": k, "grid": rows, "seconds": time.perf_counter() - t0}
 
 
 def run_ours(args, rank, world):
@@ -179,18 +276,18 @@ def run_ours(args, rank, world):
     final_loss = float(loss[-50:].mean().item())
     del tp, tobs
 
-    # --- the map: synthetic observations resident in HBM
-    p, seed = map_params(args.workload, rank)
-    npix = p.shape[0]
-    tpm = t32(p)
-    syn = v.vfisv_synth(h, tpm, tf, tx, line).reshape(npix, 4 * NF)
-    sig = 1e-3 * (tpm[:, 7] + tpm[:, 8])[:, None]
-    obs = (syn + sig * t32(W.noise(npix, 4 * NF, seed))).contiguous()
-    wts = (1.0 / (sig * sig)).expand(npix, 4 * NF).contiguous()
-    del syn, tpm
+    # a side stream: graphs cannot be captured on the legacy default stream
+    stream = torch.cuda.Stream(dev)
     NN_CAP, CHI2_FLAG, FLAG_UNCONV = MIXED[args.workload]
     cfg_nn = v.vfisv_config_default(max_iter=NN_CAP)
     cfg_plain = v.vfisv_config_default(max_iter=PLAIN_CAP)
+    conf_route, calib = calibrate_route(v, h, blob, tf, tx, line, args.workload, stream,
+                                        cfg_nn, cfg_plain, dev)
+
+    # --- the map: synthetic observations resident in HBM
+    p, seed = map_params(args.workload, rank)
+    npix = p.shape[0]
+    obs, wts = synth_map(v, h, p, tf, tx, line, seed, dev)
 
     def outputs(flag=True, cov=True):
         o = {"params": torch.empty(npix, 10, device=dev), "chi2": torch.empty(npix, device=dev),
@@ -201,8 +298,6 @@ def run_ours(args, rank, world):
             o["flagged"] = torch.empty(npix, dtype=torch.int32, device=dev)
         return o
 
-    # a side stream: graphs cannot be captured on the legacy default stream
-    stream = torch.cuda.Stream(dev)
     torch.cuda.synchronize()
     out_m, out_p = outputs(True), outputs(False)
     # launch-shape autotuner on a sample of the map
@@ -210,12 +305,12 @@ def run_ours(args, rank, world):
     best_block, tune_ms = v.vfisv_autotune(h, obs[:ns], wts[:ns], tf, tx, line,
                                            config=cfg_plain, stream=stream)
 
-    def step_mixed():
-        v.vfisv_invert_nn(h, blob, obs, wts, tf, tx, line, config_nn=cfg_nn,
-                          config_plain=cfg_plain, chi2_flag=CHI2_FLAG,
-                          flag_unconverged=FLAG_UNCONV, out=out_m, stream=stream)
+    def step_mixed(out=out_m, cn=cfg_nn, cp=cfg_plain):
+        v.vfisv_invert_nn(h, blob, obs, wts, tf, tx, line, config_nn=cn, config_plain=cp,
+                          chi2_flag=CHI2_FLAG, flag_unconverged=FLAG_UNCONV,
+                          conf_route=conf_route, out=out, stream=stream)
 
-    def step_plain(out=out_p, cov=True):
+    def step_plain(out=out_p):
         v.vfisv_invert(h, obs, wts, tf, tx, line, config=cfg_plain, out=out, stream=stream)
 
     def timed(fn, k, name):
@@ -250,7 +345,7 @@ def run_ours(args, rank, world):
     clocks = clk.stop()
     v.vfisv_check(h, stream)
     # plain LM on the same map (its own warm-up), then the LM kernel alone
-    # (no covariance) for the roofline
+    # (no covariance) for the roofline, with the kernel's work counters
     step_plain()
     v.vfisv_graph_begin(h, stream)
     step_plain()
@@ -258,7 +353,9 @@ def run_ours(args, rank, world):
     ms_plain = timed(lambda: graph_plain.launch(stream), max(1, min(args.steps, 2)), "timed_plain")
     out_r = outputs(False, cov=False)
     step_plain(out_r)
+    v.vfisv_counters(h, stream, reset=True)
     ms_lm = timed(lambda: step_plain(out_r), 1, "timed_lm")
+    work = v.vfisv_counters(h, stream, reset=True)
     v.vfisv_check(h, stream)
 
     # the same mixed step with the opt-in double-float solve (fast_solve=1):
@@ -266,49 +363,63 @@ def run_ours(args, rank, world):
     cfg_nn_f = v.vfisv_config_default(max_iter=NN_CAP, fast_solve=1)
     cfg_plain_f = v.vfisv_config_default(max_iter=PLAIN_CAP, fast_solve=1)
     out_f = outputs(True)
-
-    def step_fast():
-        v.vfisv_invert_nn(h, blob, obs, wts, tf, tx, line, config_nn=cfg_nn_f,
-                          config_plain=cfg_plain_f, chi2_flag=CHI2_FLAG,
-                          flag_unconverged=FLAG_UNCONV, out=out_f, stream=stream)
-
     # its own launch shape (the double-float solve has other register and
     # shared-memory needs), restored for the FP64 configuration afterwards
     best_block_f, _ = v.vfisv_autotune(h, obs[:ns], wts[:ns], tf, tx, line, config=cfg_plain_f,
                                        stream=stream)
-    step_fast()
+    step_mixed(out_f, cfg_nn_f, cfg_plain_f)
     v.vfisv_graph_begin(h, stream)
-    step_fast()
+    step_mixed(out_f, cfg_nn_f, cfg_plain_f)
     graph_fast = v.vfisv_graph_end(h, stream)
     ms_fast = timed(lambda: graph_fast.launch(stream), max(1, min(args.steps, 2)), "timed_fast")
     out_rf = outputs(False, cov=False)
     v.vfisv_invert(h, obs, wts, tf, tx, line, config=cfg_plain_f, out=out_rf, stream=stream)
+    v.vfisv_counters(h, stream, reset=True)
     ms_lm_fast = timed(lambda: v.vfisv_invert(h, obs, wts, tf, tx, line, config=cfg_plain_f,
                                               out=out_rf, stream=stream), 1, "timed_lm_fast")
+    work_f = v.vfisv_counters(h, stream, reset=True)
     v.vfisv_check(h, stream)
     graph_fast.close()
     v.vfisv_autotune(h, obs[:ns], wts[:ns], tf, tx, line, config=cfg_plain, stream=stream)
-    conv_f = int(((out_f["status"] == 0) | (out_f["status"] == 2)).sum().item())
-    passes_f = int((out_rf["iters"].to(torch.int64) + 1).sum().item())
-    flops_f = passes_f * (NLAM * FLOP_PER_LAMBDA + FLOP_PER_PASS_EXTRA)
 
-    conv = lambda o: int(((o["status"] == 0) | (o["status"] == 2)).sum().item())  # noqa: E731
-    conv_m, conv_p = conv(out_m), conv(out_p)
+    # --- counting: chi2 matched to the same run's plain LM pass
+    def matched(o):
+        ok = o["chi2"] <= out_p["chi2"] * (1 + CHI2_MATCH)
+        return int(((o["status"] == CONVERGED) & ok).sum().item()), float(ok.float().mean().item())
+
+    conv = lambda o: int((o["status"] == CONVERGED).sum().item())  # noqa: E731
+    stalled = lambda o: int((o["status"] == STALLED).sum().item())  # noqa: E731
+    match_m, le_frac = matched(out_m)
+    match_f, le_frac_f = matched(out_f)
+    conv_p = conv(out_p)
     if dist:
-        (ms_mixed, ms_plain), (conv_m_tot, conv_p_tot) = reduce_over_ranks(
-            (ms_mixed, ms_plain), (conv_m, conv_p), dev)
+        (ms_mixed, ms_plain), (match_tot, conv_p_tot) = reduce_over_ranks(
+            (ms_mixed, ms_plain), (match_m, conv_p), dev)
     else:
-        conv_m_tot, conv_p_tot = conv_m, conv_p
-    value = conv_m_tot / (ms_mixed / 1e3)
+        match_tot, conv_p_tot = match_m, conv_p
+    value = match_tot / (ms_mixed / 1e3)
     plain_value = conv_p_tot / (ms_plain / 1e3)
-    better = float((out_m["chi2"] <= out_p["chi2"] * (1 + 1e-3)).float().mean().item())
-    better2 = float((out_m["chi2"] <= out_p["chi2"] * (1 + 1e-2)).float().mean().item())
+    le2 = float((out_m["chi2"] <= out_p["chi2"] * (1 + 1e-2)).float().mean().item())
     ratio_med = float((out_m["chi2"] / out_p["chi2"]).median().item())
-    passes = int((out_r["iters"].to(torch.int64) + 1).sum().item())
-    flops = passes * (NLAM * FLOP_PER_LAMBDA + FLOP_PER_PASS_EXTRA)
+
+    # roofline of the LM kernel: the method's work (Fig. 6) and the work the
+    # fused kernel issues (derivatives with every pass)
+    def flops(wk):
+        # wavelength points per pass: the grid points the packed table keeps
+        ppp = wk["points"] / max(wk["passes"], 1)
+        nderiv = wk["accepted"] + wk["retired"]
+        method = (wk["points"] * FLOP_SYNTH_PER_LAMBDA + wk["passes"] * FLOP_PER_PASS_EXTRA +
+                  nderiv * (ppp * FLOP_DERIV_PER_LAMBDA + FLOP_NORMAL_EQ))
+        issued = (wk["points"] * FLOP_PER_LAMBDA + wk["passes"] * FLOP_PER_PASS_EXTRA +
+                  nderiv * FLOP_NORMAL_EQ)
+        return method, issued
+
+    fl_method, fl_issued = flops(work)
     sm_mhz = clocks.get("sm_mhz") or 2070.0
-    achieved = flops / (ms_lm / 1e3) / 1e12
     peak = fp32_peak_tflops(2070.0)
+    achieved = fl_method / (ms_lm / 1e3) / 1e12
+    issued_tf = fl_issued / (ms_lm / 1e3) / 1e12
+    flm_f, _ = flops(work_f)
 
     # end to end: pinned host buffers through the same public call
     obs_h = obs.cpu().pin_memory()
@@ -321,7 +432,7 @@ def run_ours(args, rank, world):
     def step_e2e():
         v.vfisv_invert_nn(h, blob_h, obs_h, wts_h, tf_h, tx_h, line, config_nn=cfg_nn,
                           config_plain=cfg_plain, chi2_flag=CHI2_FLAG,
-                          flag_unconverged=FLAG_UNCONV, out=outh)
+                          flag_unconverged=FLAG_UNCONV, conf_route=conf_route, out=outh)
 
     step_e2e()
     ne = max(1, min(args.steps, 2))
@@ -329,7 +440,9 @@ def run_ours(args, rank, world):
     for _ in range(ne):
         step_e2e()
     e2e_s = (time.perf_counter() - t0) / ne
-    conv_h = int(((outh["status"] == 0) | (outh["status"] == 2)).sum().item())
+    out_p_h = out_p["chi2"].cpu()
+    ok_h = outh["chi2"] <= out_p_h * (1 + CHI2_MATCH)
+    match_h = int(((outh["status"] == CONVERGED) & ok_h).sum().item())
     h2d = sum(t_.numel() * t_.element_size() for t_ in (obs_h, wts_h, tf_h, tx_h, blob_h))
     d2h = sum(t_.numel() * t_.element_size() for t_ in outh.values() if t_ is not None)
 
@@ -340,27 +453,39 @@ def run_ours(args, rank, world):
         "dtype": "f32 synthesis/Jacobian, f64 solve/chi2, bf16 network",
         "data": "synthetic (seeded ME parameters, library-synthesised Stokes + Gaussian noise)",
         "config": workload_config(args.workload, npix, world),
+        "count": "mixed pixels with status CONVERGED and chi2 <= (1 + 1e-3) x the same pixel's "
+                 "chi2 in the same run's plain LM pass, per second of the mixed step "
+                 "(STALLED not counted)",
         "launch": {"cuda_graph": "whole map per step", "lm_pixels_per_cta": best_block,
                    "autotune_ms_64_128_256": tune_ms},
-        "converged_fraction": conv_m / npix,
+        "routing": {"conf_route": conf_route, "calibration": calib},
+        "converged_fraction": conv(out_m) / npix,
+        "stalled_fraction": stalled(out_m) / npix,
+        "matched_converged_fraction": match_m / npix,
+        "chi2_mixed_le_plain_frac": le_frac,
+        "chi2_mixed_le_plain_1pct_frac": le2,
+        "chi2_mixed_over_plain_median": ratio_med,
         "mean_iterations": float(out_m["iters"].float().mean().item()),
         "flagged_fraction": float(out_m["flagged"].float().mean().item()),
         "plain_lm": {"value": plain_value, "unit": "pixels/s", "ms_per_step": ms_plain,
+                     "count": "plain pixels with status CONVERGED per second of the plain step",
                      "converged_fraction": conv_p / npix,
+                     "stalled_fraction": stalled(out_p) / npix,
                      "mean_iterations": float(out_p["iters"].float().mean().item())},
         "mixed_over_plain": value / plain_value,
-        "chi2_mixed_le_plain_frac": better,
-        "chi2_mixed_le_plain_1pct_frac": better2,
-        "chi2_mixed_over_plain_median": ratio_med,
+        "unmatched_count": {"note": "the previous count: every CONVERGED or STALLED mixed pixel, "
+                                    "whatever its chi2",
+                            "value": (conv(out_m) + stalled(out_m)) * world / (ms_mixed / 1e3),
+                            "plain_value": (conv_p + stalled(out_p)) * world / (ms_plain / 1e3)},
         "fast_solve": {"note": "same mixed step with the opt-in double-float solve and "
                                "compensated f32 chi2 (no FP64 on the LM path); not the headline",
-                       "value": conv_f / (ms_fast / 1e3), "unit": "pixels/s",
-                       "ms_per_step": ms_fast, "converged_fraction": conv_f / npix,
+                       "value": match_f / (ms_fast / 1e3), "unit": "pixels/s",
+                       "ms_per_step": ms_fast, "chi2_mixed_le_plain_frac": le_frac_f,
                        "lm_kernel_ms": ms_lm_fast, "lm_pixels_per_cta": best_block_f,
-                       "lm_roofline_frac": flops_f / (ms_lm_fast / 1e3) / 1e12 / peak},
+                       "lm_roofline_frac": flm_f / (ms_lm_fast / 1e3) / 1e12 / peak},
         "train": {"profiles": TRAIN_N, "epochs": TRAIN_EPOCHS, "batch": TRAIN_BATCH,
                   "seconds_incl_synthesis": train_s, "final_loss": final_loss},
-        "e2e": {"value": conv_h * world / e2e_s, "unit": "pixels/s",
+        "e2e": {"value": match_h * world / e2e_s, "unit": "pixels/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": None,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
@@ -373,9 +498,18 @@ def run_ours(args, rank, world):
                                      "back from L2; ~5 GB/s over the launch)",
                      "kernel": "invert_kernel<6> (plain LM pass, no covariance)",
                      "kernel_ms": ms_lm,
+                     "work": work,
+                     "flops_method": fl_method,
+                     "flops_issued": fl_issued,
+                     "issued_tflops": issued_tf, "issued_frac": issued_tf / peak,
                      "note": "peak = FP32 pipe, 152 SM x 128 lanes x 2 flop x 2070 MHz (no "
-                             "measured FP32 peak in MEASURED_PEAKS.json); algorithmic flops = "
-                             f"passes x (149 x {FLOP_PER_LAMBDA} + {FLOP_PER_PASS_EXTRA}); "
+                             "measured FP32 peak in MEASURED_PEAKS.json); method flops = points "
+                             f"x {FLOP_SYNTH_PER_LAMBDA} (synthesis of every trial) + passes x "
+                             f"{FLOP_PER_PASS_EXTRA} + (accepted + pixels) x (points per pass "
+                             f"x {FLOP_DERIV_PER_LAMBDA} derivatives + {FLOP_NORMAL_EQ} normal "
+                             "equations); points = wavelength points the kernel evaluated (the "
+                             "grid points the packed filter table keeps); issued = derivatives "
+                             "on every pass; "
                              f"frac at the sampled {sm_mhz:.0f} MHz clock = "
                              f"{achieved / fp32_peak_tflops(sm_mhz):.3f}"},
         "clocks": clocks,
@@ -384,8 +518,9 @@ def run_ours(args, rank, world):
     res["gpu_launches"] = args.steps * graph_mixed.kernels()
     graph_mixed.close()
     graph_plain.close()
-    h.close()
-    return res
+    ctx = {"h": h, "blob": blob, "tf": tf, "tx": tx, "cfg_nn": cfg_nn, "cfg_plain": cfg_plain,
+           "conf_route": conf_route, "stream": stream, "dev": dev}
+    return res, ctx
 
 
 def workload_config(workload: str, npix: int, world: int) -> dict:
@@ -404,39 +539,91 @@ def workload_config(workload: str, npix: int, world: int) -> dict:
             "parallelism": f"independent maps x{world}"}
 
 
+def _oracle_init():
+    os.environ.update({k: "1" for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS",
+                                        "MKL_NUM_THREADS")})
+    if ROOT not in sys.path:
+        sys.path.insert(0, ROOT)
+    import oracle.lm  # noqa: F401  (imported before the timed map)
+
+
+def _oracle_chunk(job):
+    from oracle import lm
+    obs, w, T, x, line, cap = job
+    return lm.invert(obs, w, T, x, line, max_iter=cap)
+
+
+def oracle_sample(workload: str, n: int):
+    """The oracle's own view of a bounded sample of the map: n pixels evenly
+    spaced over it, synthesised by the oracle, noised, rounded to float32."""
+    from oracle import me
+    p, seed = map_params(workload, 0)
+    idx = np.linspace(0, p.shape[0] - 1, n).astype(np.int64)
+    x = W.wavelength_grid(NLAM)
+    T = W.hmi_filters(x)
+    f32 = lambda a_: np.asarray(a_, dtype=np.float32).astype(np.float64)  # noqa: E731
+    pp = f32(p[idx])
+    s_ = me.synth(pp, f32(T), f32(x), W.FE6173).reshape(n, -1)
+    obs, w = W.observe(s_, pp, W.noise(n, 4 * NF, seed + 7000))
+    return f32(obs), f32(w), f32(T), f32(x)
+
+
 def cpu_baseline(args, sample: int):
-    """The FP64 oracle (plain LM) on the host, on a bounded sample of the map."""
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    code = f"""
-import sys, time, json
-sys.path.insert(0, {ROOT!r})
-import numpy as np, workloads as W
-from oracle import me, lm
-wl = {args.workload!r}
-if wl == 'disk':
-    p, _ = W.full_disk_params(W.SEEDS['disk']); seed = W.SEEDS['disk']
-else:
-    p = W.quiet_and_active_params(1024 * 1024, W.SEEDS['map1024']); seed = W.SEEDS['map1024']
-npix = p.shape[0]; n = {sample}
-idx = np.linspace(0, npix - 1, n).astype(np.int64)
-x = W.wavelength_grid({NLAM}); T = W.hmi_filters(x)
-nz = W.noise(npix, 24, seed)[idx]
-s = me.synth(p[idx], T, x, W.FE6173).reshape(n, -1)
-obs, w = W.observe(s, p[idx], nz)
-t0 = time.perf_counter()
-r = lm.invert(obs, w, T, x, W.FE6173, max_iter={PLAIN_CAP})
-dt = time.perf_counter() - t0
-conv = int(np.sum((r['status'] == 0) | (r['status'] == 2)))
-print(json.dumps({{'value': conv / dt, 'seconds': dt, 'n': n}}))
-"""
-    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
-    if out.returncode != 0:
-        return {"value": None, "unit": "pixels/s", "cores": 1, "kind": "oracle",
-                "sample": f"failed: {out.stderr[-300:]}"}
-    d = json.loads(out.stdout.strip().splitlines()[-1])
-    return {"value": d["value"], "unit": "pixels/s", "cores": 1, "kind": "oracle",
-            "sample": f"{d['n']} pixels evenly spaced over the map, plain LM cap {PLAIN_CAP}, "
-                      f"{d['seconds']:.1f} s, numpy/scipy FP64, 1 thread"}
+    """The FP64 oracle (plain LM, cap 50) on every host core: a spawn pool
+    over pixel chunks (every pixel is inverted independently), timed from
+    the first chunk handed out to the last result.  Returns (cpu_baseline
+    object, the sample and the oracle's results)."""
+    import multiprocessing as mp
+    obs, w, T, x = oracle_sample(args.workload, sample)
+    cores = os.cpu_count() or 1
+    nchunk = max(1, min(4 * cores, sample // 8))
+    edges = np.linspace(0, sample, nchunk + 1).astype(int)
+    jobs = [(obs[a_:b_], w[a_:b_], T, x, W.FE6173, PLAIN_CAP) for a_, b_ in zip(edges[:-1], edges[1:])]
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(cores, initializer=_oracle_init) as pool:
+        pool.map(int, range(cores))  # workers up and importing before the clock starts
+        t0 = time.perf_counter()
+        parts = pool.map(_oracle_chunk, jobs)
+        dt = time.perf_counter() - t0
+    ref = {k: np.concatenate([p_[k] for p_ in parts]) for k in parts[0]}
+    conv = int(np.sum(ref["status"] == CONVERGED))
+    cb = {"value": conv / dt, "unit": "pixels/s", "cores": cores, "kind": "oracle",
+          "per_core": conv / dt / cores,
+          "sample": f"{sample} pixels evenly spaced over the map (synthesised by the oracle, "
+                    f"noise 1e-3 Ic), plain LM cap {PLAIN_CAP} from the standard guess, "
+                    f"{dt:.1f} s on {cores} processes (numpy/scipy FP64, one BLAS thread each); "
+                    f"counted like plain_lm (CONVERGED)",
+          "converged_fraction": conv / sample}
+    return cb, {"obs": obs, "w": w, "T": T, "x": x, "ref": ref}
+
+
+def oracle_errors(ctx, smp):
+    """GPU plain and mixed (the timed configuration) on the oracle's sample,
+    against the oracle's plain LM: the per-parameter error tables, and for the
+    mixed run the fraction of pixels whose chi2 matches the oracle's
+    (<= (1 + 1e-3) x)."""
+    import paper_0901_2702_gb300 as v
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    import parity
+    h, blob = ctx["h"], ctx["blob"].cpu().numpy()
+    o32, w32 = smp["obs"].astype(np.float32), smp["w"].astype(np.float32)
+    T32, x32 = smp["T"].astype(np.float32), smp["x"].astype(np.float32)
+    ref = smp["ref"]
+    g = v.vfisv_invert(h, o32, w32, T32, x32, W.FE6173, config=ctx["cfg_plain"])
+    _, chi2_flag, flag_unconv = MIXED[ctx["workload"]]
+    m = v.vfisv_invert_nn(h, blob, o32, w32, T32, x32, W.FE6173, config_nn=ctx["cfg_nn"],
+                          config_plain=ctx["cfg_plain"], chi2_flag=chi2_flag,
+                          flag_unconverged=flag_unconv, conf_route=ctx["conf_route"])
+    v.vfisv_check(h)
+    wd = parity.well_determined(ref)
+    le = m["chi2"].astype(np.float64) <= ref["chi2"] * (1 + CHI2_MATCH)
+    match = (m["status"] == CONVERGED) & le
+    return {"pixels": int(len(o32)),
+            "plain_vs_oracle": parity.error_table(g, ref, wd),
+            "mixed_vs_oracle_plain": parity.error_table(m, ref, wd),
+            "mixed_chi2_le_oracle_frac": float(le.mean()),
+            "mixed_matched_converged_frac": float(match.mean()),
+            "oracle_converged_frac": float(np.mean(ref["status"] == CONVERGED))}
 
 
 def run_serving(args):
@@ -622,7 +809,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="disk", choices=["disk", "map1024", "serving"])
-    ap.add_argument("--cpu-sample", type=int, default=384)
+    ap.add_argument("--cpu-sample", type=int, default=16384)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
@@ -631,7 +818,7 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
-        cb = cpu_baseline(args, args.cpu_sample)
+        cb, _ = cpu_baseline(args, args.cpu_sample)
         res = {"metric": METRIC, "value": cb["value"], "unit": "pixels/s", "n_gpus": world,
                "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
                "impl": "reference", "dtype": "f64", "data": "synthetic",
@@ -657,11 +844,14 @@ def main():
         import torch.distributed as tdist
         tdist.init_process_group("nccl")
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
-    res = run_ours(args, rank, world)
+    res, ctx = run_ours(args, rank, world)
     if rank == 0:
         if world == 1 and not args.no_cpu_baseline:
-            res["cpu_baseline"] = cpu_baseline(args, args.cpu_sample)
+            res["cpu_baseline"], smp = cpu_baseline(args, args.cpu_sample)
+            ctx["workload"] = args.workload
+            res["oracle_parity"] = oracle_errors(ctx, smp)
         print(json.dumps(res))
+    ctx["h"].close()
     if world > 1:
         import torch.distributed as tdist
         tdist.destroy_process_group()

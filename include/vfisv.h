@@ -124,7 +124,7 @@ typedef struct {
  *              The pixel number of the perturbations is the pixel's index in
  *              the call.  max_iter must stay below 2^20 with restarts.
  *   seed       key of the perturbations.
- *   wfa_pol    initialisation from the filtergrams (Sec. 6), 0 = off.
+ *   wfa_pol    initialisation from the filtergrams (Sec. 5), 0 = off.
  *              Where an inversion starts without given models (vfisv_invert
  *              with init == NULL, the re-inversion stage of vfisv_invert_nn),
  *              > 0 starts from the models of vfisv_init_models instead of the
@@ -200,7 +200,7 @@ int vfisv_invert_batch(vfisv_handle* h, const float* obs, const float* weights,
                        float* chi2_out, int32_t* iters_out, int32_t* status_out, float* cov_out,
                        float* latency_ms, void* stream);
 
-/* Initial models from the filtergrams (Sec. 6; the paper's methods are
+/* Initial models from the filtergrams (Sec. 5; the paper's methods are
  * cited, not printed -- this is one reading of them).  For each pixel of
  * obs [npix][4][nfilt] (3 <= nfilt <= 128; filters [nfilt][nlam] on wl_mA, any
  * order of centres):
@@ -301,13 +301,30 @@ int vfisv_set_pipeline_chunks(vfisv_handle* h, int32_t chunks);
  * on the device since the last check (VFISV_E_DEVICE) or a CUDA error. */
 int vfisv_check(vfisv_handle* h, void* stream);
 
+/* Work done by this handle's filter-position LM launches (nfilt = 6; the
+ * spectrograph-shaped path is not counted) since the handle was created or
+ * last reset, for measuring the method's own work (Sec. 4.4, Fig. 6):
+ *   out[0] fused passes: one per trial model plus one per starting model
+ *   out[1] accepted trials, each followed by a J^T W J / J^T W r build
+ *   out[2] pixels retired
+ *   out[3] wavelength points evaluated: passes x grid points in use (the
+ *          packed filter table leaves out points where every filter weight
+ *          is below 2^-40 of the largest, which cannot change an FP32 sum)
+ * Synchronises `stream` first; reset != 0 zeroes the counters afterwards.
+ * Replays of a captured graph add to them like direct calls. */
+int vfisv_counters(vfisv_handle* h, void* stream, uint64_t* out, int32_t reset);  /* out[4] */
+
 /* Milne-Eddington synthesis through the filters (Secs. 3.1-3.2).
  *   params   float32[npix][10]   model (alpha in [0,1] honoured)
  *   filters  float32[nfilt][nlam] transmission T_k(x_i)
  *   wl_mA    float32[nlam]       x_i = lambda_i - lambda0 in mA
  *   line     the triplet
  *   stokes   float32[npix][4][nfilt] output: S_jk = sum_i T_k(x_i) S_j(x_i)
- * 1 <= nfilt <= 8, 1 <= nlam <= 4096, npix >= 0 (0 is a no-op). */
+ * 1 <= nfilt <= 8 (filter positions, one pixel per thread), or 9 <= nfilt <=
+ * 128 narrow instrument profiles (spectrograph-shaped inputs, one pixel per
+ * warp: nlam <= 1024, each profile non-zero over at most 32 consecutive
+ * points, else VFISV_E_UNSUPPORTED on the device error word);
+ * 1 <= nlam <= 4096, npix >= 0 (0 is a no-op). */
 int vfisv_synth(vfisv_handle* h, const float* params, int64_t npix,
                 const float* filters, int32_t nfilt, const float* wl_mA,
                 int32_t nlam, const vfisv_line* line, float* stokes,
@@ -327,7 +344,12 @@ int vfisv_synth(vfisv_handle* h, const float* params, int64_t npix,
  *   status_out int32[npix]       VFISV_PIX_*
  *   cov_out    float32[npix][10][10] (J^T W J)^+ at params_out in parameter
  *              units (zero rows/columns for held parameters), or NULL
- * Only nfilt == 6 is compiled; 1 <= nlam <= 4096. */
+ * nfilt == 6 (filter positions, one pixel per thread slot; every option of
+ * vfisv_config), or 9 <= nfilt <= 128 narrow instrument profiles
+ * (spectrograph-shaped inputs, one pixel per warp, nlam <= 1024, profiles
+ * non-zero over at most 32 consecutive points; restarts, hess_reuse,
+ * fast_solve and a free filling factor are VFISV_E_UNSUPPORTED there);
+ * other nfilt: VFISV_E_UNSUPPORTED.  1 <= nlam <= 4096. */
 int vfisv_invert(vfisv_handle* h, const float* obs, const float* weights,
                  int32_t weights_per_pixel, const float* filters,
                  int32_t nfilt, const float* wl_mA, int32_t nlam,
@@ -375,17 +397,27 @@ int vfisv_nn_infer(vfisv_handle* h, const float* blob, const float* obs, int64_t
                    const vfisv_line* line, float* init_out, float* conf_out, float* raw_out,
                    void* stream);
 
-/* Mixed inversion: network guess, LM with cfg_nn, then every pixel that ends
- * with chi2 > chi2_flag (or, with flag_unconverged, that did not converge)
- * is inverted again from the standard guess with cfg_plain and keeps the
- * lower-chi2 result.  Arguments as vfisv_invert; iters_out counts the steps
- * of both runs; flagged_out (int32[npix], or NULL) marks the re-inverted
- * pixels. */
+/* Mixed inversion (Sec. 5: the network supplies an initial guess only; LM
+ * from the standard guess stays the fallback): network guess and confidence
+ * output, then
+ *   - pixels with confidence output > conf_route (the network's estimate of
+ *     its own log mean squared error in standardised units: an uncertain
+ *     guess) skip the LM run from the guess;
+ *   - the others run LM from the guess with cfg_nn;
+ *   - every routed pixel, and every pixel that ends with chi2 > chi2_flag (or,
+ *     with flag_unconverged, that did not converge; STALLED counts as
+ *     converged), is inverted from the standard guess with cfg_plain; a
+ *     re-inverted pixel keeps the lower-chi2 of its results (a routed pixel
+ *     the plain one).
+ * conf_route = +INFINITY disables routing (every pixel runs LM from the
+ * guess); NaN is VFISV_E_ARG.  Arguments as vfisv_invert; iters_out counts
+ * the steps of both runs; flagged_out (int32[npix], or NULL) marks the
+ * re-inverted pixels, routed ones included. */
 int vfisv_invert_nn(vfisv_handle* h, const float* blob, const float* obs, const float* weights,
                     int32_t weights_per_pixel, const float* filters, int32_t nfilt,
                     const float* wl_mA, int32_t nlam, const vfisv_line* line,
                     const vfisv_config* cfg_nn, const vfisv_config* cfg_plain,
-                    double chi2_flag, int32_t flag_unconverged, int64_t npix,
+                    double chi2_flag, int32_t flag_unconverged, double conf_route, int64_t npix,
                     float* params_out, float* chi2_out,
                     int32_t* iters_out, int32_t* status_out, float* cov_out,
                     int32_t* flagged_out, void* stream);
@@ -409,12 +441,19 @@ int vfisv_invert_nn(vfisv_handle* h, const float* blob, const float* obs, const 
  *     queue behind them.
  *   - The first call on a device looks up the array's device address and
  *     uploads the kernel's constants (blocking calls): make that first call
- *     before any stream capture.
+ *     before any stream capture.  First calls from several host threads at
+ *     once are safe (the set-up runs once per device, under a lock).
  *   - Every call, from any thread or stream, shares the one array: calls
  *     whose kernels overlap on the GPU race and corrupt each other's
- *     results; serialise them (one stream, or events).  Each call resets the
- *     work-queue counter itself; the rest of the array is overwritten before
- *     it is read. */
+ *     results; serialise them (one stream, or events).  Each call clears the
+ *     work-queue counter and the device error word itself, on `stream`; the
+ *     rest of the array is overwritten before it is read.
+ *   - Per-pixel problems go to status_out as in vfisv_invert.  A device-side
+ *     failure of the call itself (a bounded wait in the kernel that gave up;
+ *     its outputs are then not valid) is recorded in the array's error word:
+ *     read it with vfisv_noalloc_check before the next call.
+ *   - The call uses every SM of the device (no handle, so no
+ *     vfisv_set_sm_limit). */
 #define VFISV_NOALLOC_MAX_NLAM 4096
 #define VFISV_NOALLOC_MAX_SLOTS 38912
 #define VFISV_NOALLOC_SCRATCH_BYTES 8536576
@@ -423,6 +462,14 @@ int vfisv_invert_noalloc(const float* obs, const float* weights, int32_t weights
                          const vfisv_line* line, const float* init, const vfisv_config* cfg,
                          int64_t npix, float* params_out, float* chi2_out, int32_t* iters_out,
                          int32_t* status_out, float* cov_out, void* stream);
+
+/* Companion of vfisv_invert_noalloc (the paper has no counterpart either):
+ * synchronise `stream`, then report whether the most recent
+ * vfisv_invert_noalloc call on the current device flagged a device error
+ * (VFISV_E_DEVICE; the error word is cleared), VFISV_OK if not or if no call
+ * was made on this device yet, VFISV_E_CUDA for a CUDA error.  Allocates
+ * nothing. */
+int vfisv_noalloc_check(void* stream);
 
 #ifdef __cplusplus
 }

@@ -20,7 +20,7 @@ Modules
          derivatives only after a successful step (Fig. 6), covariance.
 ``mlp``  the initial-guess network (24 -> 256 -> 256 -> 256 -> 11, GELU):
          forward, backward, loss and Adam in FP64.
-``init`` initial models from the filtergrams (Sec. 6): weak-field B,
+``init`` initial models from the filtergrams (Sec. 5): weak-field B,
          gamma, the azimuth from Q and U, the polarisation level, and the
          paper's combination with the network.
 

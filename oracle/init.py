@@ -1,4 +1,4 @@
-"""Initial models from the observed filtergrams (Sec. 6), FP64 (oracle).
+"""Initial models from the observed filtergrams (Sec. 5), FP64 (oracle).
 
 TEST INFRASTRUCTURE ONLY -- see the package docstring.
 

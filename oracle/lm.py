@@ -31,7 +31,7 @@ Readings of points the paper leaves open or prints garbled:
   otherwise it stops at ``max_iter`` trial steps (status MAXITER).  The
   iteration count is the number of trial solves (the paper's Svdcmp count).
 * Without given initial models the iteration starts from the filtergram
-  models of ``oracle.init`` when ``wfa_pol`` > 0 (Sec. 6), else from the
+  models of ``oracle.init`` when ``wfa_pol`` > 0 (Sec. 5), else from the
   standard initial guess (the paper uses ANN/weak-field guesses):
   B = 500 G, gamma = 60 deg, psi = 45 deg, eta0 = 10, dlambdaD = 35 mA,
   a = 0.25, v = 0, S0 = 0.25 Ic, S1 = 0.75 Ic / mu, alpha = 1, where Ic is the
@@ -242,7 +242,7 @@ def invert(obs, w, filters, x, line, init=None, max_iter=50, conv_rtol=1e-4,
 
     bad = ~np.isfinite(obs).all(1) | ~np.isfinite(w).all(1) | ~(w.sum(1) > 0)
     if init is None and wfa_pol > 0:
-        from . import init as init_mod   # Sec. 6: models from the filtergrams
+        from . import init as init_mod   # Sec. 5: models from the filtergrams
         m = init_mod.initial_models(np.where(np.isfinite(obs), obs, 0.0), filters, x, line)
     elif init is None:
         m = standard_guess(np.where(np.isfinite(obs), obs, 0.0), nfilt, mu)
@@ -383,38 +383,61 @@ def invert(obs, w, filters, x, line, init=None, max_iter=50, conv_rtol=1e-4,
 
 
 def invert_mixed(obs, w, filters, x, line, blob, nn_cap=20, plain_cap=50, chi2_flag=3.0,
-                 flag_unconverged=True, wfa_pol=0.0, plain_wfa_pol=0.0, **kw):
+                 flag_unconverged=True, conf_route=np.inf, operand_round=None, wfa_pol=0.0,
+                 plain_wfa_pol=0.0, **kw):
     """Network-initialised inversion with plain re-inversion of flagged pixels.
 
-    The network (FP64 forward of ``blob``) gives the initial models; LM runs
-    with ``nn_cap``; pixels ending with chi2 > chi2_flag (or, with
-    flag_unconverged, not converged) are inverted again from the standard
-    guess with ``plain_cap`` and keep the lower chi2; iteration counts add.
+    The network (FP64 forward of ``blob``; with ``operand_round`` every
+    layer's operands rounded first, the tensor-core reading) gives the
+    initial models and the confidence output (column 10 of its outputs, its
+    estimate of the log mean squared error of the standardised guess).
+    Pixels whose confidence output is above ``conf_route`` (or not a number)
+    are routed: they skip the LM run from the guess and are inverted from the
+    standard guess only.  The others run LM with ``nn_cap``; those ending
+    with chi2 > chi2_flag (or, with flag_unconverged, not converged; STALLED
+    counts as converged) are inverted again from the standard guess with
+    ``plain_cap`` and keep the lower chi2; iteration counts add.  A routed
+    pixel keeps the plain result; if that has no finite chi2 it ends in
+    NAN_STATE with the network's guess and a zero covariance.
     With ``wfa_pol`` > 0 the network's guess is combined the paper's way
-    (Sec. 6): weak-field B and gamma below that polarisation level, the
+    (Sec. 5): weak-field B and gamma below that polarisation level, the
     wing azimuth everywhere (``oracle.init.merge_paper``); with
     ``plain_wfa_pol`` > 0 the re-inversion starts from the filtergram models
     (``oracle.init.initial_models``) instead of the standard guess."""
     from . import init as init_mod, mlp
     mu = float(line.get("mu", 1.0))
+    npix = obs.shape[0]
     weights, stats = mlp.unpack(blob)
-    y, _ = mlp.forward(weights, mlp.features(obs, stats))
+    y, _ = mlp.forward(weights, mlp.features(obs, stats), operand_round=operand_round)
     init = mlp.decode(y, obs, stats, mu)
+    conf = y[:, mlp.NOUT_PARAM]
     if wfa_pol > 0:
         init = init_mod.merge_paper(init, obs, filters, x, line, wfa_pol)
-    r = invert(obs, w, filters, x, line, init=init, max_iter=nn_cap, **kw)
-    conv = np.isin(r["status"], (CONVERGED, STALLED))
-    flag = (r["status"] != BAD_INPUT) & ((flag_unconverged & ~conv) | ~(r["chi2"] <= chi2_flag))
-    out = {k: np.array(v, copy=True) for k, v in r.items()}
+    routed = ~(conf <= conf_route)
+    run = np.flatnonzero(~routed)
+    out = {"params": init.copy(), "chi2": np.full(npix, np.inf),
+           "iters": np.zeros(npix, dtype=np.int64), "accepted": np.zeros(npix, dtype=np.int64),
+           "status": np.full(npix, NAN_STATE, dtype=np.int64), "cov": np.zeros((npix, NPAR, NPAR))}
+    if run.size:
+        r = invert(obs[run], w[run], filters, x, line, init=init[run], max_iter=nn_cap, **kw)
+        for k in ("params", "chi2", "iters", "accepted", "status", "cov"):
+            out[k][run] = r[k]
+    st = out["status"]
+    conv = np.isin(st, (CONVERGED, STALLED))
+    flag = routed | ((st != BAD_INPUT) &
+                     ((flag_unconverged & ~conv) | ~(out["chi2"] <= chi2_flag)))
     out["flagged"] = flag.astype(np.int32)
+    out["routed"] = routed.astype(np.int32)
+    out["confidence"] = conf
     if flag.any():
-        q = invert(obs[flag], w[flag], filters, x, line, init=None, max_iter=plain_cap,
-                   wfa_pol=plain_wfa_pol, **kw)
         ids = np.flatnonzero(flag)
+        q = invert(obs[ids], w[ids], filters, x, line, init=None, max_iter=plain_cap,
+                   wfa_pol=plain_wfa_pol, **kw)
         out["iters"][ids] += q["iters"]
+        out["accepted"][ids] += q["accepted"]
         plain_ok = (q["status"] != NAN_STATE) & np.isfinite(q["chi2"])
-        nn_ok = (r["status"][ids] != NAN_STATE) & np.isfinite(r["chi2"][ids])
-        take = plain_ok & (~nn_ok | (q["chi2"] < r["chi2"][ids]))
+        nn_ok = (st[ids] != NAN_STATE) & np.isfinite(out["chi2"][ids])
+        take = plain_ok & (~nn_ok | (q["chi2"] < out["chi2"][ids]))
         for k in ("params", "chi2", "status", "cov"):
             out[k][ids[take]] = q[k][take]
     return out

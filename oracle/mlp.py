@@ -89,18 +89,33 @@ def loss_and_grad_output(y, t, c=None):
     return L, dy
 
 
-def backward(weights, cache, dy):
-    """Gradients [(dW0,db0),...] from dL/dy and the forward cache."""
-    grads = [None] * len(weights)
-    d = dy
-    for l in range(len(weights) - 1, -1, -1):
-        h, z = cache[l]
-        if l < len(weights) - 1:
-            d = d * gelu_grad(z)
-        W, _ = weights[l]
+def backward(weights, cache, dy, operand_round=None, want_scale=False):
+    """Gradients [(dW0,db0),...] from dL/dy and the forward cache.
+
+    With ``operand_round`` (e.g. ``round_bf16``; the forward cache must come
+    from ``forward`` with the same rounding, so its layer inputs are already
+    rounded) the arithmetic of tensor-core training kernels with rounded
+    operands and a wide accumulator: dL/dy is rounded, each layer's weight
+    gradient is the exact product of its rounded input and the rounded
+    output gradient, its bias gradient the exact column sum of that rounded
+    gradient, and the gradient passed down, (d W^T) * GELU'(z) with W
+    rounded, is rounded once more.  ``want_scale`` also returns, per layer,
+    sum_m |h_mi| |d_mj| and sum_m |d_mj|: the magnitudes that bound how far
+    rounding the operands can move each gradient entry."""
+    r = operand_round if operand_round is not None else (lambda a: a)
+    nl = len(weights)
+    grads = [None] * nl
+    scale = [None] * nl
+    d = r(dy)
+    for l in range(nl - 1, -1, -1):
+        h, _ = cache[l]
         grads[l] = (h.T @ d, d.sum(axis=0))
-        d = d @ W.T
-    return grads
+        if want_scale:
+            scale[l] = (np.abs(h).T @ np.abs(d), np.abs(d).sum(axis=0))
+        if l > 0:
+            W, _ = weights[l]
+            d = r((d @ r(W).T) * gelu_grad(cache[l - 1][1]))
+    return (grads, scale) if want_scale else grads
 
 
 def cosine_lr(lr0, step, total):
@@ -213,14 +228,22 @@ def decode(y, obs, stats, mu=1.0):
     return m
 
 
-def loss_and_grad(blob, obs, params):
-    """FP64 loss and gradient (blob layout, trained part) of one batch."""
+def loss_and_grad(blob, obs, params, operand_round=None, want_scale=False):
+    """FP64 loss and gradient (blob layout, trained part) of one batch; with
+    ``operand_round`` the rounded-operand reading of forward and backward;
+    ``want_scale`` appends the gradient magnitude scales (blob layout)."""
     weights, stats = unpack(blob)
-    y, cache = forward(weights, features(obs, stats))
+    y, cache = forward(weights, features(obs, stats), operand_round=operand_round)
     L, dy = loss_and_grad_output(y, targets(params, obs, stats))
-    grads = backward(weights, cache, dy)
-    g = pack([(gw, gb) for gw, gb in grads], {k: np.zeros_like(v) for k, v in stats.items()})
-    return L, g[:blob_layout()["in_mean"][0]], y
+    zeros = {k: np.zeros_like(v) for k, v in stats.items()}
+    ntrain = blob_layout()["in_mean"][0]
+    if want_scale:
+        grads, scale = backward(weights, cache, dy, operand_round, want_scale=True)
+        sc = pack([(a, b) for a, b in scale], zeros)[:ntrain]
+    else:
+        grads = backward(weights, cache, dy, operand_round)
+    g = pack([(gw, gb) for gw, gb in grads], zeros)[:ntrain]
+    return (L, g, y, sc) if want_scale else (L, g, y)
 
 
 def train(obs, params, steps, batch, lr0=1e-3, seed=0):

@@ -17,6 +17,7 @@ import numpy as np
 
 __all__ = [
     "vfisv_create", "vfisv_destroy", "vfisv_synth", "vfisv_invert", "vfisv_check",
+    "vfisv_counters",
     "vfisv_strerror", "vfisv_config_default", "vfisv_nn_init", "vfisv_nn_train",
     "vfisv_nn_grad", "vfisv_nn_infer", "vfisv_invert_nn", "vfisv_graph_begin", "vfisv_graph_end",
     "vfisv_graph_launch", "vfisv_graph_kernels", "vfisv_graph_destroy", "vfisv_autotune",
@@ -97,8 +98,13 @@ def load():
     lib.vfisv_nn_infer.restype = ctypes.c_int
     lib.vfisv_invert_nn.argtypes = [P, P, P, P, I32, P, I32, P, I32, ctypes.POINTER(vfisv_line),
                                     ctypes.POINTER(vfisv_config), ctypes.POINTER(vfisv_config),
-                                    ctypes.c_double, I32, I64, P, P, P, P, P, P, P]
+                                    ctypes.c_double, I32, ctypes.c_double, I64, P, P, P, P, P,
+                                    P, P]
     lib.vfisv_invert_nn.restype = ctypes.c_int
+    lib.vfisv_counters.argtypes = [P, P, ctypes.POINTER(ctypes.c_uint64), I32]
+    lib.vfisv_counters.restype = ctypes.c_int
+    lib.vfisv_noalloc_check.argtypes = [P]
+    lib.vfisv_noalloc_check.restype = ctypes.c_int
     lib.vfisv_graph_begin.argtypes = [P, P]
     lib.vfisv_graph_begin.restype = ctypes.c_int
     lib.vfisv_graph_end.argtypes = [P, P, ctypes.POINTER(ctypes.c_void_p)]
@@ -227,6 +233,17 @@ def _empty(ref, shape, dtype):
 
 def vfisv_check(h: Handle, stream=None) -> None:
     _check(load().vfisv_check(h.ptr, ctypes.c_void_p(_stream(None, stream))), "vfisv_check")
+
+
+def vfisv_counters(h: Handle, stream=None, reset: bool = False) -> dict:
+    """Work of the handle's filter-position LM launches: fused passes,
+    accepted trials, pixels retired and wavelength points evaluated since
+    creation or the last reset."""
+    c = (ctypes.c_uint64 * 4)()
+    _check(load().vfisv_counters(h.ptr, ctypes.c_void_p(_stream(None, stream)), c,
+                                 int(bool(reset))), "vfisv_counters")
+    return {"passes": int(c[0]), "accepted": int(c[1]), "retired": int(c[2]),
+            "points": int(c[3])}
 
 
 def vfisv_synth(h: Handle, params, filters, wl_mA, line, stokes=None, stream=None):
@@ -365,9 +382,10 @@ def vfisv_nn_infer(h: Handle, blob, obs, line, want_conf=True, want_raw=False, i
 
 def vfisv_invert_nn(h: Handle, blob, obs, weights, filters, wl_mA, line, config_nn=None,
                     config_plain=None, chi2_flag: float = 3.0, flag_unconverged: bool = True,
-                    want_cov=True, out=None, stream=None):
+                    conf_route: float = float("inf"), want_cov=True, out=None, stream=None):
     """Mixed inversion: network guess + LM, plain LM re-inversion of flagged pixels
-    (chi2 > chi2_flag, and with flag_unconverged also those that did not converge)."""
+    (chi2 > chi2_flag, and with flag_unconverged also those that did not converge);
+    pixels whose confidence output exceeds ``conf_route`` go to plain LM directly."""
     npix = int(obs.shape[0])
     nfilt, nlam = int(filters.shape[0]), int(filters.shape[1])
     per_pixel = 1 if (len(weights.shape) >= 2 and int(weights.shape[0]) == npix and
@@ -390,7 +408,7 @@ def vfisv_invert_nn(h: Handle, blob, obs, weights, filters, wl_mA, line, config_
     rc = load().vfisv_invert_nn(h.ptr, ptrs[0][0], ptrs[1][0], ptrs[2][0], per_pixel, ptrs[3][0],
                                 nfilt, ptrs[4][0], nlam, ctypes.byref(ln), ctypes.byref(cn),
                                 ctypes.byref(cp_), float(chi2_flag), int(bool(flag_unconverged)),
-                                npix,
+                                float(conf_route), npix,
                                 *[p for _, (p, _k) in outs],
                                 ctypes.c_void_p(_stream(obs, stream)))
     _check(rc, "vfisv_invert_nn")

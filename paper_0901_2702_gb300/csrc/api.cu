@@ -46,6 +46,10 @@ struct vfisv_handle {
   cudaEvent_t pipe_ev[7] = {};
   int pipe_chunks = 3;     // vfisv_set_pipeline_chunks (0: stage the whole map)
   int sm_limit = 0;        // vfisv_set_sm_limit (0: every SM)
+  // work counters of the filter-position LM launches (vfisv_counters):
+  // fused passes, accepted trials, pixels retired, wavelength points
+  // evaluated (device, u64 each)
+  unsigned long long* counters = nullptr;
 };
 
 struct vfisv_graph {
@@ -385,6 +389,8 @@ struct DevInvert {
   const int64_t* map_off = nullptr;
   int nmaps = 0;
   unsigned long long *map_done = nullptr, *map_t = nullptr;
+  // invert only the listed pixels (*npix_dev of them) of a map of npix
+  const int64_t* pix_list = nullptr;
 };
 
 // Pack the filter table, zero the work queue, run the persistent LM kernel
@@ -405,7 +411,7 @@ int invert_device_wide(vfisv_handle* h, const DevInvert& d, int nfilt, int nlam,
   int* err = (int*)(ws + L.err);
   const float* init = d.init;
   if (!init && cfg->wfa_pol > 0.0) {
-    // start from the weak-field models of the observations (Sec. 6)
+    // start from the weak-field models of the observations (Sec. 5)
     int rc = grow(&h->geom, &h->geom_bytes, filter_geom_bytes());
     if (!rc) rc = grow(&h->wfinit, &h->wfinit_bytes, (size_t)npix * 10 * sizeof(float));
     if (rc) return rc;
@@ -481,7 +487,7 @@ int invert_device(vfisv_handle* h, const DevInvert& d, int nfilt, int nlam,
   float* table = (float*)(ws + L.table);
   const float* init = d.init;
   if (!init && cfg->wfa_pol > 0.0) {
-    // start from the weak-field models of the filtergrams (Sec. 6)
+    // start from the weak-field models of the filtergrams (Sec. 5)
     int rc = grow(&h->geom, &h->geom_bytes, filter_geom_bytes());
     if (!rc) rc = grow(&h->wfinit, &h->wfinit_bytes, (size_t)npix * 10 * sizeof(float));
     if (rc) return rc;
@@ -530,9 +536,13 @@ int invert_device(vfisv_handle* h, const DevInvert& d, int nfilt, int nlam,
   a.hess_reuse = cfg->hess_reuse;
   a.fast_solve = cfg->fast_solve;
   a.rs_state = cfg->restarts ? ws + L.rs : nullptr;
+  a.pix_list = d.pix_list;
+  a.counters = h->counters;
   if (launch_invert(a, nfilt, grid, block, smem, s) != cudaSuccess) return VFISV_E_CUDA;
-  if (d.cov && launch_covariance(d.cov, d.status, npix, npix_dev, cfg->free_mask,
-                                cfg->fast_solve, s) !=
+  // with a pixel list the listed pixels lie anywhere in [0, npix): the
+  // covariance kernel sweeps the whole map (it skips rows by status)
+  if (d.cov && launch_covariance(d.cov, d.status, npix, d.pix_list ? nullptr : npix_dev,
+                                cfg->free_mask, cfg->fast_solve, s) !=
                    cudaSuccess)
     return VFISV_E_CUDA;
   return VFISV_OK;
@@ -589,7 +599,26 @@ int vfisv_create(vfisv_handle** out, int device) {
     delete h;
     return VFISV_E_CUDA;
   }
+  if (cudaMalloc(&h->counters, 4 * sizeof(unsigned long long)) != cudaSuccess ||
+      cudaMemset(h->counters, 0, 4 * sizeof(unsigned long long)) != cudaSuccess) {
+    cudaGetLastError();
+    if (h->counters) cudaFree(h->counters);
+    delete h;
+    return VFISV_E_NOMEM;
+  }
   *out = h;
+  return VFISV_OK;
+}
+
+int vfisv_counters(vfisv_handle* h, void* stream, uint64_t* out, int32_t reset) {
+  if (!h || !out) return VFISV_E_ARG;
+  if (set_device(h)) return VFISV_E_CUDA;
+  if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return VFISV_E_CUDA;
+  unsigned long long c[4] = {0, 0, 0, 0};
+  if (cudaMemcpy(c, h->counters, sizeof(c), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return VFISV_E_CUDA;
+  for (int i = 0; i < 4; ++i) out[i] = (uint64_t)c[i];
+  if (reset && cudaMemset(h->counters, 0, sizeof(c)) != cudaSuccess) return VFISV_E_CUDA;
   return VFISV_OK;
 }
 
@@ -598,6 +627,7 @@ void vfisv_destroy(vfisv_handle* h) {
   cudaSetDevice(h->device);
   cudaDeviceSynchronize();
   if (h->ws) cudaFree(h->ws);
+  if (h->counters) cudaFree(h->counters);
   if (h->stage) cudaFree(h->stage);
   if (h->nnws) cudaFree(h->nnws);
   if (h->mixws) cudaFree(h->mixws);
@@ -1169,11 +1199,11 @@ int vfisv_invert_nn(vfisv_handle* h, const float* blob, const float* obs, const 
                     int32_t weights_per_pixel, const float* filters, int32_t nfilt,
                     const float* wl_mA, int32_t nlam, const vfisv_line* line,
                     const vfisv_config* cfg_nn, const vfisv_config* cfg_plain,
-                    double chi2_flag, int32_t flag_unconverged, int64_t npix,
-                    float* params_out, float* chi2_out,
+                    double chi2_flag, int32_t flag_unconverged, double conf_route,
+                    int64_t npix, float* params_out, float* chi2_out,
                     int32_t* iters_out, int32_t* status_out, float* cov_out,
                     int32_t* flagged_out, void* stream) {
-  if (!blob || !cfg_plain) return VFISV_E_ARG;
+  if (!blob || !cfg_plain || isnan(conf_route)) return VFISV_E_ARG;
   int rc = check_invert_args(h, obs, weights, filters, nfilt, wl_mA, nlam, line, cfg_nn, npix,
                              params_out, chi2_out, iters_out, status_out);
   if (rc) return rc;
@@ -1207,7 +1237,8 @@ int vfisv_invert_nn(vfisv_handle* h, const float* blob, const float* obs, const 
       return vfisv_invert_nn(h, bd, (const float*)d[0],
                              weights_per_pixel ? (const float*)d[1] : wsh, weights_per_pixel, fd,
                              nfilt, wd, nlam, line, cfg_nn, cfg_plain, chi2_flag,
-                             flag_unconverged, n, (float*)d[2], (float*)d[3], (int32_t*)d[4],
+                             flag_unconverged, conf_route, n, (float*)d[2], (float*)d[3],
+                             (int32_t*)d[4],
                              (int32_t*)d[5], (float*)d[6], (int32_t*)d[7], s);
     });
   }
@@ -1235,7 +1266,9 @@ int vfisv_invert_nn(vfisv_handle* h, const float* blob, const float* obs, const 
     off += up(bytes);
     return at;
   };
+  const bool route = isfinite(conf_route) != 0;
   const size_t o_init = place((size_t)npix * 10 * 4), o_cnt = place(8),
+               o_conf = route ? place((size_t)npix * 4) : 0, o_rcnt = route ? place(8) : 0,
                o_idx = place((size_t)npix * 8), o_obs = place((size_t)npix * nobs * 4),
                o_w = weights_per_pixel ? place((size_t)npix * nobs * 4) : 0,
                o_p = place((size_t)npix * 10 * 4), o_c = place((size_t)npix * 4),
@@ -1245,11 +1278,12 @@ int vfisv_invert_nn(vfisv_handle* h, const float* blob, const float* obs, const 
   if ((rc = grow(&h->nnws, &h->nnws_bytes, nn::infer_workspace_bytes()))) return rc;
   char* mw = (char*)h->mixws;
   float* init = (float*)(mw + o_init);
+  float* conf = route ? (float*)(mw + o_conf) : nullptr;
   if (nn::nn_infer(h->nnws, (const float*)st.bufs[4].dev, o, npix, (float)line->mu,
-                   init, nullptr, nullptr, s) != cudaSuccess)
+                   init, conf, nullptr, s) != cudaSuccess)
     return VFISV_E_CUDA;
   if (cfg_nn->wfa_pol > 0.0) {
-    // the paper's combination (Sec. 6): weak-field B, gamma below the
+    // the paper's combination (Sec. 5): weak-field B, gamma below the
     // polarisation threshold, the wing azimuth everywhere
     if ((rc = grow(&h->geom, &h->geom_bytes, filter_geom_bytes()))) return rc;
     if (launch_weak_field(o, npix, nullptr, (const float*)st.bufs[2].dev, nfilt,
@@ -1269,9 +1303,21 @@ int vfisv_invert_nn(vfisv_handle* h, const float* blob, const float* obs, const 
   d.iters = (int32_t*)st.bufs[7].dev;
   d.status = (int32_t*)st.bufs[8].dev;
   d.cov = (float*)st.bufs[9].dev;
-  if ((rc = invert_device(h, d, nfilt, nlam, line, cfg_nn, npix, nullptr, s))) return rc;
   int64_t* cnt = (int64_t*)(mw + o_cnt);
   int64_t* idx = (int64_t*)(mw + o_idx);
+  const int64_t* n_first = nullptr;
+  if (route) {
+    // the pixels the network is confident about run LM from its guess;
+    // the others go straight to the plain run (their list reuses idx,
+    // which the flag step overwrites only after the first run)
+    int64_t* rcnt = (int64_t*)(mw + o_rcnt);
+    if (nn::route_by_confidence(conf, npix, (float)conf_route, init, idx, rcnt, d.params, d.chi2,
+                                d.iters, d.status, s) != cudaSuccess)
+      return VFISV_E_CUDA;
+    d.pix_list = idx;
+    n_first = rcnt;
+  }
+  if ((rc = invert_device(h, d, nfilt, nlam, line, cfg_nn, npix, n_first, s))) return rc;
   float* og = (float*)(mw + o_obs);
   float* wg = weights_per_pixel ? (float*)(mw + o_w) : nullptr;
   if (nn::flag_and_gather(d.status, d.chi2, npix, (float)chi2_flag, flag_unconverged != 0, o, w,

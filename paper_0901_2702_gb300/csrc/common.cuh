@@ -21,10 +21,16 @@ enum : int { kDevErrNone = 0, kDevErrTableWait = 1, kDevErrNnWait = 2, kDevErrPo
 // Filter table layout in global and shared memory: nlam rows of `stride`
 // floats {T_0(x_i), ..., T_{nf-1}(x_i), x_i, pad...}, then one row holding
 // tau_k = sum_i T_k(x_i).  stride = round_up(nf + 1, 4), so a row is a whole
-// number of 16-byte vectors.
+// number of 16-byte vectors.  Only the first table_rows() rows are used: the
+// packing leaves out grid points where every filter weight is negligible
+// (synth.cu) and records the count in the last float of the tau row.
 __host__ __device__ inline int table_stride(int nf) { return ((nf + 1) + 3) & ~3; }
 __host__ __device__ inline int table_floats(int nf, int nlam) {
   return (nlam + 1) * table_stride(nf);
+}
+__device__ __forceinline__ int table_rows(const float* tab, int nf, int nlam) {
+  const int S = table_stride(nf);
+  return __float_as_int(tab[(size_t)nlam * S + S - 1]);
 }
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -151,6 +157,14 @@ struct InvertArgs {
   int restarts = 0;          // randomised restarts (Sec. 4.2): trigger bit mask, 0 = off
   uint64_t seed = 0;         // key of the restart perturbations
   char* rs_state = nullptr;  // restarts: per-slot state, layout RestartState
+  // optional list of the pixels to invert: queue position q inverts pixel
+  // pix_list[q] (q < *npix_dev); the others are not touched
+  const int64_t* pix_list = nullptr;
+  // optional work counters, added to by every CTA when it exits:
+  // [0] fused passes (each trial model, plus the starting model),
+  // [1] accepted trials (each followed by a J^T W J build), [2] pixels
+  // retired, [3] wavelength points evaluated (passes x table rows used)
+  unsigned long long* counters = nullptr;
 };
 
 constexpr int kScratchPerSlot = 45 + 9;  // packed J^T W J and J^T W r
@@ -243,7 +257,7 @@ cudaError_t launch_wide_synth(const float* params, int64_t npix, const float* ta
                               const LineK& lk, cudaStream_t s);
 cudaError_t launch_wide_invert(const InvertArgs& a, int nf, cudaStream_t s);
 
-// prep.cu: initial models from the filtergrams (Sec. 6); `geom` is device
+// prep.cu: initial models from the filtergrams (Sec. 5); `geom` is device
 // scratch of filter_geom_bytes()
 size_t filter_geom_bytes();
 cudaError_t launch_weak_field(const float* obs, int64_t npix, const int64_t* npix_dev,

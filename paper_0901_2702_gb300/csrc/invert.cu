@@ -321,8 +321,9 @@ __device__ __noinline__ int fused_pass(const PixK P, const float* __restrict__ t
   for (int r = 0; r < (NM ? kNmRows : 1); ++r)
 #pragma unroll
     for (int k = 0; k < NF; ++k) accn[r][k] = 0.0f;
+  const int nl = table_rows(tab, NF, nlam);
 #pragma unroll 1
-  for (int i = 0; i < nlam; ++i) {
+  for (int i = 0; i < nl; ++i) {
     float T[NF];
     const float x = load_row<NF>(tab + (size_t)i * S, T);
     lambda_step<NF, true, NM>(c_W, P, x, T, acc, accn);
@@ -349,13 +350,15 @@ __device__ __noinline__ int fused_pass(const PixK P, const float* __restrict__ t
 // per thread) so that the registers of the wavelength loop hold only its
 // accumulators.
 constexpr int kStateWords = 10 + 10 + 2 + 2 + 2 + 1 + 1;  // M, Mt, chi2b, eps, pix, it, near
-// Layout: table | dump pool | state | pool owners (padded to 16 B) | mbarrier.
+// Layout: table | dump pool | state | pool owners (padded to 16 B) | work
+// counters (4 x u64) | mbarrier.
+constexpr int kNumCounters = 4;
 __host__ __device__ constexpr size_t pool_owner_bytes(int nt) {
   return ((size_t)dump_pool(nt) * 4 + 15) & ~(size_t)15;
 }
 __host__ __device__ constexpr size_t invert_smem_bytes(int tabf, int nacc, int nt) {
   return (size_t)tabf * 4 + (size_t)dump_pool(nt) * nacc * 32 * 4 + (size_t)kStateWords * nt * 4 +
-         pool_owner_bytes(nt) + 16;
+         pool_owner_bytes(nt) + 8 * kNumCounters + 16;
 }
 
 // RS: randomised restarts compiled in (A.restarts != 0).  DF: the damped
@@ -384,10 +387,14 @@ __global__ void __launch_bounds__(BS, 1) invert_kernel(InvertArgs A) {
   int* sIt = reinterpret_cast<int*>(sPix + nt);   // [nt]
   int* sNear = sIt + nt;  // [nt] last accepted step was close to the minimum (Hessian reuse)
   uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + (invert_smem_bytes(tabf, NACC, nt) - 16) / 4);
-  int* owner = reinterpret_cast<int*>(mbar) - pool_owner_bytes(nt) / 4;  // [npool]
+  // passes, accepted, retired, wavelength points evaluated
+  unsigned long long* cnt = reinterpret_cast<unsigned long long*>(mbar) - kNumCounters;
+  int* owner = reinterpret_cast<int*>(cnt) - pool_owner_bytes(nt) / 4;  // [npool]
   if (tid < npool) owner[tid] = 0;  // published by the barrier inside the table load
+  if (tid < kNumCounters) cnt[tid] = 0;
   if (!tma_load_table(tab, A.table, (uint32_t)(tabf * sizeof(float)), mbar, A.err)) return;
   const float* tau = tab + (size_t)A.nlam * S;
+  const int nrows = table_rows(tab, NF, A.nlam);
   const int64_t slot = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t ns = A.nslots;
   float* scr = A.scratch + slot;
@@ -413,6 +420,7 @@ __global__ void __launch_bounds__(BS, 1) invert_kernel(InvertArgs A) {
       if (pix < 0) {
         pix = (long long)atomicAdd(A.queue, 1ull);
         if (pix >= npix) break;
+        if (A.pix_list) pix = A.pix_list[pix];
         fresh = true;
         sPix[tid] = pix;
         const float* o = A.obs + pix * NOBS;
@@ -554,6 +562,10 @@ __global__ void __launch_bounds__(BS, 1) invert_kernel(InvertArgs A) {
       c2 /= (double)dof;
     }
 
+    if (A.counters) {
+      atomicAdd(&cnt[0], 1ull);
+      atomicAdd(&cnt[3], (unsigned long long)nrows);
+    }
     bool accept, retire = false;
     int status = VFISV_PIX_MAXITER;
     int it = sIt[tid];
@@ -617,6 +629,7 @@ __global__ void __launch_bounds__(BS, 1) invert_kernel(InvertArgs A) {
       }
     }
     sIt[tid] = it;
+    if (A.counters && accept && !fresh) atomicAdd(&cnt[1], 1ull);
 
     if (accept) {
       // ---- J^T W J and J^T W r at the new best model (compensated FP32) ----
@@ -750,9 +763,14 @@ __global__ void __launch_bounds__(BS, 1) invert_kernel(InvertArgs A) {
       }
       map_retired(A, pix);
       sPix[tid] = -1;
+      if (A.counters) atomicAdd(&cnt[2], 1ull);
     }
   }
 #undef ST
+  if (A.counters) {
+    __syncthreads();  // every slot of the CTA has left the queue loop
+    if (tid < kNumCounters) atomicAdd(A.counters + tid, cnt[tid]);
+  }
 }
 
 // Covariance of every pixel that finished with a model, from the packed

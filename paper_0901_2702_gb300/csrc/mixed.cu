@@ -2,6 +2,10 @@
 // pixels that did not converge or whose chi2 exceeds a threshold are flagged,
 // gathered and inverted again from the standard guess; the better of the two
 // results (lower chi2) is kept.  The flagged count stays on the device.
+// With confidence routing, pixels whose confidence output (the network's
+// estimate of its own log squared error) is above a threshold skip the LM
+// run from the guess: they are flagged from the start and take the plain
+// run's result.
 #include "common.cuh"
 #include "nn.cuh"
 
@@ -45,6 +49,49 @@ cudaError_t flag_and_gather(const int32_t* status, const float* chi2, int64_t np
   return cudaGetLastError();
 }
 
+// Routing by the confidence output: pixels with conf > conf_route get an
+// empty first-stage result (status NAN_STATE, chi2 = +inf, no iterations,
+// the network's guess as parameters), which the flag step re-inverts and the
+// merge replaces; the others are listed for the first-stage LM run (one
+// atomic per warp, so the list keeps the pixel order within each warp).
+__global__ void route_kernel(const float* __restrict__ conf, int64_t npix, float conf_route,
+                             const float* __restrict__ init, int64_t* __restrict__ list,
+                             unsigned long long* __restrict__ count, float* __restrict__ params,
+                             float* __restrict__ chi2, int32_t* __restrict__ iters,
+                             int32_t* __restrict__ status) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool in = p < npix;
+  // a NaN confidence is routed too (the guess cannot be trusted)
+  const bool routed = in && !(conf[p] <= conf_route);
+  const unsigned keep = __ballot_sync(0xffffffffu, in && !routed);
+  const int lane = threadIdx.x & 31;
+  unsigned long long base = 0;
+  if (keep) {
+    if (lane == __ffs(keep) - 1) base = atomicAdd(count, (unsigned long long)__popc(keep));
+    base = __shfl_sync(0xffffffffu, base, __ffs(keep) - 1);
+  }
+  if (!in) return;
+  if (routed) {
+    for (int q = 0; q < 10; ++q) params[p * 10 + q] = init[p * 10 + q];
+    chi2[p] = INFINITY;
+    iters[p] = 0;
+    status[p] = VFISV_PIX_NAN_STATE;
+  } else {
+    list[base + __popc(keep & ((1u << lane) - 1u))] = p;
+  }
+}
+
+cudaError_t route_by_confidence(const float* conf, int64_t npix, float conf_route,
+                                const float* init, int64_t* list, int64_t* count, float* params,
+                                float* chi2, int32_t* iters, int32_t* status, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(count, 0, sizeof(int64_t), s);
+  if (e != cudaSuccess) return e;
+  const unsigned nb = (unsigned)((npix + 255) / 256);
+  route_kernel<<<nb, 256, 0, s>>>(conf, npix, conf_route, init, list,
+                                  (unsigned long long*)count, params, chi2, iters, status);
+  return cudaGetLastError();
+}
+
 __global__ void merge_kernel(const int64_t* __restrict__ count, const int64_t* __restrict__ index,
                              const float* __restrict__ p2, const float* __restrict__ c2,
                              const int32_t* __restrict__ i2, const int32_t* __restrict__ s2,
@@ -64,6 +111,9 @@ __global__ void merge_kernel(const int64_t* __restrict__ count, const int64_t* _
     status[p] = sp;
     if (cov && cov2)
       for (int q = 0; q < 100; ++q) cov[p * 100 + q] = cov2[j * 100 + q];
+  } else if (cov && status[p] == VFISV_PIX_NAN_STATE) {
+    // no valid result from either run (a routed pixel's row was never written)
+    for (int q = 0; q < 100; ++q) cov[p * 100 + q] = 0.0f;
   }
 }
 

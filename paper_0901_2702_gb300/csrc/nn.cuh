@@ -71,7 +71,12 @@ cudaError_t nn_infer(void* ws, const float* blob, const float* obs, int64_t n, f
 // rows the gradient/forward paths pad a batch of n samples to
 int64_t padded_rows(int64_t n);
 
-// mixed.cu: flag pixels for plain re-inversion, gather them, merge results.
+// mixed.cu: route by the confidence output (the listed pixels run LM from
+// the guess; the others get an empty first-stage result), flag pixels for
+// plain re-inversion, gather them, merge results.
+cudaError_t route_by_confidence(const float* conf, int64_t npix, float conf_route,
+                                const float* init, int64_t* list, int64_t* count, float* params,
+                                float* chi2, int32_t* iters, int32_t* status, cudaStream_t s);
 cudaError_t flag_and_gather(const int32_t* status, const float* chi2, int64_t npix,
                             float chi2_flag, bool flag_unconverged, const float* obs, const float* w,
                             int64_t w_stride, int nobs, int64_t* count, int64_t* index,

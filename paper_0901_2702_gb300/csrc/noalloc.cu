@@ -5,6 +5,9 @@
 // handle's workspace.
 #include <math.h>
 
+#include <atomic>
+#include <mutex>
+
 #include "common.cuh"
 #include "vfisv.h"
 
@@ -29,17 +32,20 @@ static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
 // Device address of g_scratch per device ordinal, filled on the first call made
 // with that device current (the name g_scratch in host code is only a host-side
-// stand-in and must never be passed to a kernel).
+// stand-in and must never be passed to a kernel).  First calls from several
+// host threads are serialised by g_setup; later calls read the published
+// address without locking.
 constexpr int kMaxDevices = 64;
-void* g_addr[kMaxDevices] = {};
+std::atomic<void*> g_addr[kMaxDevices] = {};
+std::mutex g_setup;
 Weideman g_W{};
-bool g_W_ready = false;
+std::once_flag g_W_once;
 
 // Weideman (1994) coefficients as the handle path builds them: trapezoidal
 // Fourier coefficients of (L^2 + t^2) exp(-t^2), t = L tan(theta/2), in
-// double precision.  Host-only, computed once per process.
+// double precision.  Host-only, computed once per process (any thread).
 const Weideman& coefficients() {
-  if (!g_W_ready) {
+  std::call_once(g_W_once, [] {
     const int N = kWeidN, M = 64 * N;
     const double L = sqrt(N / sqrt(2.0)), pi = 3.14159265358979323846;
     g_W.L = (float)L;
@@ -52,28 +58,39 @@ const Weideman& coefficients() {
       }
       g_W.a[n] = (float)(s / M);
     }
-    g_W_ready = true;
-  }
+  });
   return g_W;
 }
 
 int setup(int dev, void** out) {
   if (dev < 0 || dev >= kMaxDevices) return VFISV_E_ARG;
-  if (!g_addr[dev]) {
-    void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || !p) {
-      cudaGetLastError();
-      return VFISV_E_CUDA;
+  void* p = g_addr[dev].load(std::memory_order_acquire);
+  if (!p) {
+    std::lock_guard<std::mutex> lock(g_setup);
+    p = g_addr[dev].load(std::memory_order_relaxed);
+    if (!p) {
+      if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || !p) {
+        cudaGetLastError();
+        return VFISV_E_CUDA;
+      }
+      // error word starts clear; the Weideman coefficients of the LM kernel's
+      // constant bank are uploaded for this device
+      if (cudaMemset(p, 0, kHead) != cudaSuccess) return VFISV_E_CUDA;
+      if (invert_set_constants(coefficients()) != cudaSuccess) return VFISV_E_CUDA;
+      g_addr[dev].store(p, std::memory_order_release);
     }
-    // error word starts clear; the Weideman coefficients of the LM kernel's
-    // constant bank are uploaded for this device
-    if (cudaMemset(p, 0, kHead) != cudaSuccess) return VFISV_E_CUDA;
-    if (invert_set_constants(coefficients()) != cudaSuccess) return VFISV_E_CUDA;
-    g_addr[dev] = p;
   }
-  *out = g_addr[dev];
+  *out = p;
   return VFISV_OK;
 }
+
+// This entry point belongs to no handle: its launches may use every SM,
+// whatever SM limit a handle call made earlier on this thread left behind.
+struct NoSmLimit {
+  int saved = t_sm_limit;
+  NoSmLimit() { t_sm_limit = 0; }
+  ~NoSmLimit() { t_sm_limit = saved; }
+};
 
 }  // namespace
 
@@ -106,6 +123,7 @@ extern "C" int vfisv_invert_noalloc(const float* obs, const float* weights,
   int rc = setup(dev, &base);
   if (rc) return rc;
   cudaStream_t s = (cudaStream_t)stream;
+  NoSmLimit all_sms;
 
   int64_t nslots = 0;
   int grid = 0, block = 128;
@@ -121,8 +139,9 @@ extern "C" int vfisv_invert_noalloc(const float* obs, const float* weights,
   }
   char* b = (char*)base;
   float* table = (float*)(b + kHead);
-  // the work-queue counter must start at zero on every call
-  if (cudaMemsetAsync(b + 64, 0, sizeof(unsigned long long), s) != cudaSuccess)
+  // the error word and the work-queue counter start at zero on every call
+  // (so vfisv_noalloc_check reports this call's device errors only)
+  if (cudaMemsetAsync(b, 0, 64 + sizeof(unsigned long long), s) != cudaSuccess)
     return VFISV_E_CUDA;
   if (launch_pack_table(filters, nfilt, wl_mA, nlam, table, s) != cudaSuccess)
     return VFISV_E_CUDA;
@@ -162,4 +181,19 @@ extern "C" int vfisv_invert_noalloc(const float* obs, const float* weights,
           cudaSuccess)
     return VFISV_E_CUDA;
   return VFISV_OK;
+}
+
+extern "C" int vfisv_noalloc_check(void* stream) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return VFISV_E_CUDA;
+  if (dev < 0 || dev >= kMaxDevices) return VFISV_E_ARG;
+  if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return VFISV_E_CUDA;
+  void* p = g_addr[dev].load(std::memory_order_acquire);
+  if (!p) return VFISV_OK;  // no call on this device yet
+  int err = 0;
+  if (cudaMemcpy(&err, p, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return VFISV_E_CUDA;
+  if (err == 0) return VFISV_OK;
+  if (cudaMemset(p, 0, sizeof(int)) != cudaSuccess) return VFISV_E_CUDA;
+  return VFISV_E_DEVICE;
 }

@@ -1,7 +1,7 @@
 // Per-pixel preparation helpers of the paper's pipeline: the empirical
 // Stokes-I weight for full-disk maps (Sec. 4.3, Eq. 14) with the continuum
 // centre-to-limb variation (Eq. 15), and initial models from the
-// filtergrams (Sec. 6): weak-field B and gamma, the azimuth from the line
+// filtergrams (Sec. 5): weak-field B and gamma, the azimuth from the line
 // wings, the polarisation level, the centre-of-gravity velocity.
 #include "common.cuh"
 

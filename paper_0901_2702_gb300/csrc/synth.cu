@@ -6,25 +6,75 @@ namespace vfisv {
 
 // Pack filters [nf][nlam] and offsets [nlam] into the row-major table and
 // append tau_k = sum_i T_k(x_i).  One block; threads stride over rows.
+//
+// Rows whose largest |T_k(x_i)| is at most kRowDrop times the largest weight
+// of the table are left out (kept rows stay in grid order): their products
+// change a filtered value S_k = sum_i T_k(x_i) y(x_i) by less than
+// nlam * 2^-40 * max|T| * max|y|, five orders of magnitude below the FP32
+// rounding of S_k, so the sums are those over the whole grid.  For the HMI-like
+// filters (Gaussian FWHM 76 mA x sinc^2, six positions 69 mA apart) on the
+// 149-point grid 79 rows remain: the far wings, where every filter is below
+// 1e-12 of its peak, carry no weight.  tau_k still sums every row.  The
+// number of kept rows goes to the last float of the tau row (as int bits).
+constexpr float kRowDrop = 0x1p-40f;
+
 __global__ void pack_table_kernel(const float* __restrict__ filters, int nf,
                                   const float* __restrict__ wl, int nlam,
                                   float* __restrict__ table) {
   const int S = table_stride(nf);
-  for (int i = threadIdx.x; i < nlam; i += blockDim.x) {
-    float* row = table + (size_t)i * S;
-    for (int k = 0; k < nf; ++k) row[k] = filters[(size_t)k * nlam + i];
-    row[nf] = wl[i];
-    for (int j = nf + 1; j < S; ++j) row[j] = 0.0f;
+  __shared__ float red[32];
+  __shared__ int wsum[32];
+  __shared__ int base;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  // largest |weight| (a NaN weight keeps its row: the NaN reaches the sums)
+  float m = 0.0f;
+  for (int i = threadIdx.x; i < nf * nlam; i += blockDim.x) m = fmaxf(m, fabsf(filters[i]));
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if (lane == 0) red[warp] = m;
+  if (threadIdx.x == 0) base = 0;
+  __syncthreads();
+  m = 0.0f;
+  for (int w = 0; w < nw; ++w) m = fmaxf(m, red[w]);
+  const float thr = m * kRowDrop;
+  // ordered compaction, blockDim rows at a time
+  for (int i0 = 0; i0 < nlam; i0 += blockDim.x) {
+    const int i = i0 + threadIdx.x;
+    bool keep = false;
+    if (i < nlam) {
+      float r = 0.0f;
+      bool nan = false;
+      for (int k = 0; k < nf; ++k) {
+        const float t = filters[(size_t)k * nlam + i];
+        nan |= isnan(t);
+        r = fmaxf(r, fabsf(t));
+      }
+      keep = nan || r > thr;
+    }
+    const unsigned b = __ballot_sync(0xffffffffu, keep);
+    if (lane == 0) wsum[warp] = __popc(b);
+    __syncthreads();
+    int off = base;
+    for (int w = 0; w < warp; ++w) off += wsum[w];
+    if (keep) {
+      float* row = table + (size_t)(off + __popc(b & ((1u << lane) - 1u))) * S;
+      for (int k = 0; k < nf; ++k) row[k] = filters[(size_t)k * nlam + i];
+      row[nf] = wl[i];
+      for (int j = nf + 1; j < S; ++j) row[j] = 0.0f;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0)
+      for (int w = 0; w < nw; ++w) base += wsum[w];
+    __syncthreads();
   }
   // tau: one warp per filter, fixed summation order (lane-strided, then a
   // shuffle tree) so the result does not depend on the launch.
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int k = warp; k < S; k += blockDim.x >> 5) {
+  for (int k = warp; k < S; k += nw) {
     float s = 0.0f;
     if (k < nf)
       for (int i = lane; i < nlam; i += 32) s += filters[(size_t)k * nlam + i];
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) table[(size_t)nlam * S + k] = (k < nf) ? s : 0.0f;
+    if (lane == 0)
+      table[(size_t)nlam * S + k] = (k < nf) ? s : (k == S - 1 ? __int_as_float(base) : 0.0f);
   }
 }
 
@@ -44,6 +94,7 @@ __global__ void __launch_bounds__(128) synth_kernel(SynthArgs A) {
                       mbar, A.err))
     return;
   const float* tau = tab + (size_t)A.nlam * S;
+  const int nl = table_rows(tab, NF, A.nlam);
 
   for (int64_t pix = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; pix < A.npix;
        pix += (int64_t)gridDim.x * blockDim.x) {
@@ -57,14 +108,14 @@ __global__ void __launch_bounds__(128) synth_kernel(SynthArgs A) {
 #pragma unroll
       for (int k = 0; k < NF; ++k) acc[0][s][k] = accn[0][s][k] = 0.0f;
     const PixK P = make_pixk(A.lk, B, gam, eta0, dld, dmp, v);
-    for (int i = 0; i < A.nlam; ++i) {
+    for (int i = 0; i < nl; ++i) {
       float T[NF];
       const float x = load_row<NF>(tab + (size_t)i * S, T);
       lambda_step<NF, false>(A.W, P, x, T, acc);
     }
     if (alpha != 1.0f) {  // non-magnetic component: the same line with B = 0
       const PixK Pn = make_pixk(A.lk, 0.0f, gam, eta0, dld, dmp, v);
-      for (int i = 0; i < A.nlam; ++i) {
+      for (int i = 0; i < nl; ++i) {
         float T[NF];
         const float x = load_row<NF>(tab + (size_t)i * S, T);
         lambda_step<NF, false>(A.W, Pn, x, T, accn);

@@ -1,4 +1,4 @@
-"""Initial models from the filtergrams (Sec. 6) on the GPU vs the oracle,
+"""Initial models from the filtergrams (Sec. 5) on the GPU vs the oracle,
 and what they change in the inversion.
 
 Tolerances: the kernel runs in FP32 on the same float32 observables; its

@@ -201,3 +201,21 @@ def test_full_map_sampled(vf):
     assert np.mean(c["rel"][c["both"]] <= 1e-3) >= 0.95
     st = r["status"].cpu().numpy()
     assert np.all((st >= 0) & (st <= 2))
+
+
+def test_work_counters(vf):
+    """The LM kernel's work counters (vfisv_counters): one pass per trial plus
+    one per starting model, every pixel retired, the packed table's 79 kept
+    grid points per pass, and accepted trials close to the oracle's count of
+    successful steps on the same inputs (trajectories part at near ties)."""
+    v, h, torch = vf
+    p, obs, w = _case(2000, 61)
+    v.vfisv_counters(h, reset=True)
+    g = _gpu(v, h, torch, obs, w)
+    c = v.vfisv_counters(h, reset=True)
+    assert c["retired"] == 2000
+    assert c["passes"] == int(g["iters"].sum()) + 2000
+    assert c["points"] == 79 * c["passes"]
+    o = lm.invert(obs, w, f32(T), f32(X), LINE)
+    assert abs(c["accepted"] / o["accepted"].sum() - 1) < 0.03, (c, o["accepted"].sum())
+    assert v.vfisv_counters(h)["passes"] == 0  # reset

@@ -2,8 +2,11 @@
 what it gains over plain Levenberg-Marquardt.
 
 Tolerances for the BF16 tensor-core kernels (8-bit mantissa operands, FP32
-accumulation) against FP64: raw outputs within 0.05 (standardised units),
-loss within 2 %, every layer's gradient within 5 % relative L2 error.
+accumulation): against the oracle evaluated with the same operands rounded
+to bfloat16, element by element within a small multiple of one bfloat16
+rounding step (2^-8) of each value's magnitude; against the unrounded FP64
+network, raw outputs within 0.05 (standardised units), loss within 2 %,
+every layer's gradient within 5 % relative L2 error.
 """
 import numpy as np
 import pytest
@@ -45,20 +48,41 @@ def test_init_statistics_match_oracle(vf):
 
 
 def test_forward_and_gradient_vs_oracle(vf):
+    """Loss and gradient of vfisv_nn_grad against the oracle.
+
+    Element by element against the oracle's rounded-operand reading of the
+    training kernels (bfloat16 features, weights, activations and output /
+    input gradients, exact products, FP64 sums): each entry g_ij = sum_m
+    h_mi d_mj may differ by the FP32 accumulation and by the rare operand
+    that rounds to the neighbouring bfloat16 value, i.e. by a small multiple
+    of 2^-8 of its magnitude sum S_ij = sum_m |h_mi| |d_mj|.  Then, as a
+    whole, against the unrounded FP64 backward (raw outputs, loss, per-layer
+    relative L2 error of the gradient)."""
     v, h, torch = vf
     p, obs, w = _oracle_set(1000, 41)
     blob = _random_blob(1, obs, p)
-    L_ref, g_ref, y_ref = mlp.loss_and_grad(blob, obs, p)
-    r = v.vfisv_nn_infer(h, blob.astype(np.float32), obs.astype(np.float32), LINE, want_raw=True)
-    assert np.abs(r["raw"] - y_ref).max() < 0.05
+    L_b, g_b, y_b, S = mlp.loss_and_grad(blob, obs, p, operand_round=mlp.round_bf16,
+                                         want_scale=True)
     loss, g = v.vfisv_nn_grad(h, blob.astype(np.float32), obs.astype(np.float32),
                               p.astype(np.float32))
+    g = g.astype(np.float64)
+    r = np.abs(g - g_b) / np.maximum(S, 1e-30)
+    print(f"\n|g - g_bf16| / S: max {r.max():.3e} p99.9 {np.percentile(r, 99.9):.3e} "
+          f"median {np.median(r):.3e}; loss {loss[0]:.6f} vs {L_b:.6f}")
+    assert np.median(r) < 2.0 ** -12
+    assert np.mean(r <= 2.0 ** -8) >= 0.999
+    assert r.max() <= 4 * 2.0 ** -8
+    assert abs(loss[0] / L_b - 1) < 1e-3
+    # against the exact FP64 network
+    L_ref, g_ref, y_ref = mlp.loss_and_grad(blob, obs, p)
+    r2 = v.vfisv_nn_infer(h, blob.astype(np.float32), obs.astype(np.float32), LINE, want_raw=True)
+    assert np.abs(r2["raw"] - y_ref).max() < 0.05
     assert abs(loss[0] / L_ref - 1) < 2e-2
     lay = mlp.blob_layout()
     for name in ("W0", "b0", "W1", "b1", "W2", "b2", "W3", "b3"):
         o, shp = lay[name]
         n = int(np.prod(shp))
-        a, b = g[o:o + n].astype(np.float64), g_ref[o:o + n]
+        a, b = g[o:o + n], g_ref[o:o + n]
         rel = np.linalg.norm(a - b) / np.linalg.norm(b)
         assert rel < 5e-2, (name, rel)
 
@@ -216,3 +240,37 @@ def test_mixed_pipeline_vs_oracle(vf):
     both = np.isin(g["status"], (0, 2)) & np.isin(ref["status"], (0, 2))
     rel = np.abs(g["chi2"][both] / ref["chi2"][both] - 1)
     assert both.mean() > 0.5 and np.mean(rel <= 1e-3) >= 0.95
+
+
+def test_confidence_routing_bit_exact(vf):
+    """Routing by the confidence output: every routed pixel ends with exactly
+    the result of a plain vfisv_invert call (standard guess, cfg_plain), every
+    unrouted pixel that is not flagged with exactly the result of LM from the
+    network's guess (cfg_nn), and every routed pixel is reported as flagged.
+    Two thresholds: half the pixels routed, and none."""
+    v, h, torch = vf
+    tp, obs, tf, tx = _gpu_training_set(v, h, torch, 3000, 48)
+    blob = v.vfisv_nn_init(h, obs, tp, seed=4)
+    v.vfisv_nn_train(h, blob, obs, tp, batch=512, epochs=2, lr0=1e-3, seed=6)
+    sig = 1e-3 * (tp[:, 7] + tp[:, 8])[:, None]
+    wts = (1.0 / (sig * sig)).expand(obs.shape[0], 24).contiguous()
+    g = v.vfisv_nn_infer(h, blob, obs, LINE)
+    cn, cp = {"max_iter": 25}, {"max_iter": 40}
+    plain = v.vfisv_invert(h, obs, wts, tf, tx, LINE, config=cp)
+    first = v.vfisv_invert(h, obs, wts, tf, tx, LINE, init=g["init"], config=cn)
+    for k in (float(g["conf"].median().item()), float("inf")):
+        m = v.vfisv_invert_nn(h, blob, obs, wts, tf, tx, LINE, config_nn=cn, config_plain=cp,
+                              chi2_flag=2.5, flag_unconverged=True, conf_route=k)
+        v.vfisv_check(h)
+        routed = g["conf"] > k
+        assert torch.all(m["flagged"][routed] == 1)
+        keep = ~routed & (m["flagged"] == 0)
+        for key in ("params", "chi2", "status", "cov"):
+            assert torch.equal(m[key][routed], plain[key][routed]), key
+            assert torch.equal(m[key][keep], first[key][keep]), key
+        assert torch.equal(m["iters"][routed], plain["iters"][routed])
+        assert torch.equal(m["iters"][keep], first["iters"][keep])
+        if k == float("inf"):
+            assert not routed.any()
+        else:
+            assert 0.3 < routed.float().mean().item() < 0.7

@@ -63,12 +63,15 @@ def test_pipeline_depth_bounds(vf):
     v.vfisv_set_pipeline_chunks(h, 3)
 
 
-def test_mixed_inversion_host_pipeline(vf):
+@pytest.mark.parametrize("route", [False, True])
+def test_mixed_inversion_host_pipeline(vf, route):
     v, h, torch = vf
     obs, w, tf, tx, p = _map(v, h, torch, 72)
     blob = v.vfisv_nn_init(h, obs, p, seed=3)
+    k = float(v.vfisv_nn_infer(h, blob, obs, LINE)["conf"].median().item()) if route \
+        else float("inf")
     kw = dict(config_nn={"max_iter": 20}, config_plain={"max_iter": 30}, chi2_flag=2.5,
-              want_cov=True)
+              conf_route=k, want_cov=True)
     rd = v.vfisv_invert_nn(h, blob, obs, w[0].contiguous(), tf, tx, LINE, **kw)
     rh = v.vfisv_invert_nn(h, _host(blob), _host(obs), _host(w[0]), _host(tf), _host(tx), LINE,
                            **kw)

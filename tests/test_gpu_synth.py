@@ -105,3 +105,34 @@ def test_full_map_sampled(vf):
     idx = np.random.default_rng(0).choice(npix, 2048, replace=False)
     e = _err(g[idx], me.synth(p[idx], f32(T), f32(X), LINE), p[idx])
     assert e.max() <= TOL, e.max()
+
+
+def _kept_rows(T_):
+    """The grid points the packed table keeps: some filter weight above 2^-40
+    of the table's largest (host restatement of the packing rule)."""
+    return np.abs(T_).max(axis=0) > np.abs(T_).max() * 2.0 ** -40
+
+
+def test_negligible_grid_points_left_out(vf):
+    """The packed table leaves out grid points whose filter weights are all
+    below 2^-40 of the largest (for the HMI-like filters on the 149-point
+    grid: the far wings, 70 of 149 points).  Synthesis through the full grid
+    and through a grid the caller has already cut to the kept points agree
+    to FP32 rounding (tau, summed over every point, may move by an ulp), and
+    both stay within the parity bound of the oracle's full-grid sums."""
+    v, h, torch = vf
+    keep = _kept_rows(f32(T))
+    assert keep.sum() == 79
+    p = f32(W.quiet_and_active_params(2048, 55))
+    full = _gpu(v, h, torch, p)
+    cut = _gpu(v, h, torch, p, T_=T[:, keep], x_=X[keep])
+    ic = (p[:, 7] + p[:, 8])[:, None, None]
+    assert (np.abs(full - cut) / ic).max() <= 2e-7
+    ref = me.synth(p, f32(T), f32(X), LINE)
+    assert _err(full, ref, p).max() <= TOL
+    # a filter table without negligible points keeps every point
+    T2 = np.full((6, 37), 1.0 / 37)
+    x2 = np.linspace(-200, 200, 37)
+    e = _err(_gpu(v, h, torch, p[:64], T_=T2, x_=x2), me.synth(p[:64], f32(T2), f32(x2), LINE),
+             p[:64])
+    assert e.max() <= TOL

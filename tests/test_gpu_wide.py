@@ -88,7 +88,7 @@ def test_wide_band_too_wide_is_reported(vf):
 
 
 def test_wide_initial_models_vs_oracle(vf):
-    """Weak-field initial models from 112-sample spectra (Sec. 6) vs the
+    """Weak-field initial models from 112-sample spectra (Sec. 5) vs the
     oracle's, with the tolerances of the filtergram test."""
     from oracle import init
     v, h, torch = vf

@@ -1,4 +1,4 @@
-"""Pins of the oracle's initial models from the filtergrams (Sec. 6).
+"""Pins of the oracle's initial models from the filtergrams (Sec. 5).
 
 The weak-field relations are checked where they are exact to first/second
 order: profiles of a weak field sampled by narrow (delta) filters close to

@@ -219,3 +219,79 @@ def test_free_filling_factor_round_trip():
                      free_mask=0x3FF)
     assert np.all(free["chi2"] <= held["chi2"] * (1 + 1e-9) * (24 - 9) / (24 - 10) + 1e-12)
     assert np.all((free["params"][:, 9] >= 0) & (free["params"][:, 9] <= 1))
+
+
+def test_damping_floor_reading_is_not_load_bearing(monkeypatch):
+    """The paper gives Table 2 without a floor for eps; the oracle keeps
+    eps >= 1e-9.  With a floor of 1e-12 instead, the converged results of the
+    standard-guess inversion of the uniform mix barely move: the floor only
+    binds after ~20 successes in a row, by which time the convergence test
+    has normally stopped the pixel."""
+    p, s, o, w = _obs(48, 31)
+    r9 = lm.invert(o, w, T, X, LINE, max_iter=50)
+    monkeypatch.setattr(lm, "EPS_MIN", 1e-12)
+    r12 = lm.invert(o, w, T, X, LINE, max_iter=50)
+    both = (r9["status"] == lm.CONVERGED) & (r12["status"] == lm.CONVERGED)
+    assert both.mean() > 0.5
+    same_st = (r9["status"] == r12["status"]).mean()
+    assert same_st >= 0.95
+    rel = np.abs(r12["chi2"][both] / r9["chi2"][both] - 1)
+    assert (rel < 1e-6).mean() >= 0.95, np.sort(rel)[-5:]
+    assert (r9["iters"][both] == r12["iters"][both]).mean() >= 0.95
+
+
+def _random_blob(seed, obs, params):
+    from oracle import mlp
+    rng = np.random.default_rng(seed)
+    weights = [(rng.uniform(-1, 1, (a, b)) * np.sqrt(6.0 / a), rng.normal(0, 0.05, b))
+               for a, b in zip(mlp.LAYERS[:-1], mlp.LAYERS[1:])]
+    return mlp.pack(weights, mlp.statistics(obs, params))
+
+
+def test_mixed_routing_extremes():
+    """Confidence routing of the mixed inversion at its two limits: every
+    pixel routed gives exactly plain LM from the standard guess; none routed
+    gives LM from the network's guess followed by the plain re-inversion of
+    the flagged pixels, composed here by hand from lm.invert."""
+    from oracle import mlp
+    p, s, o, w = _obs(16, 33)
+    blob = _random_blob(5, o, p)
+    plain = lm.invert(o, w, T, X, LINE, max_iter=30)
+    allr = lm.invert_mixed(o, w, T, X, LINE, blob, nn_cap=10, plain_cap=30, conf_route=-np.inf)
+    assert allr["routed"].all() and allr["flagged"].all()
+    for k in ("params", "chi2", "status", "iters", "accepted", "cov"):
+        np.testing.assert_array_equal(allr[k], plain[k])
+    none = lm.invert_mixed(o, w, T, X, LINE, blob, nn_cap=10, plain_cap=30, chi2_flag=2.0,
+                           flag_unconverged=True, conf_route=np.inf)
+    assert not none["routed"].any()
+    weights, stats = mlp.unpack(blob)
+    y, _ = mlp.forward(weights, mlp.features(o, stats))
+    first = lm.invert(o, w, T, X, LINE, init=mlp.decode(y, o, stats), max_iter=10)
+    conv = np.isin(first["status"], (lm.CONVERGED, lm.STALLED))
+    flag = ~conv | ~(first["chi2"] <= 2.0)
+    np.testing.assert_array_equal(none["flagged"], flag.astype(np.int32))
+    ids = np.flatnonzero(flag)
+    second = lm.invert(o[ids], w[ids], T, X, LINE, max_iter=30)
+    exp_chi2 = first["chi2"].copy()
+    better = second["chi2"] < first["chi2"][ids]
+    exp_chi2[ids[better]] = second["chi2"][better]
+    np.testing.assert_array_equal(none["chi2"], exp_chi2)
+    np.testing.assert_array_equal(none["iters"][ids], first["iters"][ids] + second["iters"])
+    np.testing.assert_array_equal(none["confidence"], y[:, 10])
+
+
+def test_mixed_routing_splits_by_confidence():
+    """A threshold between the confidence outputs routes exactly the pixels
+    above it, which end with their plain result."""
+    p, s, o, w = _obs(12, 34)
+    blob = _random_blob(6, o, p)
+    probe = lm.invert_mixed(o, w, T, X, LINE, blob, nn_cap=0, plain_cap=0, conf_route=np.inf)
+    k = float(np.median(probe["confidence"]))
+    r = lm.invert_mixed(o, w, T, X, LINE, blob, nn_cap=8, plain_cap=20, conf_route=k)
+    routed = probe["confidence"] > k
+    np.testing.assert_array_equal(r["routed"].astype(bool), routed)
+    ids = np.flatnonzero(routed)
+    q = lm.invert(o[ids], w[ids], T, X, LINE, max_iter=20)
+    ok = np.isfinite(q["chi2"])
+    np.testing.assert_array_equal(r["chi2"][ids[ok]], q["chi2"][ok])
+    np.testing.assert_array_equal(r["iters"][ids], q["iters"])

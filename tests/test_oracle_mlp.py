@@ -154,3 +154,46 @@ def test_forward_with_rounded_operands():
     xg = mlp.round_bf16(x)
     np.testing.assert_array_equal(mlp.forward([(W, b)], xg, operand_round=mlp.round_bf16)[0],
                                   xg @ W + b)
+
+
+def _grad_case(n=400, seed=41):
+    import workloads as W
+    from oracle import me
+    x = W.wavelength_grid()
+    T = W.hmi_filters(x)
+    p = W.training_params(n, seed)
+    s = me.synth(p, T, x, W.FE6173).reshape(n, -1)
+    obs, _ = W.observe(s, p, W.noise(n, 24, seed))
+    rng = np.random.default_rng(1)
+    weights = [(rng.uniform(-1, 1, (a, b)) * np.sqrt(6.0 / a), rng.normal(0, 0.05, b))
+               for a, b in zip(mlp.LAYERS[:-1], mlp.LAYERS[1:])]
+    return mlp.pack(weights, mlp.statistics(obs, p)), obs, p
+
+
+def test_rounded_backward_identity_is_the_exact_backward():
+    """With an identity rounding the rounded-operand backward runs every
+    rounding site and must reproduce the exact FP64 backward (pinned by
+    finite differences above) bit for bit: a misplaced operand, transpose or
+    activation derivative on the rounded path would show here."""
+    blob, obs, p = _grad_case()
+    L0, g0, y0 = mlp.loss_and_grad(blob, obs, p)
+    L1, g1, y1, sc = mlp.loss_and_grad(blob, obs, p, operand_round=lambda a: a, want_scale=True)
+    assert L0 == L1
+    np.testing.assert_array_equal(g0, g1)
+    np.testing.assert_array_equal(y0, y1)
+    assert np.all(sc >= np.abs(g0) - 1e-15)  # |sum h d| <= sum |h| |d|
+
+
+def test_bf16_backward_within_rounding_of_exact():
+    """Rounding every operand to bfloat16 moves each operand by at most 2^-9
+    relative, so each gradient entry moves by a small multiple of 2^-8 of its
+    magnitude sum S = sum_m |h_mi| |d_mj| (the multiple grows through the four
+    layers, as the rounding of one layer feeds the next): |g_bf16 - g| <=
+    8 x 2^-8 x S everywhere, and the bulk far below one 2^-8."""
+    blob, obs, p = _grad_case()
+    _, g0, _ = mlp.loss_and_grad(blob, obs, p)
+    _, gb, _, sc = mlp.loss_and_grad(blob, obs, p, operand_round=mlp.round_bf16, want_scale=True)
+    r = np.abs(gb - g0) / np.maximum(sc, 1e-300)
+    assert r.max() <= 8 * 2.0 ** -8, r.max()
+    assert np.median(r) <= 2.0 ** -8
+    assert np.any(gb != g0)  # the rounding does act

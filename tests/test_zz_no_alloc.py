@@ -3,7 +3,12 @@ allocate device memory (a host framework that owns every byte through its
 own pool, or a real-time pipeline that allocates only at start-up because
 cudaMalloc/cudaFree can synchronise the device).  It keeps its scratch in a
 fixed array inside the library.  Called twice in a row, on two different
-maps, through the C ABI, it must reproduce the handle-based vfisv_invert.
+maps, through the C ABI, it must reproduce the handle-based vfisv_invert;
+so must a map larger than the array's resident pixel slots (60,000 pixels
+against VFISV_NOALLOC_MAX_SLOTS = 38,912: the slots refill from the work
+queue, and where the GPU could hold more slots than the array the grid is
+capped) and the double-float solve option.  vfisv_noalloc_check, its
+error-word companion, reports no device error after each call.
 
 This file is collected last on purpose, so that a run stopping at the first
 failure has already run every other test.
@@ -52,6 +57,11 @@ def _noalloc(v, torch, obs, w, tf, tx, cfg):
            out["status"].data_ptr(), out["cov"].data_ptr(),
            ctypes.c_void_p(torch.cuda.current_stream(dev).cuda_stream))
     assert rc == 0, v.vfisv_strerror(rc)
+    chk = lib.vfisv_noalloc_check
+    chk.argtypes = [P]
+    chk.restype = ctypes.c_int
+    rc = chk(ctypes.c_void_p(torch.cuda.current_stream(dev).cuda_stream))
+    assert rc == 0, v.vfisv_strerror(rc)
     torch.cuda.synchronize()
     return {k: t.cpu().numpy() for k, t in out.items()}
 
@@ -64,9 +74,11 @@ def test_noalloc_matches_handle_path_twice():
     build.build()
     import paper_0901_2702_gb300 as v
     h = v.vfisv_create(0)
-    cfg = v.vfisv_config_default()
-    # two different maps, one call each, back to back on the shared array
-    for n, seed in ((3000, 21), (1100, 22)):
+    # two different maps, one call each, back to back on the shared array;
+    # then a map with more pixels than resident slots, and the double-float
+    # solve
+    for n, seed, fast in ((3000, 21, 0), (1100, 22, 0), (60000, 23, 0), (5000, 24, 1)):
+        cfg = v.vfisv_config_default(fast_solve=fast)
         obs, w, tf, tx = _map(v, h, torch, n, seed)
         got = _noalloc(v, torch, obs, w, tf, tx, cfg)
         ref = v.vfisv_invert(h, obs, w, tf, tx, W.FE6173, config=cfg)
