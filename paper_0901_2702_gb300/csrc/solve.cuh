@@ -18,6 +18,18 @@ constexpr int kNPk = 45;  // packed lower triangle of a 9x9 matrix
 
 __device__ __forceinline__ int tri(int i, int j) { return i * (i + 1) / 2 + j; }  // i >= j
 
+// 2^e as a float / double built from its exponent bits (e clamped to the
+// normal range); a product with it is exact unless the result leaves the
+// normal range.
+__device__ __forceinline__ float pow2f(int e) {
+  e = max(-126, min(127, e));
+  return __int_as_float((e + 127) << 23);
+}
+__device__ __forceinline__ double pow2d(int e) {
+  e = max(-1022, min(1023, e));
+  return __longlong_as_double((long long)(e + 1023) << 52);
+}
+
 // Table 2 (with the oracle's reading of its overlapping rows).
 __device__ __forceinline__ double eps_update(double e, bool success) {
   double n;
@@ -203,28 +215,64 @@ __device__ __forceinline__ void scaled_system(const float* scr, int64_t ns, uint
 }
 
 // Eq. 5 with the Marquardt diagonal (Eq. 4): delta = (A + eps diag A)^-1 g,
-// Jacobi-scaled, in FP64 (the default precision of the solve).
+// in FP64 (the default precision of the solve).
+//
+// The system is balanced by a diagonal scaling P of powers of two before the
+// factorisation: with A' = P A P (diagonal in [1/4, 1)), (A' + eps diag A') y
+// = P g has the solution y = P^-1 delta, the same system.  Scaling by powers
+// of two is exact (an exponent change in FP32, before the conversion to
+// FP64), so the FP64 work is only the damped diagonal, the Cholesky
+// factorisation and the substitutions; the rare fallback (a pivot below
+// 1e-10) takes the unit-diagonal Jacobi scaling and the truncated
+// eigen-decomposition.
 template <int N = kNP>
 static __device__ __noinline__ void damped_step_fp64(const float* scr, int64_t ns, uint32_t free_mask, double eps,
                             double (&delta)[N]) {
-  double L[(N * (N + 1) / 2)], sc[N];
+  double L[(N * (N + 1) / 2)];
+  int ex[N];  // P_ii = 2^-ex[i]
   bool held[N];
-  scaled_system<N>(scr, ns, free_mask, eps, L, sc, held);
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    const float d = scr[(int64_t)tri(i, i) * ns];
+    held[i] = !((free_mask >> i) & 1u) || !(d > 0.0f) || !isfinite(d);
+    int k = 0;
+    frexpf(held[i] ? 1.0f : d, &k);  // d = m 2^k, m in [1/2, 1)
+    ex[i] = (k + 1) >> 1;            // d 2^-2ex in [1/4, 1)
+  }
+  const double one_eps = 1.0 + eps;
+  float pw[N];
+#pragma unroll
+  for (int i = 0; i < N; ++i) pw[i] = pow2f(-ex[i]);
+#pragma unroll
+  for (int i = 0; i < N; ++i)
+#pragma unroll
+    for (int j = 0; j <= i; ++j) {
+      double m;
+      if (i == j)
+        m = held[i] ? 1.0 : (double)(scr[(int64_t)tri(i, i) * ns] * pw[i] * pw[i]) * one_eps;
+      else
+        m = (held[i] || held[j]) ? 0.0 : (double)(scr[(int64_t)tri(i, j) * ns] * pw[i] * pw[j]);
+      L[tri(i, j)] = m;
+    }
   double y[N];
 #pragma unroll
   for (int i = 0; i < N; ++i)
-    y[i] = held[i] ? 0.0 : (double)scr[(int64_t)((N * (N + 1) / 2) + i) * ns] * sc[i];
+    y[i] = held[i] ? 0.0 : (double)(scr[(int64_t)((N * (N + 1) / 2) + i) * ns] * pw[i]);
   double ri[N];
   if (cholesky9<N>(L, ri)) {
     chol_solve9<N>(L, ri, y);
-  } else {
-    // rebuild the scaled matrix (the factorisation overwrote it)
-    scaled_system<N>(scr, ns, free_mask, eps, L, sc, held);
-    double b[N];
 #pragma unroll
-    for (int i = 0; i < N; ++i) b[i] = y[i];
-    jacobi_pinv<N>(L, b, y, nullptr);
+    for (int i = 0; i < N; ++i) delta[i] = held[i] ? 0.0 : y[i] * pow2d(-ex[i]);
+    return;
   }
+  // numerically singular: unit-diagonal Jacobi scaling, truncated
+  // eigen-decomposition
+  double sc[N], b[N];
+  scaled_system<N>(scr, ns, free_mask, eps, L, sc, held);
+#pragma unroll
+  for (int i = 0; i < N; ++i)
+    b[i] = held[i] ? 0.0 : (double)scr[(int64_t)((N * (N + 1) / 2) + i) * ns] * sc[i];
+  jacobi_pinv<N>(L, b, y, nullptr);
 #pragma unroll
   for (int i = 0; i < N; ++i) delta[i] = held[i] ? 0.0 : sc[i] * y[i];
 }
