@@ -302,8 +302,8 @@ def run_ours(args, rank, world):
     out_m, out_p = outputs(True), outputs(False)
     # launch-shape autotuner on a sample of the map
     ns = min(npix, 1 << 18)
-    best_block, tune_ms = v.vfisv_autotune(h, obs[:ns], wts[:ns], tf, tx, line,
-                                           config=cfg_plain, stream=stream)
+    best_block, best_tpp, tune_ms = v.vfisv_autotune(h, obs[:ns], wts[:ns], tf, tx, line,
+                                                     config=cfg_plain, stream=stream)
 
     def step_mixed(out=out_m, cn=cfg_nn, cp=cfg_plain):
         v.vfisv_invert_nn(h, blob, obs, wts, tf, tx, line, config_nn=cn, config_plain=cp,
@@ -365,8 +365,8 @@ def run_ours(args, rank, world):
     out_f = outputs(True)
     # its own launch shape (the double-float solve has other register and
     # shared-memory needs), restored for the FP64 configuration afterwards
-    best_block_f, _ = v.vfisv_autotune(h, obs[:ns], wts[:ns], tf, tx, line, config=cfg_plain_f,
-                                       stream=stream)
+    best_block_f, best_tpp_f, _ = v.vfisv_autotune(h, obs[:ns], wts[:ns], tf, tx, line,
+                                                   config=cfg_plain_f, stream=stream)
     step_mixed(out_f, cfg_nn_f, cfg_plain_f)
     v.vfisv_graph_begin(h, stream)
     step_mixed(out_f, cfg_nn_f, cfg_plain_f)
@@ -380,7 +380,7 @@ def run_ours(args, rank, world):
     work_f = v.vfisv_counters(h, stream, reset=True)
     v.vfisv_check(h, stream)
     graph_fast.close()
-    v.vfisv_autotune(h, obs[:ns], wts[:ns], tf, tx, line, config=cfg_plain, stream=stream)
+    v.vfisv_set_launch_shape(h, best_block, best_tpp)
 
     # --- counting: chi2 matched to the same run's plain LM pass
     def matched(o):
@@ -456,8 +456,12 @@ def run_ours(args, rank, world):
         "count": "mixed pixels with status CONVERGED and chi2 <= (1 + 1e-3) x the same pixel's "
                  "chi2 in the same run's plain LM pass, per second of the mixed step "
                  "(STALLED not counted)",
-        "launch": {"cuda_graph": "whole map per step", "lm_pixels_per_cta": best_block,
-                   "autotune_ms_64_128_256": tune_ms},
+        "launch": {"cuda_graph": "whole map per step", "lm_threads_per_cta": best_block,
+                   "lm_threads_per_pixel": best_tpp,
+                   "autotune_ms": {f"{t}x{b}": m for (t, b), m in
+                                   zip([(t, b) for t in (1, 2, 4) for b in (64, 128, 256)],
+                                       tune_ms)},
+                   "autotune_sample_pixels": ns},
         "routing": {"conf_route": conf_route, "calibration": calib},
         "converged_fraction": conv(out_m) / npix,
         "stalled_fraction": stalled(out_m) / npix,
@@ -481,7 +485,8 @@ def run_ours(args, rank, world):
                                "compensated f32 chi2 (no FP64 on the LM path); not the headline",
                        "value": match_f / (ms_fast / 1e3), "unit": "pixels/s",
                        "ms_per_step": ms_fast, "chi2_mixed_le_plain_frac": le_frac_f,
-                       "lm_kernel_ms": ms_lm_fast, "lm_pixels_per_cta": best_block_f,
+                       "lm_kernel_ms": ms_lm_fast, "lm_threads_per_cta": best_block_f,
+                       "lm_threads_per_pixel": best_tpp_f,
                        "lm_roofline_frac": flm_f / (ms_lm_fast / 1e3) / 1e12 / peak},
         "train": {"profiles": TRAIN_N, "epochs": TRAIN_EPOCHS, "batch": TRAIN_BATCH,
                   "seconds_incl_synthesis": train_s, "final_loss": final_loss},

@@ -268,15 +268,30 @@ int vfisv_graph_launch(vfisv_graph* g, void* stream);
 int vfisv_graph_kernels(const vfisv_graph* g, int64_t* count);
 void vfisv_graph_destroy(vfisv_graph* g);
 
-/* Autotuner: time the LM kernel with 64, 128 and 256 pixel slots per CTA on
- * the given sample (arguments as vfisv_invert, no covariance), keep the
- * fastest for this handle's later inversions and return it in best_block
- * (and the times in ms_out[3] if not NULL).  Synchronises `stream`. */
+/* Autotuner for the launch shape of the filter-position LM kernel (the
+ * workload asks for pixels per CTA and threads per pixel to be tuned): time
+ * an inversion of the given sample (arguments as vfisv_invert, no
+ * covariance) with 64, 128 and 256 threads per CTA and 1, 2 and 4 threads
+ * per pixel, keep the fastest shape for this handle's later inversions and
+ * return it in best_block (threads per CTA) and best_tpp (threads per
+ * pixel, may be NULL); ms_out (may be NULL) receives the nine times,
+ * threads-per-pixel-major: ms_out[3 * i + j] for tpp = {1, 2, 4}[i], block =
+ * {64, 128, 256}[j].  With tpp threads per pixel the lanes of a pixel split
+ * its wavelength points: a pass has tpp times as many threads, so small
+ * maps (fewer pixels than resident slots) finish sooner, while the solve
+ * and the normal equations are repeated on every lane of the pixel.
+ * Restarts and a free filling factor always run 128 x 1.  Results do not
+ * depend on the shape beyond FP32 summation order.  Synchronises `stream`. */
 int vfisv_autotune(vfisv_handle* h, const float* obs, const float* weights,
                    int32_t weights_per_pixel, const float* filters, int32_t nfilt,
                    const float* wl_mA, int32_t nlam, const vfisv_line* line,
-                   const vfisv_config* cfg, int64_t npix, int32_t* best_block, float* ms_out,
-                   void* stream);
+                   const vfisv_config* cfg, int64_t npix, int32_t* best_block, int32_t* best_tpp,
+                   float* ms_out, void* stream);
+
+/* Set the launch shape of the handle's filter-position LM kernel directly:
+ * block in {64, 128, 256} threads per CTA, tpp in {1, 2, 4} threads per
+ * pixel (default 128 x 1).  VFISV_E_ARG for any other value. */
+int vfisv_set_launch_shape(vfisv_handle* h, int32_t block, int32_t tpp);
 
 /* Persistent launches of this handle (the LM, wide, covariance and network
  * kernels) use at most `nsm` SMs; 0 (the default) lets them take every SM.

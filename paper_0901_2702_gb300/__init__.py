@@ -21,7 +21,7 @@ __all__ = [
     "vfisv_strerror", "vfisv_config_default", "vfisv_nn_init", "vfisv_nn_train",
     "vfisv_nn_grad", "vfisv_nn_infer", "vfisv_invert_nn", "vfisv_graph_begin", "vfisv_graph_end",
     "vfisv_graph_launch", "vfisv_graph_kernels", "vfisv_graph_destroy", "vfisv_autotune",
-    "vfisv_set_pipeline_chunks", "vfisv_set_sm_limit", "vfisv_voigt",
+    "vfisv_set_pipeline_chunks", "vfisv_set_sm_limit", "vfisv_set_launch_shape", "vfisv_voigt",
     "vfisv_limb_weights", "vfisv_restart_models", "vfisv_init_models", "vfisv_invert_batch",
     "VfisvError",
     "library_path",
@@ -121,8 +121,10 @@ def load():
     lib.vfisv_graph_destroy.restype = None
     lib.vfisv_autotune.argtypes = [P, P, P, I32, P, I32, P, I32, ctypes.POINTER(vfisv_line),
                                    ctypes.POINTER(vfisv_config), I64, ctypes.POINTER(I32),
-                                   P, P]
+                                   ctypes.POINTER(I32), P, P]
     lib.vfisv_autotune.restype = ctypes.c_int
+    lib.vfisv_set_launch_shape.argtypes = [P, I32, I32]
+    lib.vfisv_set_launch_shape.restype = ctypes.c_int
     lib.vfisv_voigt.argtypes = [P, P, P, I64, I32, P, P, P]
     lib.vfisv_voigt.restype = ctypes.c_int
     lib.vfisv_limb_weights.argtypes = [P, P, P, I64, I32, ctypes.c_float, P, P, P]
@@ -482,20 +484,26 @@ def vfisv_graph_destroy(g: Graph) -> None:
 
 
 def vfisv_autotune(h: Handle, obs, weights, filters, wl_mA, line, config=None, stream=None):
-    """Pick the LM kernel's pixel slots per CTA on a sample; returns (best, [ms x 3])."""
+    """Pick the LM kernel's launch shape on a sample; returns (threads per CTA,
+    threads per pixel, [ms x 9] threads-per-pixel-major)."""
     npix = int(obs.shape[0])
     nfilt, nlam = int(filters.shape[0]), int(filters.shape[1])
     per_pixel = 1 if (len(weights.shape) >= 2 and int(weights.shape[0]) == npix) else 0
     cfg = config if isinstance(config, vfisv_config) else vfisv_config_default(**(config or {}))
     ptrs = [_ptr(x, np.float32) for x in (obs, weights, filters, wl_mA)]
-    best = ctypes.c_int32()
-    ms = np.zeros(3, np.float32)
+    best, tpp = ctypes.c_int32(), ctypes.c_int32()
+    ms = np.zeros(9, np.float32)
     ln = _line(line)
     _check(load().vfisv_autotune(h.ptr, ptrs[0][0], ptrs[1][0], per_pixel, ptrs[2][0], nfilt,
                                  ptrs[3][0], nlam, ctypes.byref(ln), ctypes.byref(cfg), npix,
-                                 ctypes.byref(best), ms.ctypes.data,
+                                 ctypes.byref(best), ctypes.byref(tpp), ms.ctypes.data,
                                  ctypes.c_void_p(_stream(obs, stream))), "vfisv_autotune")
-    return int(best.value), ms.tolist()
+    return int(best.value), int(tpp.value), ms.tolist()
+
+
+def vfisv_set_launch_shape(h: Handle, block: int, tpp: int = 1) -> None:
+    """Threads per CTA (64, 128, 256) and per pixel (1, 2, 4) of the LM kernel."""
+    _check(load().vfisv_set_launch_shape(h.ptr, int(block), int(tpp)), "vfisv_set_launch_shape")
 
 
 VOIGT_RATIONAL, VOIGT_TAYLOR1, VOIGT_TAYLOR2 = 0, 1, 2

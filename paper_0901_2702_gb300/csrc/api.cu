@@ -27,7 +27,8 @@ struct vfisv_handle {
   size_t nnws_bytes = 0;
   void* mixws = nullptr;   // mixed inversion: guesses, gathered pixels, 2nd run
   size_t mixws_bytes = 0;
-  int lm_block = 128;      // LM pixel slots per CTA (vfisv_autotune)
+  int lm_block = 128;      // LM threads per CTA (vfisv_autotune)
+  int lm_tpp = 1;          // LM threads per pixel (vfisv_autotune)
   void* vtab = nullptr;    // Taylor table of H, F (built on first use)
   void* geom = nullptr;    // filter centres and wing weights of the weak-field init
   size_t geom_bytes = 0;
@@ -468,11 +469,11 @@ int invert_device(vfisv_handle* h, const DevInvert& d, int nfilt, int nlam,
                   const int64_t* npix_dev, cudaStream_t s) {
   if (nfilt > 8) return invert_device_wide(h, d, nfilt, nlam, line, cfg, npix, npix_dev, s);
   int64_t nslots = 0;
-  int grid = 0, block = h->lm_block;
+  int grid = 0, block = h->lm_block, tpp = h->lm_tpp;
   size_t smem = 0;
   const bool alpha_free = (cfg->free_mask >> 9) & 1u;
   if (invert_slots(nfilt, nlam, npix, cfg->restarts, cfg->fast_solve, alpha_free, &nslots, &grid,
-                   &block, &smem) !=
+                   &block, &tpp, &smem) !=
       cudaSuccess) {
     cudaGetLastError();
     return VFISV_E_CUDA;
@@ -538,7 +539,7 @@ int invert_device(vfisv_handle* h, const DevInvert& d, int nfilt, int nlam,
   a.rs_state = cfg->restarts ? ws + L.rs : nullptr;
   a.pix_list = d.pix_list;
   a.counters = h->counters;
-  if (launch_invert(a, nfilt, grid, block, smem, s) != cudaSuccess) return VFISV_E_CUDA;
+  if (launch_invert(a, nfilt, grid, block, tpp, smem, s) != cudaSuccess) return VFISV_E_CUDA;
   // with a pixel list the listed pixels lie anywhere in [0, npix): the
   // covariance kernel sweeps the whole map (it skips rows by status)
   if (d.cov && launch_covariance(d.cov, d.status, npix, d.pix_list ? nullptr : npix_dev,
@@ -733,8 +734,8 @@ int vfisv_set_pipeline_chunks(vfisv_handle* h, int32_t chunks) {
 int vfisv_autotune(vfisv_handle* h, const float* obs, const float* weights,
                    int32_t weights_per_pixel, const float* filters, int32_t nfilt,
                    const float* wl_mA, int32_t nlam, const vfisv_line* line,
-                   const vfisv_config* cfg, int64_t npix, int32_t* best_block, float* ms_out,
-                   void* stream) {
+                   const vfisv_config* cfg, int64_t npix, int32_t* best_block, int32_t* best_tpp,
+                   float* ms_out, void* stream) {
   if (!h || !best_block || h->capturing) return VFISV_E_ARG;
   if (npix < 1) return VFISV_E_SIZE;
   if (set_device(h)) return VFISV_E_CUDA;
@@ -751,14 +752,16 @@ int vfisv_autotune(vfisv_handle* h, const float* obs, const float* weights,
   int rc = grow(&h->mixws, &h->mixws_bytes, off);
   if (rc) return rc;
   char* mw = (char*)h->mixws;
-  const int cand[3] = {64, 128, 256};
+  // threads per CTA x threads per pixel, threads-per-pixel-major
+  const int cand_b[3] = {64, 128, 256}, cand_t[3] = {1, 2, 4};
   float best = 0.0f;
-  int best_b = 128;
+  int best_b = 128, best_t = 1;
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  for (int c = 0; c < 3; ++c) {
-    h->lm_block = cand[c];
+  for (int c = 0; c < 9; ++c) {
+    h->lm_block = cand_b[c % 3];
+    h->lm_tpp = cand_t[c / 3];
     float ms = 0.0f;
     for (int rep = 0; rep < 2; ++rep) {  // the first run warms up
       cudaEventRecord(e0, s);
@@ -774,14 +777,25 @@ int vfisv_autotune(vfisv_handle* h, const float* obs, const float* weights,
     if (ms_out) ms_out[c] = ms;
     if (c == 0 || ms < best) {
       best = ms;
-      best_b = cand[c];
+      best_b = cand_b[c % 3];
+      best_t = cand_t[c / 3];
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   h->lm_block = best_b;
+  h->lm_tpp = best_t;
   *best_block = best_b;
+  if (best_tpp) *best_tpp = best_t;
   return rc;
+}
+
+int vfisv_set_launch_shape(vfisv_handle* h, int32_t block, int32_t tpp) {
+  if (!h || !(block == 64 || block == 128 || block == 256) || !(tpp == 1 || tpp == 2 || tpp == 4))
+    return VFISV_E_ARG;
+  h->lm_block = block;
+  h->lm_tpp = tpp;
+  return VFISV_OK;
 }
 
 int vfisv_voigt(vfisv_handle* h, const float* a, const float* u, int64_t n, int32_t method,

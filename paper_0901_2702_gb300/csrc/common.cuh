@@ -221,11 +221,14 @@ constexpr int kRestartAtConvergence = 1, kRestartA = 2, kRestartB = 4;
 cudaError_t launch_pack_table(const float* filters, int nf, const float* wl, int nlam,
                               float* table, cudaStream_t s);
 cudaError_t launch_synth(const SynthArgs& a, int nf, cudaStream_t s);
-// Persistent LM kernel: launch shape for `npix` pixels with *block pixel
-// slots per CTA (64, 128 or 256; anything else selects 128 and is written
-// back), and the number of resident slots (the scratch it needs).
+// Persistent LM kernel: launch shape for `npix` pixels with *block threads
+// per CTA (64, 128 or 256; anything else selects 128) and *tpp threads per
+// pixel (1, 2 or 4; anything else selects 1), both written back as used
+// (restarts and a free filling factor take 128 x 1), and the number of
+// resident pixel slots (the scratch it needs): grid x block / tpp.
 cudaError_t invert_slots(int nf, int nlam, int64_t npix, int restarts, int fast_solve,
-                         int alpha_free, int64_t* nslots, int* grid, int* block, size_t* smem);
+                         int alpha_free, int64_t* nslots, int* grid, int* block, int* tpp,
+                         size_t* smem);
 cudaError_t launch_restart_perturb(const float* in, int64_t n, int64_t pix0, int k,
                                    uint32_t free_mask, uint64_t seed, float* out, cudaStream_t s);
 // Upload the Weideman coefficients to the LM kernel's constant bank on the
@@ -234,7 +237,7 @@ cudaError_t invert_set_constants(const Weideman& W);
 cudaError_t launch_covariance(float* cov, const int32_t* status, int64_t npix,
                               const int64_t* npix_dev, uint32_t free_mask, int fast_solve,
                               cudaStream_t s);
-cudaError_t launch_invert(const InvertArgs& a, int nf, int grid, int block, size_t smem,
+cudaError_t launch_invert(const InvertArgs& a, int nf, int grid, int block, int tpp, size_t smem,
                           cudaStream_t s);
 
 // voigt.cu: bulk Voigt/Faraday-Voigt evaluation and the Taylor table.

@@ -302,8 +302,12 @@ __device__ __forceinline__ void pool_release(int* owner, int b) {
 
 // The fused pass over the wavelength grid, kept out of line so that its
 // 168 accumulators get the whole register file; results go to the lane's
-// column of a pooled dump buffer, whose index it returns.
-template <int NF, bool NM = false>
+// column of a pooled dump buffer, whose index it returns.  With TPP > 1 the
+// TPP consecutive lanes of a pixel each take every TPP-th grid point and
+// then add their partial sums by xor-shuffles: every lane of the pixel ends
+// with the same sums (IEEE addition is commutative, and the pairs are added
+// in the same tree on every lane).
+template <int NF, bool NM = false, int TPP = 1>
 __device__ __noinline__ int fused_pass(const PixK P, const float* __restrict__ tab, int nlam,
                                        float* __restrict__ pool, int* owner, int npool,
                                        int* err) {
@@ -323,10 +327,22 @@ __device__ __noinline__ int fused_pass(const PixK P, const float* __restrict__ t
     for (int k = 0; k < NF; ++k) accn[r][k] = 0.0f;
   const int nl = table_rows(tab, NF, nlam);
 #pragma unroll 1
-  for (int i = 0; i < nl; ++i) {
+  for (int i = (TPP > 1) ? (int)(threadIdx.x % TPP) : 0; i < nl; i += TPP) {
     float T[NF];
     const float x = load_row<NF>(tab + (size_t)i * S, T);
     lambda_step<NF, true, NM>(c_W, P, x, T, acc, accn);
+  }
+  if constexpr (TPP > 1) {
+    const int lane = threadIdx.x & 31;
+    const unsigned pm = ((1u << TPP) - 1u) << (lane & ~(TPP - 1));
+#pragma unroll
+    for (int o = 1; o < TPP; o <<= 1)
+#pragma unroll
+      for (int r = 0; r < kRows; ++r)
+#pragma unroll
+        for (int s = 0; s < 4; ++s)
+#pragma unroll
+          for (int k = 0; k < NF; ++k) acc[r][s][k] += __shfl_xor_sync(pm, acc[r][s][k], o);
   }
   const int b = pool_acquire(owner, npool, err);
   float* dump = pool + (size_t)b * NACC * 32 + (threadIdx.x & 31);
@@ -356,8 +372,9 @@ constexpr int kNumCounters = 4;
 __host__ __device__ constexpr size_t pool_owner_bytes(int nt) {
   return ((size_t)dump_pool(nt) * 4 + 15) & ~(size_t)15;
 }
-__host__ __device__ constexpr size_t invert_smem_bytes(int tabf, int nacc, int nt) {
-  return (size_t)tabf * 4 + (size_t)dump_pool(nt) * nacc * 32 * 4 + (size_t)kStateWords * nt * 4 +
+// nt threads per CTA serving nps pixel slots (nt / threads per pixel)
+__host__ __device__ constexpr size_t invert_smem_bytes(int tabf, int nacc, int nt, int nps) {
+  return (size_t)tabf * 4 + (size_t)dump_pool(nt) * nacc * 32 * 4 + (size_t)kStateWords * nps * 4 +
          pool_owner_bytes(nt) + 8 * kNumCounters + 16;
 }
 
@@ -365,9 +382,14 @@ __host__ __device__ constexpr size_t invert_smem_bytes(int tabf, int nacc, int n
 // solve in double-float and chi2 by a compensated FP32 sum (fast_solve);
 // otherwise both in FP64.  AF: the filling factor alpha free (Sec. 2): the
 // model mixes the magnetic and the non-magnetic (B = 0) profile, and the
-// solve takes 10 parameters.
-template <int NF, int BS, bool RS, bool DF, bool AF = false>
+// solve takes 10 parameters.  TPP: threads per pixel (1, 2 or 4): the lanes
+// of a pixel split its wavelength points and otherwise run the same steps
+// on the same data (every decision, and every value they write, is the
+// same on each of them); a CTA of BS threads serves BS / TPP pixel slots.
+template <int NF, int BS, bool RS, bool DF, bool AF = false, int TPP = 1>
 __global__ void __launch_bounds__(BS, 1) invert_kernel(InvertArgs A) {
+  static_assert(TPP == 1 || TPP == 2 || TPP == 4, "threads per pixel");
+  static_assert(TPP == 1 || (!RS && !AF), "several threads per pixel: plain path only");
   constexpr int NOBS = 4 * NF;
   constexpr int NACC = kRows * 4 * NF + (AF ? kNmRows * NF : 0);
   constexpr int NP = AF ? 10 : kNP;        // parameters in the solve
@@ -376,17 +398,19 @@ __global__ void __launch_bounds__(BS, 1) invert_kernel(InvertArgs A) {
   const int S = table_stride(NF);
   const int tabf = table_floats(NF, A.nlam);
   const int tid = threadIdx.x, nt = blockDim.x;
+  const int nps = nt / TPP, ps = tid / TPP, q = tid % TPP;  // pixel slots, this slot, lane in it
   float* tab = smem;
   const int npool = dump_pool(nt);
   float* pool = smem + tabf;                      // [npool][NACC][32]
-  float* sM = pool + (size_t)npool * NACC * 32;   // [10][nt] best model
-  float* sMt = sM + 10 * nt;                      // [10][nt] trial model
-  double* sChi = reinterpret_cast<double*>(sMt + 10 * nt);  // [nt]
-  double* sEps = sChi + nt;                       // [nt]
-  long long* sPix = reinterpret_cast<long long*>(sEps + nt);  // [nt]
-  int* sIt = reinterpret_cast<int*>(sPix + nt);   // [nt]
-  int* sNear = sIt + nt;  // [nt] last accepted step was close to the minimum (Hessian reuse)
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + (invert_smem_bytes(tabf, NACC, nt) - 16) / 4);
+  float* sM = pool + (size_t)npool * NACC * 32;   // [10][nps] best model
+  float* sMt = sM + 10 * nps;                     // [10][nps] trial model
+  double* sChi = reinterpret_cast<double*>(sMt + 10 * nps);  // [nps]
+  double* sEps = sChi + nps;                      // [nps]
+  long long* sPix = reinterpret_cast<long long*>(sEps + nps);  // [nps]
+  int* sIt = reinterpret_cast<int*>(sPix + nps);  // [nps]
+  int* sNear = sIt + nps;  // [nps] last accepted step was close to the minimum (Hessian reuse)
+  uint64_t* mbar =
+      reinterpret_cast<uint64_t*>(smem + (invert_smem_bytes(tabf, NACC, nt, nps) - 16) / 4);
   // passes, accepted, retired, wavelength points evaluated
   unsigned long long* cnt = reinterpret_cast<unsigned long long*>(mbar) - kNumCounters;
   int* owner = reinterpret_cast<int*>(cnt) - pool_owner_bytes(nt) / 4;  // [npool]
@@ -395,12 +419,12 @@ __global__ void __launch_bounds__(BS, 1) invert_kernel(InvertArgs A) {
   if (!tma_load_table(tab, A.table, (uint32_t)(tabf * sizeof(float)), mbar, A.err)) return;
   const float* tau = tab + (size_t)A.nlam * S;
   const int nrows = table_rows(tab, NF, A.nlam);
-  const int64_t slot = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t slot = (int64_t)blockIdx.x * nps + ps;
   const int64_t ns = A.nslots;
   float* scr = A.scratch + slot;
   const int dof = NOBS - A.nfree;
   const int64_t npix = A.npix_dev ? *A.npix_dev : A.npix;
-#define ST(arr, j) arr[(j) * nt + tid]
+#define ST(arr, j) arr[(j) * nps + ps]
   // restart state of this slot: best chi2, initial chi2; best J^T W J, J^T W r,
   // model; failed trials in a row, restart count, flags
   const RestartState R0(A.rs_state, ns);
@@ -412,17 +436,25 @@ __global__ void __launch_bounds__(BS, 1) invert_kernel(InvertArgs A) {
   int* rsFlags = R0.i + 2 * ns + slot;
   constexpr int kEverConv = 1, kEverStall = 2, kPending = 4;
 
-  sPix[tid] = -1;
+  sPix[ps] = -1;
+  // lanes of one pixel (TPP > 1): they run the same steps on the same data,
+  // but independent thread scheduling may let one run ahead of the other;
+  // the slot's shared state is written only after both have read it (a
+  // barrier of the pixel's lanes at the top of every iteration, and the
+  // reads of the post-pass state taken into registers before a second one)
+  const unsigned pm = (TPP > 1) ? (((1u << TPP) - 1u) << ((tid & 31) & ~(TPP - 1))) : 0u;
   while (true) {
     bool fresh = false, restart = false;
+    if constexpr (TPP > 1) __syncwarp(pm);
     {
-      long long pix = sPix[tid];
+      long long pix = sPix[ps];
       if (pix < 0) {
-        pix = (long long)atomicAdd(A.queue, 1ull);
+        if (q == 0) pix = (long long)atomicAdd(A.queue, 1ull);
+        if constexpr (TPP > 1) pix = __shfl_sync(pm, pix, (tid & 31) & ~(TPP - 1));
         if (pix >= npix) break;
         if (A.pix_list) pix = A.pix_list[pix];
         fresh = true;
-        sPix[tid] = pix;
+        sPix[ps] = pix;
         const float* o = A.obs + pix * NOBS;
         const float* wv = weight_row(A, pix, NOBS);
         bool bad = false;
@@ -460,15 +492,15 @@ __global__ void __launch_bounds__(BS, 1) invert_kernel(InvertArgs A) {
           A.status_out[pix] = VFISV_PIX_BAD_INPUT;
           if (A.cov_out)
             for (int j = 0; j < 100; ++j) A.cov_out[pix * 100 + j] = 0.0f;
-          map_retired(A, pix);
-          sPix[tid] = -1;
+          if (q == 0) map_retired(A, pix);
+          sPix[ps] = -1;
           continue;
         }
 #pragma unroll
         for (int j = 0; j < 10; ++j) ST(sMt, j) = Mt[j];
-        sIt[tid] = 0;
-        sEps[tid] = A.eps0;
-        sNear[tid] = 0;
+        sIt[ps] = 0;
+        sEps[ps] = A.eps0;
+        sNear[ps] = 0;
         if (RS) {
           *rsBest = INFINITY;
           *rsFail = 0;
@@ -489,7 +521,7 @@ __global__ void __launch_bounds__(BS, 1) invert_kernel(InvertArgs A) {
         float Mt[10];
         if constexpr (DF) {
           dfl d[kNP];
-          damped_step_df(scr, ns, A.free_mask, sEps[tid], d);
+          damped_step_df(scr, ns, A.free_mask, sEps[ps], d);
 #pragma unroll
           for (int j = 0; j < kNP; ++j) {
             const dfl t = two_sum(ST(sM, j), d[j].hi);
@@ -497,7 +529,7 @@ __global__ void __launch_bounds__(BS, 1) invert_kernel(InvertArgs A) {
           }
         } else {
           double d[NP];
-          damped_step_fp64<NP>(scr, ns, A.free_mask, sEps[tid], d);
+          damped_step_fp64<NP>(scr, ns, A.free_mask, sEps[ps], d);
 #pragma unroll
           for (int j = 0; j < NP; ++j) Mt[j] = (float)((double)ST(sM, j) + d[j]);
         }
@@ -512,7 +544,7 @@ __global__ void __launch_bounds__(BS, 1) invert_kernel(InvertArgs A) {
     }
 
     // ---- fused synthesis + Jacobian at the trial model (Secs. 3 and 4.4) ----
-    const int dbuf = fused_pass<NF, AF>(make_pixk(A.lk, ST(sMt, 0), ST(sMt, 1), ST(sMt, 3),
+    const int dbuf = fused_pass<NF, AF, TPP>(make_pixk(A.lk, ST(sMt, 0), ST(sMt, 1), ST(sMt, 3),
                                                   ST(sMt, 4), ST(sMt, 5), ST(sMt, 6)),
                                         tab, A.nlam, pool, owner, npool, A.err);
     const float* dump = pool + (size_t)dbuf * NACC * 32 + (tid & 31);
@@ -521,9 +553,14 @@ __global__ void __launch_bounds__(BS, 1) invert_kernel(InvertArgs A) {
     auto N = [&](int r, int k) { return dump[(kRows * 4 * NF + r * NF + k) * 32]; };
     const float alf = AF ? ST(sMt, 9) : 1.0f;
 
-    const long long pix = sPix[tid];
+    const long long pix = sPix[ps];
     const float* o = A.obs + pix * NOBS;
     const float* wv = weight_row(A, pix, NOBS);
+    // the slot state this iteration updates, read before any lane writes it
+    const int it_in = sIt[ps];
+    const double chi2_in = sChi[ps], eps_in = sEps[ps];
+    const int near_in = sNear[ps];
+    if constexpr (TPP > 1) __syncwarp(pm);
 
     // ---- model, residual and chi-square (Eq. 1, FP64) ----
     float c2p, s2p;
@@ -562,13 +599,13 @@ __global__ void __launch_bounds__(BS, 1) invert_kernel(InvertArgs A) {
       c2 /= (double)dof;
     }
 
-    if (A.counters) {
+    if (A.counters && q == 0) {
       atomicAdd(&cnt[0], 1ull);
       atomicAdd(&cnt[3], (unsigned long long)nrows);
     }
     bool accept, retire = false;
     int status = VFISV_PIX_MAXITER;
-    int it = sIt[tid];
+    int it = it_in;
     double rel_acc = INFINITY;  // relative chi2 decrease of an accepted trial step
     if (fresh) {
       accept = isfinite(c2);
@@ -583,17 +620,17 @@ __global__ void __launch_bounds__(BS, 1) invert_kernel(InvertArgs A) {
       ++it;
       accept = isfinite(c2);
       if (accept) {
-        sEps[tid] = A.eps0;
+        sEps[ps] = A.eps0;
         *rsFail = 0;
         *rsFlags &= ~kPending;
       }
     } else {
       ++it;
-      const double chi2b = sChi[tid];
+      const double chi2b = chi2_in;
       accept = isfinite(c2) && c2 < chi2b;
-      const double eps_used = sEps[tid];
+      const double eps_used = eps_in;
       const double eps = eps_update(eps_used, accept);
-      sEps[tid] = eps;
+      sEps[ps] = eps;
       bool conv = false, stall = false;
       if (accept) {
         const double rel = (chi2b - c2) / chi2b;
@@ -628,14 +665,14 @@ __global__ void __launch_bounds__(BS, 1) invert_kernel(InvertArgs A) {
         *rsFlags = fl;
       }
     }
-    sIt[tid] = it;
-    if (A.counters && accept && !fresh) atomicAdd(&cnt[1], 1ull);
+    sIt[ps] = it;
+    if (A.counters && q == 0 && accept && !fresh) atomicAdd(&cnt[1], 1ull);
 
     if (accept) {
       // ---- J^T W J and J^T W r at the new best model (compensated FP32) ----
 #pragma unroll
       for (int j = 0; j < 10; ++j) ST(sM, j) = ST(sMt, j);
-      sChi[tid] = c2;
+      sChi[ps] = c2;
       Dot2 a[NPK], g[NP];
 #pragma unroll
       for (int i = 0; i < NPK; ++i) a[i] = Dot2{0.0f, 0.0f};
@@ -649,8 +686,8 @@ __global__ void __launch_bounds__(BS, 1) invert_kernel(InvertArgs A) {
       // Hessian reuse (Sec. 4.4): this and the previous accepted step both
       // close to the minimum -> keep J^T W J, rebuild J^T W r only
       const bool near = rel_acc < A.hess_reuse;
-      const bool keepA = near && sNear[tid];
-      sNear[tid] = near;
+      const bool keepA = near && near_in;
+      sNear[ps] = near;
       // Runtime loops over (filter, Stokes) keep this block small: it runs
       // on accepted steps only and must not evict the wavelength loop from
       // the instruction cache.  Observable (s, k) of row r is
@@ -716,7 +753,7 @@ __global__ void __launch_bounds__(BS, 1) invert_kernel(InvertArgs A) {
     if (!retire && it >= A.max_iter) retire = true;  // status stays MAXITER
 
     if (retire) {
-      double chi2b = sChi[tid];
+      double chi2b = accept ? c2 : chi2_in;
       // with restarts the result is the best model of all segments
       const float* src = scr;
       if (status == VFISV_PIX_NAN_STATE) {
@@ -761,9 +798,9 @@ __global__ void __launch_bounds__(BS, 1) invert_kernel(InvertArgs A) {
           }
         }
       }
-      map_retired(A, pix);
-      sPix[tid] = -1;
-      if (A.counters) atomicAdd(&cnt[2], 1ull);
+      if (q == 0) map_retired(A, pix);
+      sPix[ps] = -1;
+      if (A.counters && q == 0) atomicAdd(&cnt[2], 1ull);
     }
   }
 #undef ST
@@ -845,11 +882,12 @@ cudaError_t launch_covariance(float* cov, const int32_t* status, int64_t npix,
   return cudaGetLastError();
 }
 
-template <int BS, bool RS, bool DF, bool AF = false>
+template <int BS, bool RS, bool DF, bool AF = false, int TPP = 1>
 static cudaError_t slots_for(int nlam, int64_t npix, int64_t* nslots, int* grid, size_t* smem) {
-  auto kern = invert_kernel<6, BS, RS, DF, AF>;
+  auto kern = invert_kernel<6, BS, RS, DF, AF, TPP>;
+  constexpr int NPS = BS / TPP;  // pixel slots per CTA
   const size_t sm =
-      invert_smem_bytes(table_floats(6, nlam), kRows * 4 * 6 + (AF ? kNmRows * 6 : 0), BS);
+      invert_smem_bytes(table_floats(6, nlam), kRows * 4 * 6 + (AF ? kNmRows * 6 : 0), BS, NPS);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   int dev = 0, nsm = 0, per = 0;
@@ -860,74 +898,101 @@ static cudaError_t slots_for(int nlam, int64_t npix, int64_t* nslots, int* grid,
   if (e != cudaSuccess) return e;
   if (per < 1) return cudaErrorLaunchOutOfResources;
   int64_t g = (int64_t)nsm * per;
-  const int64_t need = (npix + BS - 1) / BS;
+  const int64_t need = (npix + NPS - 1) / NPS;
   if (need < g) g = need;
   if (g < 1) g = 1;
   *grid = (int)g;
   *smem = sm;
-  *nslots = g * BS;
+  *nslots = g * NPS;
   return cudaSuccess;
+}
+
+template <bool DF, int TPP>
+static cudaError_t slots_bs(int bs, int nlam, int64_t npix, int64_t* nslots, int* grid,
+                            size_t* smem) {
+  switch (bs) {
+    case 64: return slots_for<64, false, DF, false, TPP>(nlam, npix, nslots, grid, smem);
+    case 256: return slots_for<256, false, DF, false, TPP>(nlam, npix, nslots, grid, smem);
+    default: return slots_for<128, false, DF, false, TPP>(nlam, npix, nslots, grid, smem);
+  }
 }
 
 template <bool DF>
 static cudaError_t invert_slots_t(int nlam, int64_t npix, int restarts, int64_t* nslots,
-                                  int* grid, int* block, size_t* smem) {
+                                  int* grid, int* block, int* tpp, size_t* smem) {
   if (restarts) {  // compiled for the default slot count only
     *block = kInvThreadsDefault;
+    *tpp = 1;
     return slots_for<kInvThreadsDefault, true, DF>(nlam, npix, nslots, grid, smem);
   }
   const int bs = (*block == 64 || *block == 256) ? *block : kInvThreadsDefault;
+  const int t = (*tpp == 2 || *tpp == 4) ? *tpp : 1;
   *block = bs;
-  switch (bs) {
-    case 64: return slots_for<64, false, DF>(nlam, npix, nslots, grid, smem);
-    case 256: return slots_for<256, false, DF>(nlam, npix, nslots, grid, smem);
-    default: return slots_for<128, false, DF>(nlam, npix, nslots, grid, smem);
+  *tpp = t;
+  switch (t) {
+    case 2: return slots_bs<DF, 2>(bs, nlam, npix, nslots, grid, smem);
+    case 4: return slots_bs<DF, 4>(bs, nlam, npix, nslots, grid, smem);
+    default: return slots_bs<DF, 1>(bs, nlam, npix, nslots, grid, smem);
   }
 }
 
 cudaError_t invert_slots(int nf, int nlam, int64_t npix, int restarts, int fast_solve,
-                         int alpha_free, int64_t* nslots, int* grid, int* block, size_t* smem) {
+                         int alpha_free, int64_t* nslots, int* grid, int* block, int* tpp,
+                         size_t* smem) {
   if (nf != 6) return cudaErrorInvalidValue;
   if (alpha_free) {  // compiled for the default slot count, FP64 solve, no restarts
     if (restarts || fast_solve) return cudaErrorInvalidValue;
     *block = kInvThreadsDefault;
+    *tpp = 1;
     return slots_for<kInvThreadsDefault, false, false, true>(nlam, npix, nslots, grid, smem);
   }
-  return fast_solve ? invert_slots_t<true>(nlam, npix, restarts, nslots, grid, block, smem)
-                    : invert_slots_t<false>(nlam, npix, restarts, nslots, grid, block, smem);
+  return fast_solve ? invert_slots_t<true>(nlam, npix, restarts, nslots, grid, block, tpp, smem)
+                    : invert_slots_t<false>(nlam, npix, restarts, nslots, grid, block, tpp, smem);
 }
 
 cudaError_t invert_set_constants(const Weideman& W) {
   return cudaMemcpyToSymbol(c_W, &W, sizeof(W));
 }
 
-template <bool DF>
-static cudaError_t launch_invert_t(const InvertArgs& a, int grid, int block, size_t smem,
-                                   cudaStream_t s) {
-  if (a.restarts) {
-    if (block != kInvThreadsDefault || !a.rs_state) return cudaErrorInvalidValue;
-    invert_kernel<6, kInvThreadsDefault, true, DF><<<grid, block, smem, s>>>(a);
-    return cudaGetLastError();
-  }
+template <bool DF, int TPP>
+static cudaError_t launch_bs(const InvertArgs& a, int grid, int block, size_t smem,
+                             cudaStream_t s) {
   switch (block) {
-    case 64: invert_kernel<6, 64, false, DF><<<grid, 64, smem, s>>>(a); break;
-    case 256: invert_kernel<6, 256, false, DF><<<grid, 256, smem, s>>>(a); break;
-    case 128: invert_kernel<6, 128, false, DF><<<grid, 128, smem, s>>>(a); break;
+    case 64: invert_kernel<6, 64, false, DF, false, TPP><<<grid, 64, smem, s>>>(a); break;
+    case 256: invert_kernel<6, 256, false, DF, false, TPP><<<grid, 256, smem, s>>>(a); break;
+    case 128: invert_kernel<6, 128, false, DF, false, TPP><<<grid, 128, smem, s>>>(a); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
 }
 
-cudaError_t launch_invert(const InvertArgs& a, int nf, int grid, int block, size_t smem,
+template <bool DF>
+static cudaError_t launch_invert_t(const InvertArgs& a, int grid, int block, int tpp,
+                                   size_t smem, cudaStream_t s) {
+  if (a.restarts) {
+    if (block != kInvThreadsDefault || tpp != 1 || !a.rs_state) return cudaErrorInvalidValue;
+    invert_kernel<6, kInvThreadsDefault, true, DF><<<grid, block, smem, s>>>(a);
+    return cudaGetLastError();
+  }
+  switch (tpp) {
+    case 1: return launch_bs<DF, 1>(a, grid, block, smem, s);
+    case 2: return launch_bs<DF, 2>(a, grid, block, smem, s);
+    case 4: return launch_bs<DF, 4>(a, grid, block, smem, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_invert(const InvertArgs& a, int nf, int grid, int block, int tpp, size_t smem,
                           cudaStream_t s) {
   if (nf != 6) return cudaErrorInvalidValue;
   if (a.free_mask & (1u << 9)) {
-    if (a.restarts || a.fast_solve || block != kInvThreadsDefault) return cudaErrorInvalidValue;
+    if (a.restarts || a.fast_solve || block != kInvThreadsDefault || tpp != 1)
+      return cudaErrorInvalidValue;
     invert_kernel<6, kInvThreadsDefault, false, false, true><<<grid, block, smem, s>>>(a);
     return cudaGetLastError();
   }
-  return a.fast_solve ? launch_invert_t<true>(a, grid, block, smem, s)
-                      : launch_invert_t<false>(a, grid, block, smem, s);
+  return a.fast_solve ? launch_invert_t<true>(a, grid, block, tpp, smem, s)
+                      : launch_invert_t<false>(a, grid, block, tpp, smem, s);
 }
 
 }  // namespace vfisv

@@ -126,9 +126,10 @@ extern "C" int vfisv_invert_noalloc(const float* obs, const float* weights,
   NoSmLimit all_sms;
 
   int64_t nslots = 0;
-  int grid = 0, block = 128;
+  int grid = 0, block = 128, tpp = 1;
   size_t smem = 0;
-  if (invert_slots(nfilt, nlam, npix, 0, cfg->fast_solve, 0, &nslots, &grid, &block, &smem) !=
+  if (invert_slots(nfilt, nlam, npix, 0, cfg->fast_solve, 0, &nslots, &grid, &block, &tpp,
+                   &smem) !=
       cudaSuccess) {
     cudaGetLastError();
     return VFISV_E_CUDA;
@@ -175,7 +176,7 @@ extern "C" int vfisv_invert_noalloc(const float* obs, const float* weights,
   a.eps0 = cfg->eps0;
   a.hess_reuse = cfg->hess_reuse;
   a.fast_solve = cfg->fast_solve;
-  if (launch_invert(a, nfilt, grid, block, smem, s) != cudaSuccess) return VFISV_E_CUDA;
+  if (launch_invert(a, nfilt, grid, block, tpp, smem, s) != cudaSuccess) return VFISV_E_CUDA;
   if (cov_out &&
       launch_covariance(cov_out, status_out, npix, nullptr, cfg->free_mask, cfg->fast_solve, s) !=
           cudaSuccess)

@@ -7,6 +7,7 @@ synthesised by the library itself.  Prints one JSON line with the time of
 the timed inversion (CUDA events, after --warmup untimed ones).
 
     python -m paper_0901_2702_gb300.lm_bench --npix 262144 --no-cov [--fast-solve] [--autotune]
+    python -m paper_0901_2702_gb300.lm_bench --npix 16384 --no-cov --tpp 2 --block 128
     python -m paper_0901_2702_gb300.lm_bench --npix 16384 --no-cov --spectrograph
 """
 from __future__ import annotations
@@ -30,6 +31,8 @@ def main():
     ap.add_argument("--fast-solve", action="store_true", help="double-float solve (fast_solve=1)")
     ap.add_argument("--autotune", action="store_true",
                     help="pick the pixel slots per CTA with vfisv_autotune first (as bench.py)")
+    ap.add_argument("--tpp", type=int, default=0, help="threads per pixel (with --block)")
+    ap.add_argument("--block", type=int, default=128, help="threads per CTA (with --tpp)")
     ap.add_argument("--spectrograph", action="store_true",
                     help="spectrograph-shaped inputs (112 samples x 4 Stokes, Fe I 6302.5 A)")
     args = ap.parse_args()
@@ -59,9 +62,12 @@ def main():
     obs = (syn + sig * t32(W.noise(n, nobs, args.seed))).contiguous()
     w = (1.0 / (sig * sig)).expand(n, nobs).contiguous()
     cfg = {"max_iter": args.max_iter, "fast_solve": int(args.fast_solve)}
-    block = None
+    block = tpp = None
+    if args.tpp:
+        v.vfisv_set_launch_shape(h, args.block, args.tpp)
+        block, tpp = args.block, args.tpp
     if args.autotune:
-        block, _ = v.vfisv_autotune(h, obs, w, tf, tx, line, config=cfg)
+        block, tpp, _ = v.vfisv_autotune(h, obs, w, tf, tx, line, config=cfg)
     for _ in range(args.warmup):
         v.vfisv_invert(h, obs, w, tf, tx, line, config=cfg, want_cov=not args.no_cov)
     torch.cuda.synchronize()
@@ -75,7 +81,7 @@ def main():
     st = r["status"]
     print(json.dumps({"npix": n, "ms": e0.elapsed_time(e1), "cov": not args.no_cov,
                       "fast_solve": bool(args.fast_solve), "spectrograph": args.spectrograph,
-                      "lm_pixels_per_cta": block,
+                      "lm_threads_per_cta": block, "lm_threads_per_pixel": tpp,
                       "mean_iters": r["iters"].float().mean().item(),
                       "passes": int(r["iters"].sum().item()) + n,
                       "converged": ((st == 0) | (st == 2)).float().mean().item()}))

@@ -73,10 +73,26 @@ def test_autotune_picks_a_shape_and_keeps_results(vf):
     v, h, torch = vf
     dev = torch.device("cuda:0")
     obs, w, tf, tx = _map(v, h, torch, 30000, 64, dev)
+    v.vfisv_set_launch_shape(h, 128, 1)
     base = v.vfisv_invert(h, obs, w, tf, tx, LINE)
-    best, ms = v.vfisv_autotune(h, obs, w, tf, tx, LINE)
-    assert best in (64, 128, 256) and all(m > 0 for m in ms)
+    best, tpp, ms = v.vfisv_autotune(h, obs, w, tf, tx, LINE)
+    assert best in (64, 128, 256) and tpp in (1, 2, 4)
+    assert len(ms) == 9 and all(m > 0 for m in ms)
+    assert ms[3 * (1, 2, 4).index(tpp) + (64, 128, 256).index(best)] == min(ms)
     tuned = v.vfisv_invert(h, obs, w, tf, tx, LINE)
     v.vfisv_check(h)
-    for k in base:
-        assert torch.equal(base[k], tuned[k]), k
+    if tpp == 1:
+        # the slots per CTA change the order pixels are drawn, not their results
+        for k in base:
+            assert torch.equal(base[k], tuned[k]), k
+    else:
+        # the wavelength sums are split across the lanes of a pixel: rounding
+        # differs, trajectories part only at near ties
+        assert (base["status"] == tuned["status"]).float().mean().item() >= 0.97
+        rel = (base["chi2"] / tuned["chi2"] - 1).abs()
+        assert (rel <= 1e-3).float().mean().item() >= 0.97
+    v.vfisv_set_launch_shape(h, 128, 1)
+    with pytest.raises(v.VfisvError):
+        v.vfisv_set_launch_shape(h, 96, 1)
+    with pytest.raises(v.VfisvError):
+        v.vfisv_set_launch_shape(h, 128, 3)

@@ -219,3 +219,28 @@ def test_work_counters(vf):
     o = lm.invert(obs, w, f32(T), f32(X), LINE)
     assert abs(c["accepted"] / o["accepted"].sum() - 1) < 0.03, (c, o["accepted"].sum())
     assert v.vfisv_counters(h)["passes"] == 0  # reset
+
+
+@pytest.mark.parametrize("tpp,block", [(2, 64), (2, 256), (4, 128)])
+def test_threads_per_pixel_parity(vf, tpp, block):
+    """Several threads per pixel (the lanes of a pixel split its wavelength
+    points and add their sums by shuffles) meet the same parity criteria
+    against the oracle as one thread per pixel, on 1000 pixels of the small
+    workload; the work counters still count each pixel once."""
+    v, h, torch = vf
+    p, obs, w = _case(1000, W.SEEDS["small"])
+    v.vfisv_set_launch_shape(h, block, tpp)
+    try:
+        v.vfisv_counters(h, reset=True)
+        g = _gpu(v, h, torch, obs, w)
+        c_ = v.vfisv_counters(h, reset=True)
+    finally:
+        v.vfisv_set_launch_shape(h, 128, 1)
+    assert c_["retired"] == 1000 and c_["passes"] == int(g["iters"].sum()) + 1000
+    o = lm.invert(obs, w, f32(T), f32(X), LINE)
+    c = _compare(g, o)
+    assert c["both"].mean() > 0.5
+    assert np.mean(c["rel"][c["both"]] <= 1e-3) >= 0.98
+    assert np.mean(c["angles_ok"][c["wd"]]) >= 0.98
+    same = c["both"] & (g["iters"] == o["iters"])
+    assert same.sum() > 100 and np.all(c["rel"][same] <= 1e-3)
