@@ -101,12 +101,12 @@ FLOP_PER_PASS_EXTRA = 60  # model and residual outside the wavelength loop
 FLOP_NORMAL_EQ = 24 * 30 + 24 * (9 + 2 * 54)
 # DRAM bytes (read + write) of one plain-LM launch without covariance (FP64
 # solve, the default), per pixel, from one ncu capture of invert_kernel on
-# 262,144 pixels of the 1024^2 distributions, 64 slots per CTA as autotuned
-# (54.6 MB read + 222.8 MB write; profiles/invert_kernel_traffic.md); scaled
+# 262,144 pixels of the 1024^2 distributions, 64 x 1 threads as autotuned
+# (54.2 MB read + 153.7 MB write; profiles/invert_kernel_262k_px.md); scaled
 # by the pixels of a launch.  Algorithmic: 192 B read (observables, weights)
 # + 52 B written (model, chi2, counts); the extra writes are spilled
 # registers and the FP64 solve's call stack written back from L2.
-TRAFFIC_BYTES_PER_PIXEL = (54_599_680 + 222_795_264) / 262_144
+TRAFFIC_BYTES_PER_PIXEL = (54_240_512 + 153_698_048) / 262_144
 
 
 def fp32_peak_tflops(sm_mhz: float, nsm: int = 152) -> float:
@@ -497,10 +497,10 @@ def run_ours(args, rank, world):
                      "frac": achieved / peak,
                      "traffic": int(TRAFFIC_BYTES_PER_PIXEL * npix),
                      "traffic_note": "dram read+write bytes per launch, scaled by pixels from a "
-                                     "262,144-pixel ncu capture (1,058 B/px; algorithmic 244 "
-                                     "B/px: reads 208 vs 192, writes 850 B/px of which ~800 are "
-                                     "spilled registers and the FP64 solve's call stack written "
-                                     "back from L2; ~5 GB/s over the launch)",
+                                     "262,144-pixel ncu capture (793 B/px; algorithmic 244 "
+                                     "B/px: reads 207 vs 192, writes 586 B/px, mostly spilled "
+                                     "registers and the FP64 solve's call stack written back "
+                                     "from L2; ~6 GB/s over the launch)",
                      "kernel": "invert_kernel<6> (plain LM pass, no covariance)",
                      "kernel_ms": ms_lm,
                      "work": work,

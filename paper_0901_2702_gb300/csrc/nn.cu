@@ -1,7 +1,10 @@
 // Initial-guess network (Sec. 5): a 24-256-256-256-11 multilayer perceptron
 // with GELU activations, trained and evaluated by hand-written BF16
-// tensor-core kernels (mma.sync m16n8k16, FP32 accumulation, operands staged
-// in shared memory by cp.async and fed with ldmatrix).
+// tensor-core kernels with FP32 accumulation: the training products run on
+// tcgen05 (nn_tc.cu), inference in one fused tcgen05 kernel (mlp_tc.cu).
+// This file holds the rest of training: features and targets, the loss and
+// its gradient, bias gradients, the split-K reduction, Adam, weight packing,
+// initialisation and the standardisation statistics, and the host driver.
 //
 // Parameter blob (float32, see vfisv.h): W0[24][256] b0[256] W1[256][256]
 // b1[256] W2[256][256] b2[256] W3[256][11] b3[11] in_mean[24] in_std[24]
@@ -14,201 +17,12 @@
 #include "common.cuh"
 #include "nn.cuh"
 #include "nn_device.cuh"
+#include "nn_tc.cuh"
 
 namespace vfisv {
 namespace nn {
 
 using bf16 = __nv_bfloat16;
-
-__constant__ LayerDim kLayers[4] = {{IN, HID, K0P, HID, OFF_W0, OFF_B0},
-                                    {HID, HID, HID, HID, OFF_W1, OFF_B1},
-                                    {HID, HID, HID, HID, OFF_W2, OFF_B2},
-                                    {HID, OUT, HID, N3P, OFF_W3, OFF_B3}};
-
-// ---------------------------------------------------------------------------
-// small PTX helpers
-
-__device__ __forceinline__ void cp_async16(void* s, const void* g) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(s)), "l"(g) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() {
-  asm volatile("cp.async.commit_group;" ::: "memory");
-}
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
-}
-__device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], const void* p) {
-  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-               : "r"(smem_u32(p)));
-}
-__device__ __forceinline__ void ldsm_x4_t(uint32_t (&r)[4], const void* p) {
-  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-               : "r"(smem_u32(p)));
-}
-__device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], uint32_t b0,
-                                         uint32_t b1) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
-      "{%8,%9}, {%0,%1,%2,%3};"
-      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-
-// ---------------------------------------------------------------------------
-// Tiled GEMM C[M,N] = sum_k A(m,k) B(k,n), BF16 in, FP32 accumulate.
-// A is stored [M][K] (AK = true) or [K][M]; B is stored [N][K] (BKM = true) or
-// [K][N].  M % 128 == 0, N % 64 == 0, K % 32 == 0 (callers pad).  blockIdx.z
-// selects a K chunk of length kchunk (split-K for the weight gradients).
-
-constexpr int BM = 128, BN = 64, BK = 32, GT = 128;
-enum Epi { EPI_HIDDEN = 0, EPI_OUT = 1, EPI_DX_GELU = 2, EPI_PARTIAL = 3 };
-
-struct GemmArgs {
-  const bf16* A;
-  int lda;
-  const bf16* B;
-  int ldb;
-  int M, N, K, kchunk;
-  const float* bias;
-  int n_valid;
-  float* Z;  // HIDDEN: pre-activation; OUT: output; PARTIAL: [split][M][N]
-  int ldz;
-  bf16* H;   // HIDDEN: GELU(Z); DX_GELU: dZ of the layer input
-  int ldh;
-  const float* Zprev;  // DX_GELU: pre-activation of the layer input
-  int ldzp;
-};
-
-template <bool AK, bool BKM, int EPI>
-__global__ void __launch_bounds__(GT) gemm_kernel(GemmArgs g) {
-  constexpr int SA = AK ? BM * (BK + 8) : BK * (BM + 8);
-  constexpr int SB = BKM ? BN * (BK + 8) : BK * (BN + 8);
-  __shared__ __align__(16) bf16 sA[2][SA];
-  __shared__ __align__(16) bf16 sB[2][SB];
-  const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
-  const int kbeg = blockIdx.z * g.kchunk;
-  const int kend = min(g.K, kbeg + g.kchunk);
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int wm = (warp >> 1) * 64, wn = (warp & 1) * 32;
-  float acc[4][4][4];
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-#pragma unroll
-      for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.0f;
-
-  auto load_tile = [&](int st, int k0) {
-    if (AK) {
-      for (int c = tid; c < BM * BK / 8; c += GT) {
-        const int r = c / (BK / 8), cc = (c % (BK / 8)) * 8;
-        cp_async16(&sA[st][r * (BK + 8) + cc], g.A + (size_t)(m0 + r) * g.lda + k0 + cc);
-      }
-    } else {
-      for (int c = tid; c < BK * BM / 8; c += GT) {
-        const int r = c / (BM / 8), cc = (c % (BM / 8)) * 8;
-        cp_async16(&sA[st][r * (BM + 8) + cc], g.A + (size_t)(k0 + r) * g.lda + m0 + cc);
-      }
-    }
-    if (BKM) {
-      for (int c = tid; c < BN * BK / 8; c += GT) {
-        const int r = c / (BK / 8), cc = (c % (BK / 8)) * 8;
-        cp_async16(&sB[st][r * (BK + 8) + cc], g.B + (size_t)(n0 + r) * g.ldb + k0 + cc);
-      }
-    } else {
-      for (int c = tid; c < BK * BN / 8; c += GT) {
-        const int r = c / (BN / 8), cc = (c % (BN / 8)) * 8;
-        cp_async16(&sB[st][r * (BN + 8) + cc], g.B + (size_t)(k0 + r) * g.ldb + n0 + cc);
-      }
-    }
-    cp_async_commit();
-  };
-
-  const int nk = (kend - kbeg) / BK;
-  if (nk > 0) load_tile(0, kbeg);
-  for (int t = 0; t < nk; ++t) {
-    if (t + 1 < nk) {
-      load_tile((t + 1) & 1, kbeg + (t + 1) * BK);
-      cp_async_wait<1>();
-    } else {
-      cp_async_wait<0>();
-    }
-    __syncthreads();
-    const bf16* a = sA[t & 1];
-    const bf16* b = sB[t & 1];
-#pragma unroll
-    for (int kk = 0; kk < BK / 16; ++kk) {
-      uint32_t af[4][4], bfr[4][2];
-      const int j = lane >> 3, r = lane & 7;
-#pragma unroll
-      for (int mi = 0; mi < 4; ++mi) {
-        const int mb = j & 1, kb = j >> 1;
-        if (AK)
-          ldsm_x4(af[mi], a + (wm + mi * 16 + mb * 8 + r) * (BK + 8) + kk * 16 + kb * 8);
-        else
-          ldsm_x4_t(af[mi], a + (kk * 16 + kb * 8 + r) * (BM + 8) + wm + mi * 16 + mb * 8);
-      }
-#pragma unroll
-      for (int np = 0; np < 2; ++np) {
-        const int nb = j >> 1, kb = j & 1;
-        uint32_t q[4];
-        if (BKM)
-          ldsm_x4(q, b + (wn + (2 * np + nb) * 8 + r) * (BK + 8) + kk * 16 + kb * 8);
-        else
-          ldsm_x4_t(q, b + (kk * 16 + kb * 8 + r) * (BN + 8) + wn + (2 * np + nb) * 8);
-        bfr[2 * np][0] = q[0];
-        bfr[2 * np][1] = q[1];
-        bfr[2 * np + 1][0] = q[2];
-        bfr[2 * np + 1][1] = q[3];
-      }
-#pragma unroll
-      for (int mi = 0; mi < 4; ++mi)
-#pragma unroll
-        for (int ni = 0; ni < 4; ++ni) mma_bf16(acc[mi][ni], af[mi], bfr[ni][0], bfr[ni][1]);
-    }
-    __syncthreads();
-  }
-
-  // epilogue: thread holds rows (lane/4, +8) and column pairs ((lane%4)*2)
-#pragma unroll
-  for (int mi = 0; mi < 4; ++mi)
-#pragma unroll
-    for (int ni = 0; ni < 4; ++ni)
-#pragma unroll
-      for (int hh = 0; hh < 2; ++hh) {
-        const int row = m0 + wm + mi * 16 + (lane >> 2) + hh * 8;
-        const int col = n0 + wn + ni * 8 + (lane & 3) * 2;
-        float v0 = acc[mi][ni][2 * hh], v1 = acc[mi][ni][2 * hh + 1];
-        if (EPI == EPI_HIDDEN) {
-          v0 += g.bias[col];
-          v1 += g.bias[col + 1];
-          *reinterpret_cast<float2*>(g.Z + (size_t)row * g.ldz + col) = make_float2(v0, v1);
-          *reinterpret_cast<__nv_bfloat162*>(g.H + (size_t)row * g.ldh + col) =
-              __floats2bfloat162_rn(gelu(v0), gelu(v1));
-        } else if (EPI == EPI_OUT) {
-          v0 += (col < g.n_valid) ? g.bias[col] : 0.0f;
-          v1 += (col + 1 < g.n_valid) ? g.bias[col + 1] : 0.0f;
-          *reinterpret_cast<float2*>(g.Z + (size_t)row * g.ldz + col) = make_float2(v0, v1);
-        } else if (EPI == EPI_DX_GELU) {
-          const float2 zp = *reinterpret_cast<const float2*>(g.Zprev + (size_t)row * g.ldzp + col);
-          *reinterpret_cast<__nv_bfloat162*>(g.H + (size_t)row * g.ldh + col) =
-              __floats2bfloat162_rn(v0 * gelu_grad(zp.x), v1 * gelu_grad(zp.y));
-        } else {
-          float* P = g.Z + (size_t)blockIdx.z * g.M * g.N;
-          *reinterpret_cast<float2*>(P + (size_t)row * g.N + col) = make_float2(v0, v1);
-        }
-      }
-}
-
-template <bool AK, bool BKM, int EPI>
-static cudaError_t gemm(const GemmArgs& g, int splits, cudaStream_t s) {
-  dim3 grid(g.M / BM, g.N / BN, splits);
-  gemm_kernel<AK, BKM, EPI><<<grid, GT, 0, s>>>(g);
-  return cudaGetLastError();
-}
 
 // ---------------------------------------------------------------------------
 // Features, targets, decoding (the network's view of a pixel).
@@ -222,24 +36,50 @@ __device__ __forceinline__ int64_t sample_of(int64_t m, const Perm& p) {
   return (int64_t)((p.mult * (uint64_t)(p.offset + m) + p.add) % (uint64_t)p.n);
 }
 
+// Padded widths of the training operands: the input features (24) fill one
+// 64-column K-chunk; their transposed copy (a weight-gradient operand of N =
+// 32) has 32 rows; the outputs (11) are a 16-column tile, their gradient a
+// 64-column K-chunk.
+constexpr int XK = 64, XT = 32, YN = 16, DYK = 64;
+
+__device__ __forceinline__ void put_bf16(uint8_t* base, size_t off, float v) {
+  *reinterpret_cast<bf16*>(base + off) = __float2bfloat16(v);
+}
+
+// Features of row m (sample perm(m)) into X0 = TL(mpad, 64) and its
+// transpose X0T = TL(32, mpad); rows past `rows` and the padding are zero.
 __global__ void features_kernel(const float* __restrict__ obs, int64_t rows, int64_t mpad,
                                 Perm perm, const float* __restrict__ blob,
-                                bf16* __restrict__ X, float* __restrict__ ic_out) {
+                                uint8_t* __restrict__ X, uint8_t* __restrict__ XTr,
+                                float* __restrict__ ic_out) {
   const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (m >= mpad) return;
-  bf16* x = X + m * K0P;
-  if (m >= rows) {
-    for (int j = 0; j < K0P; ++j) x[j] = __float2bfloat16(0.0f);
-    ic_out[m] = 1.0f;
-    return;
+  float f[XT];
+#pragma unroll
+  for (int j = 0; j < XT; ++j) f[j] = 0.0f;
+  float ic = 1.0f;
+  if (m < rows) {
+    const int64_t s = sample_of(m, perm);
+    const float* o = obs + s * IN;
+    ic = ic_of(o);
+    const float inv = 1.0f / ic;
+#pragma unroll
+    for (int j = 0; j < IN; ++j) f[j] = (o[j] * inv - blob[OFF_INM + j]) / blob[OFF_INS + j];
   }
-  const int64_t s = sample_of(m, perm);
-  const float* o = obs + s * IN;
-  const float ic = ic_of(o);
-  const float inv = 1.0f / ic;
-  for (int j = 0; j < IN; ++j)
-    x[j] = __float2bfloat16((o[j] * inv - blob[OFF_INM + j]) / blob[OFF_INS + j]);
-  for (int j = IN; j < K0P; ++j) x[j] = __float2bfloat16(0.0f);
+  for (int j = 0; j < XK; j += 8) {
+    uint4 pk = make_uint4(0u, 0u, 0u, 0u);
+    if (j < XT) {
+      __nv_bfloat162 t0 = __floats2bfloat162_rn(f[j], f[j + 1]);
+      __nv_bfloat162 t1 = __floats2bfloat162_rn(f[j + 2], f[j + 3]);
+      __nv_bfloat162 t2 = __floats2bfloat162_rn(f[j + 4], f[j + 5]);
+      __nv_bfloat162 t3 = __floats2bfloat162_rn(f[j + 6], f[j + 7]);
+      pk = make_uint4(*reinterpret_cast<uint32_t*>(&t0), *reinterpret_cast<uint32_t*>(&t1),
+                      *reinterpret_cast<uint32_t*>(&t2), *reinterpret_cast<uint32_t*>(&t3));
+    }
+    *reinterpret_cast<uint4*>(X + tl_off(m, j, mpad)) = pk;
+  }
+#pragma unroll
+  for (int j = 0; j < XT; ++j) put_bf16(XTr, tl_off(j, m, XT), f[j]);
   ic_out[m] = ic;
 }
 
@@ -257,21 +97,25 @@ __device__ __forceinline__ void targets(const float* p, float ic, float (&t)[OUT
   t[9] = p[8] / ic;
 }
 
-// Loss of Sec. 5's regression plus the confidence output, and dL/dy.
+// Loss of Sec. 5's regression plus the confidence output, and dL/dy: the
+// outputs Y [mpad][16] (FP32), the gradient into dY = TL(mpad, 64) and
+// dYT = TL(16, mpad) (BF16; zero on padding rows and columns).
 __global__ void loss_kernel(const float* __restrict__ Y, int64_t rows, int64_t mpad, Perm perm,
                             const float* __restrict__ params, const float* __restrict__ ic,
-                            const float* __restrict__ blob, bf16* __restrict__ dY,
-                            float* __restrict__ partial) {
+                            const float* __restrict__ blob, uint8_t* __restrict__ dY,
+                            uint8_t* __restrict__ dYT, float* __restrict__ partial) {
   __shared__ float red[256];
   const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   float l = 0.0f;
   if (m < mpad) {
-    bf16* d = dY + m * N3P;
+    float d[YN];
+#pragma unroll
+    for (int o = 0; o < YN; ++o) d[o] = 0.0f;
     if (m < rows) {
       const int64_t s = sample_of(m, perm);
       float t[OUT - 1];
       targets(params + s * 10, ic[m], t);
-      const float* y = Y + m * N3P;
+      const float* y = Y + m * YN;
       const float invn = 1.0f / (float)rows;
       float e[OUT - 1], mse = 0.0f;
 #pragma unroll
@@ -284,12 +128,23 @@ __global__ void loss_kernel(const float* __restrict__ Y, int64_t rows, int64_t m
       const float ec = y[OUT - 1] - c;
       l = mse * invn / (OUT - 1) + ec * ec * invn;
 #pragma unroll
-      for (int o = 0; o < OUT - 1; ++o) d[o] = __float2bfloat16(2.0f * e[o] * invn / (OUT - 1));
-      d[OUT - 1] = __float2bfloat16(2.0f * ec * invn);
-      for (int o = OUT; o < N3P; ++o) d[o] = __float2bfloat16(0.0f);
-    } else {
-      for (int o = 0; o < N3P; ++o) d[o] = __float2bfloat16(0.0f);
+      for (int o = 0; o < OUT - 1; ++o) d[o] = 2.0f * e[o] * invn / (OUT - 1);
+      d[OUT - 1] = 2.0f * ec * invn;
     }
+    for (int j = 0; j < DYK; j += 8) {
+      uint4 pk = make_uint4(0u, 0u, 0u, 0u);
+      if (j < YN) {
+        __nv_bfloat162 t0 = __floats2bfloat162_rn(d[j], d[j + 1]);
+        __nv_bfloat162 t1 = __floats2bfloat162_rn(d[j + 2], d[j + 3]);
+        __nv_bfloat162 t2 = __floats2bfloat162_rn(d[j + 4], d[j + 5]);
+        __nv_bfloat162 t3 = __floats2bfloat162_rn(d[j + 6], d[j + 7]);
+        pk = make_uint4(*reinterpret_cast<uint32_t*>(&t0), *reinterpret_cast<uint32_t*>(&t1),
+                        *reinterpret_cast<uint32_t*>(&t2), *reinterpret_cast<uint32_t*>(&t3));
+      }
+      *reinterpret_cast<uint4*>(dY + tl_off(m, j, mpad)) = pk;
+    }
+#pragma unroll
+    for (int o = 0; o < YN; ++o) put_bf16(dYT, tl_off(o, m, YN), d[o]);
   }
   red[threadIdx.x] = l;
   __syncthreads();
@@ -300,16 +155,34 @@ __global__ void loss_kernel(const float* __restrict__ Y, int64_t rows, int64_t m
   if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
 }
 
-// Column sums of dZ [M][N] (bias gradients) in row chunks: partial[s][N].
-__global__ void colsum_kernel(const bf16* __restrict__ dZ, int M, int N, int chunk,
+// Bias gradients: row sums of a transposed gradient GT = TL(N, M) (the sum
+// over the batch of each output's gradient) over batch chunks of `chunk`
+// columns (a multiple of 64): partial[s][N].  One warp per 8-row group and
+// chunk: a 64-column block of the group is 1024 contiguous bytes, 64 segments
+// of 16 bytes, segment j holding row j % 8; lane l loads segments l and l + 32
+// (both row l % 8), and lanes of one row combine by xor-shuffles in a fixed
+// order.
+__global__ void rowsum_kernel(const uint8_t* __restrict__ GT, int N, int64_t M, int64_t chunk,
                               float* __restrict__ partial) {
-  const int n = blockIdx.x * blockDim.x + threadIdx.x;
-  if (n >= N) return;
-  const int s = blockIdx.y;
+  const int grp = blockIdx.x, s = blockIdx.y, lane = threadIdx.x;
+  const int64_t m0 = (int64_t)s * chunk, m1 = (m0 + chunk < M) ? m0 + chunk : M;
   float acc = 0.0f;
-  for (int m = s * chunk; m < min(M, (s + 1) * chunk); ++m)
-    acc += __bfloat162float(dZ[(size_t)m * N + n]);
-  partial[(size_t)s * N + n] = acc;
+  for (int64_t c = m0; c < m1; c += 64) {
+    const uint8_t* blk = GT + tl_off((int64_t)grp * 8, (int)c, N);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const uint4 q = *reinterpret_cast<const uint4*>(blk + 16 * (lane + 32 * h));
+      const __nv_bfloat162* e = reinterpret_cast<const __nv_bfloat162*>(&q);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const float2 f = __bfloat1622float2(e[k]);
+        acc += f.x + f.y;
+      }
+    }
+  }
+  acc += __shfl_xor_sync(0xffffffffu, acc, 8);
+  acc += __shfl_xor_sync(0xffffffffu, acc, 16);
+  if (lane < 8) partial[(size_t)s * N + grp * 8 + lane] = acc;
 }
 
 // Sum split-K partials into the gradient blob (fixed order: deterministic).
@@ -370,17 +243,30 @@ __global__ void adam_kernel(float* __restrict__ w, const float* __restrict__ g,
   w[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
 }
 
-// BF16 copies of the weights: Wt [Np][Kp] (forward) and Wn [Kp][Np] (input
-// gradient), zero padded.
+__constant__ LayerDim kLayers[4] = {{IN, HID, K0P, HID, OFF_W0, OFF_B0},
+                                    {HID, HID, HID, HID, OFF_W1, OFF_B1},
+                                    {HID, HID, HID, HID, OFF_W2, OFF_B2},
+                                    {HID, OUT, HID, N3P, OFF_W3, OFF_B3}};
+
+// Tiled (TL) BF16 copies of the weights, zero padded: Wt[l] with element
+// (n, k) = W_l[k][n] (rows = outputs: 256, or 16 for the output layer; K =
+// inputs: 64 for layer 0, else 256), the B operand of the forward products;
+// Wn[l] with element (k, n) = W_l[k][n] (rows = the 256 inputs; K = outputs,
+// 64 for the output layer), the B operand of the input gradients (l >= 1).
 __global__ void pack_kernel(const float* __restrict__ blob, PackedNet P) {
   const int l = blockIdx.y;
   const LayerDim& D = kLayers[l];
-  const int total = D.Kp * D.Np;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
-    const int k = i / D.Np, n = i % D.Np;
+  const int rt = (l == 3) ? YN : HID, kt = (l == 0) ? XK : HID, kn = (l == 3) ? DYK : HID;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < rt * kt; i += gridDim.x * blockDim.x) {
+    const int n = i / kt, k = i % kt;
     const float w = (k < D.K && n < D.N) ? blob[D.offW + (size_t)k * D.N + n] : 0.0f;
-    P.Wn[l][(size_t)k * D.Np + n] = __float2bfloat16(w);
-    P.Wt[l][(size_t)n * D.Kp + k] = __float2bfloat16(w);
+    put_bf16(P.Wt[l], tl_off(n, k, rt), w);
+  }
+  if (l == 0) return;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < HID * kn; i += gridDim.x * blockDim.x) {
+    const int k = i / kn, n = i % kn;
+    const float w = (n < D.N) ? blob[D.offW + (size_t)k * D.N + n] : 0.0f;
+    put_bf16(P.Wn[l], tl_off(k, n, HID), w);
   }
 }
 
@@ -472,10 +358,12 @@ __global__ void stats_final_kernel(const double* __restrict__ part, int nblocks,
 static int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 
 struct Bufs {
-  bf16 *X0, *H[3], *dY, *dZ[2];
+  uint8_t *X0, *X0T, *H[3], *HT[3], *dY, *dYT, *dZ[3], *dZT[3];
   float *Z[3], *Y, *ic, *wpart[4], *bpart[4], *grad, *m, *v, *lossp;
   PackedNet P;
 };
+
+constexpr int kMaxLossBlocks = 4096;  // loss partials (256 rows each)
 
 static Bufs carve(void* ws, int64_t M, size_t* used = nullptr) {
   char* p = (char*)ws;
@@ -486,15 +374,18 @@ static Bufs carve(void* ws, int64_t M, size_t* used = nullptr) {
   };
   Bufs b;
   take(infer_workspace_bytes());  // error word and packed inference weights
-  b.X0 = (bf16*)take((size_t)M * K0P * 2);
+  b.X0 = (uint8_t*)take((size_t)M * XK * 2);
+  b.X0T = (uint8_t*)take((size_t)M * XT * 2);
   for (int i = 0; i < 3; ++i) {
     b.Z[i] = (float*)take((size_t)M * HID * 4);
-    b.H[i] = (bf16*)take((size_t)M * HID * 2);
+    b.H[i] = (uint8_t*)take((size_t)M * HID * 2);
+    b.HT[i] = (uint8_t*)take((size_t)M * HID * 2);
+    b.dZ[i] = (uint8_t*)take((size_t)M * HID * 2);
+    b.dZT[i] = (uint8_t*)take((size_t)M * HID * 2);
   }
-  b.Y = (float*)take((size_t)M * N3P * 4);
-  b.dY = (bf16*)take((size_t)M * N3P * 2);
-  b.dZ[0] = (bf16*)take((size_t)M * HID * 2);
-  b.dZ[1] = (bf16*)take((size_t)M * HID * 2);
+  b.Y = (float*)take((size_t)M * YN * 4);
+  b.dY = (uint8_t*)take((size_t)M * DYK * 2);
+  b.dYT = (uint8_t*)take((size_t)M * YN * 2);
   b.ic = (float*)take((size_t)M * 4);
   for (int l = 0; l < 4; ++l) {
     b.wpart[l] = (float*)take((size_t)kSplits * HID * HID * 4);
@@ -503,10 +394,10 @@ static Bufs carve(void* ws, int64_t M, size_t* used = nullptr) {
   b.grad = (float*)take(NBLOB * 4);
   b.m = (float*)take(NBLOB * 4);
   b.v = (float*)take(NBLOB * 4);
-  b.lossp = (float*)take(4096 * 4);
+  b.lossp = (float*)take(kMaxLossBlocks * 4);
   for (int l = 0; l < 4; ++l) {
-    b.P.Wt[l] = (bf16*)take((size_t)kLayersHost[l].Kp * kLayersHost[l].Np * 2);
-    b.P.Wn[l] = (bf16*)take((size_t)kLayersHost[l].Kp * kLayersHost[l].Np * 2);
+    b.P.Wt[l] = (uint8_t*)take((size_t)(l == 3 ? YN : HID) * (l == 0 ? XK : HID) * 2);
+    b.P.Wn[l] = (uint8_t*)take((size_t)HID * (l == 3 ? DYK : HID) * 2);
   }
   if (used) *used = (size_t)(p - (char*)ws);
   return b;
@@ -514,90 +405,114 @@ static Bufs carve(void* ws, int64_t M, size_t* used = nullptr) {
 
 size_t workspace_bytes(int64_t rows) {
   size_t used = 0;
-  carve(nullptr, round_up(rows, BM), &used);
+  carve(nullptr, padded_rows(rows), &used);
   const size_t stats = infer_workspace_bytes() + (size_t)256 * 2 * (IN + OUT - 1) * sizeof(double);
   return used > stats ? used : stats;
 }
 
-int64_t padded_rows(int64_t n) { return round_up(n > 0 ? n : 1, (int64_t)kSplits * BK); }
+// batch rows padded to the 128-row tiles of the products
+int64_t padded_rows(int64_t n) { return round_up(n > 0 ? n : 1, 128); }
 
 static cudaError_t pack(const float* blob, const PackedNet& P, cudaStream_t s) {
   pack_kernel<<<dim3(64, 4), 256, 0, s>>>(blob, P);
   return cudaGetLastError();
 }
 
+static TcGemmArgs gemm_args(const uint8_t* A, int64_t MA, const uint8_t* B, int64_t NB, int K,
+                            int* err) {
+  TcGemmArgs g{};
+  g.A = A;
+  g.MA = MA;
+  g.B = B;
+  g.NB = NB;
+  g.K = K;
+  g.kchunks_per_split = K / 64;
+  g.err = err;
+  return g;
+}
+
 // Forward pass over M (padded) rows whose features are already in X0.
-static cudaError_t forward(const float* blob, const Bufs& b, int64_t M, cudaStream_t s) {
+static cudaError_t forward(const float* blob, const Bufs& b, int64_t M, int* err, cudaStream_t s) {
   cudaError_t e;
-  const bf16* in = b.X0;
-  int kin = K0P;
+  const uint8_t* in = b.X0;
+  int kin = XK;
+  const int mt = (int)(M / 128);
   for (int l = 0; l < 3; ++l) {
-    GemmArgs g{};
-    g.A = in; g.lda = kin;
-    g.B = b.P.Wt[l]; g.ldb = kin;
-    g.M = (int)M; g.N = HID; g.K = kin; g.kchunk = kin;
+    TcGemmArgs g = gemm_args(in, M, b.P.Wt[l], HID, kin, err);
     g.bias = blob + kLayersHost[l].offB;
-    g.Z = b.Z[l]; g.ldz = HID;
-    g.H = b.H[l]; g.ldh = HID;
-    if ((e = gemm<true, true, EPI_HIDDEN>(g, 1, s)) != cudaSuccess) return e;
+    g.Z = b.Z[l];
+    g.ldz = HID;
+    g.H = b.H[l];
+    g.HT = b.HT[l];
+    if ((e = tc_gemm(g, HID, EPI_HIDDEN, mt, 1, s)) != cudaSuccess) return e;
     in = b.H[l];
     kin = HID;
   }
-  GemmArgs g{};
-  g.A = b.H[2]; g.lda = HID;
-  g.B = b.P.Wt[3]; g.ldb = HID;
-  g.M = (int)M; g.N = N3P; g.K = HID; g.kchunk = HID;
+  TcGemmArgs g = gemm_args(b.H[2], M, b.P.Wt[3], YN, HID, err);
   g.bias = blob + OFF_B3;
   g.n_valid = OUT;
-  g.Z = b.Y; g.ldz = N3P;
-  return gemm<true, true, EPI_OUT>(g, 1, s);
+  g.Z = b.Y;
+  g.ldz = YN;
+  return tc_gemm(g, YN, EPI_OUT, mt, 1, s);
+}
+
+// Split of a batch-long K (M rows, 64 per chunk) over at most kSplits CTAs
+// per tile, every split owning at least one chunk.
+static void batch_split(int64_t M, int* per, int* splits) {
+  const int64_t total = M / 64;
+  const int64_t want = total < kSplits ? total : kSplits;
+  *per = (int)((total + want - 1) / want);
+  *splits = (int)((total + *per - 1) / *per);
 }
 
 // Backward pass for a batch of M rows (dY already written): weight and bias
 // gradients into b.grad, in blob layout.
-static cudaError_t backward(const Bufs& b, int64_t M, float* loss_out, int nloss,
+static cudaError_t backward(const Bufs& b, int64_t M, float* loss_out, int nloss, int* err,
                             cudaStream_t s) {
   cudaError_t e;
-  const int chunk = (int)(M / kSplits);  // M % (kSplits * BK) == 0 by construction
-  const bf16* dOut = b.dY;
-  int nOut = N3P;
+  const int mt = (int)(M / 128);
+  int per = 1, S = 1;
+  batch_split(M, &per, &S);
+  // bias-gradient batch columns per split (whole 64-column blocks)
+  const int64_t bchunk = ((M + kSplits - 1) / kSplits + 63) / 64 * 64;
+  const int SB = (int)((M + bchunk - 1) / bchunk);
+  // input gradient of layer l (l = 3, 2, 1): dZ_{l-1} = (dZ_l W_l^T) * GELU'(Z_{l-1})
+  auto dx = [&](int l, const uint8_t* dOut, int kout, uint8_t* H, uint8_t* HT) {
+    TcGemmArgs g = gemm_args(dOut, M, b.P.Wn[l], HID, kout, err);
+    g.Zprev = b.Z[l - 1];
+    g.ldzp = HID;
+    g.H = H;
+    g.HT = HT;
+    return tc_gemm(g, HID, EPI_DX, mt, 1, s);
+  };
+  // weight gradient: D[256][n] = A^T-rows x B^T-rows over the batch, split-K
+  auto dw = [&](int l, const uint8_t* AT, const uint8_t* BT, int n) {
+    TcGemmArgs g = gemm_args(AT, HID, BT, n, (int)M, err);
+    g.kchunks_per_split = per;
+    g.P = b.wpart[l];
+    return tc_gemm(g, n, EPI_PARTIAL, HID / 128, S, s);
+  };
+  auto bias = [&](int l, const uint8_t* GT, int n) {
+    rowsum_kernel<<<dim3(n / 8, SB), 32, 0, s>>>(GT, n, M, bchunk, b.bpart[l]);
+    return cudaGetLastError();
+  };
+  if ((e = dx(3, b.dY, DYK, b.dZ[2], b.dZT[2])) != cudaSuccess) return e;
+  if ((e = dw(3, b.HT[2], b.dYT, YN)) != cudaSuccess) return e;
+  if ((e = bias(3, b.dYT, YN)) != cudaSuccess) return e;
+  if ((e = dx(2, b.dZ[2], HID, b.dZ[1], b.dZT[1])) != cudaSuccess) return e;
+  if ((e = dw(2, b.HT[1], b.dZT[2], HID)) != cudaSuccess) return e;
+  if ((e = bias(2, b.dZT[2], HID)) != cudaSuccess) return e;
+  if ((e = dx(1, b.dZ[1], HID, nullptr, b.dZT[0])) != cudaSuccess) return e;
+  if ((e = dw(1, b.HT[0], b.dZT[1], HID)) != cudaSuccess) return e;
+  if ((e = bias(1, b.dZT[1], HID)) != cudaSuccess) return e;
+  // layer 0 transposed: dW0^T[n][k] = sum_m dZ0[m][n] X0[m][k]
+  if ((e = dw(0, b.dZT[0], b.X0T, XT)) != cudaSuccess) return e;
+  if ((e = bias(0, b.dZT[0], HID)) != cudaSuccess) return e;
   GradArgs ga{};
-  for (int l = 3; l >= 0; --l) {
-    const LayerDim& D = kLayersHost[l];
-    const bf16* Hin = (l == 0) ? b.X0 : b.H[l - 1];
-    const int kin = D.Kp;
-    // weight gradient: dW = H_in^T dOut (layer 0 computed transposed: dOut^T X0)
-    GemmArgs g{};
-    if (l == 0) {
-      g.A = dOut; g.lda = nOut;  // A(i = n, c = m) stored [m][n]
-      g.B = Hin; g.ldb = kin;    // B(c = m, j = k) stored [m][k]
-      g.M = nOut; g.N = kin;
-    } else {
-      g.A = Hin; g.lda = kin;
-      g.B = dOut; g.ldb = nOut;
-      g.M = kin; g.N = nOut;
-    }
-    g.K = (int)M; g.kchunk = chunk;
-    g.Z = b.wpart[l];
-    if ((e = gemm<false, false, EPI_PARTIAL>(g, kSplits, s)) != cudaSuccess) return e;
-    colsum_kernel<<<dim3((nOut + 127) / 128, kSplits), 128, 0, s>>>(dOut, (int)M, nOut, chunk,
-                                                                    b.bpart[l]);
-    ga.L[l] = GradLayer{b.wpart[l], b.bpart[l], g.M, g.N, D.K, D.N, l == 0 ? 1 : 0,
-                        kSplits, kSplits, D.offW, D.offB};
-    if (l > 0) {
-      // input gradient through the GELU of the layer below
-      GemmArgs d{};
-      d.A = dOut; d.lda = nOut;
-      d.B = b.P.Wn[l]; d.ldb = nOut;
-      d.M = (int)M; d.N = kin; d.K = nOut; d.kchunk = nOut;
-      d.Zprev = b.Z[l - 1]; d.ldzp = HID;
-      bf16* dst = b.dZ[l & 1];
-      d.H = dst; d.ldh = HID;
-      if ((e = gemm<true, true, EPI_DX_GELU>(d, 1, s)) != cudaSuccess) return e;
-      dOut = dst;
-      nOut = HID;
-    }
-  }
+  ga.L[0] = GradLayer{b.wpart[0], b.bpart[0], HID, XT, IN, HID, 1, S, SB, OFF_W0, OFF_B0};
+  ga.L[1] = GradLayer{b.wpart[1], b.bpart[1], HID, HID, HID, HID, 0, S, SB, OFF_W1, OFF_B1};
+  ga.L[2] = GradLayer{b.wpart[2], b.bpart[2], HID, HID, HID, HID, 0, S, SB, OFF_W2, OFF_B2};
+  ga.L[3] = GradLayer{b.wpart[3], b.bpart[3], HID, YN, HID, OUT, 0, S, SB, OFF_W3, OFF_B3};
   ga.grad = b.grad;
   ga.loss_partial = b.lossp;
   ga.nloss = nloss;
@@ -610,7 +525,8 @@ static cudaError_t loss_and_dy(const Bufs& b, int64_t rows, int64_t M, Perm perm
                                const float* params, const float* blob, int* nloss,
                                cudaStream_t s) {
   const int nb = (int)((M + 255) / 256);
-  loss_kernel<<<nb, 256, 0, s>>>(b.Y, rows, M, perm, params, b.ic, blob, b.dY, b.lossp);
+  if (nb > kMaxLossBlocks) return cudaErrorInvalidValue;
+  loss_kernel<<<nb, 256, 0, s>>>(b.Y, rows, M, perm, params, b.ic, blob, b.dY, b.dYT, b.lossp);
   *nloss = nb;
   return cudaGetLastError();
 }
@@ -632,11 +548,13 @@ cudaError_t nn_grad(void* ws, const float* blob, const float* obs, const float* 
   cudaError_t e;
   if ((e = pack(blob, b.P, s)) != cudaSuccess) return e;
   Perm id{1, 0, 0, n};
-  features_kernel<<<(unsigned)((M + 255) / 256), 256, 0, s>>>(obs, n, M, id, blob, b.X0, b.ic);
-  if ((e = forward(blob, b, M, s)) != cudaSuccess) return e;
+  int* err = static_cast<int*>(ws);
+  features_kernel<<<(unsigned)((M + 255) / 256), 256, 0, s>>>(obs, n, M, id, blob, b.X0, b.X0T,
+                                                              b.ic);
+  if ((e = forward(blob, b, M, err, s)) != cudaSuccess) return e;
   int nloss = 0;
   if ((e = loss_and_dy(b, n, M, id, params, blob, &nloss, s)) != cudaSuccess) return e;
-  if ((e = backward(b, M, loss_out, nloss, s)) != cudaSuccess) return e;
+  if ((e = backward(b, M, loss_out, nloss, err, s)) != cudaSuccess) return e;
   return cudaMemcpyAsync(grad_out, b.grad, NTRAIN * sizeof(float), cudaMemcpyDeviceToDevice, s);
 }
 
@@ -645,6 +563,7 @@ cudaError_t nn_train(void* ws, float* blob, const float* obs, const float* param
                      cudaStream_t s) {
   const int64_t M = batch;
   Bufs b = carve(ws, M);
+  int* err = static_cast<int*>(ws);
   cudaError_t e;
   if ((e = cudaMemsetAsync(b.m, 0, NBLOB * 4, s)) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(b.v, 0, NBLOB * 4, s)) != cudaSuccess) return e;
@@ -672,11 +591,11 @@ cudaError_t nn_train(void* ws, float* blob, const float* obs, const float* param
     Perm perm{mult, (h >> 17) % (uint64_t)n, bi * batch, n};
     if ((e = pack(blob, b.P, s)) != cudaSuccess) return e;
     features_kernel<<<(unsigned)((M + 255) / 256), 256, 0, s>>>(obs, M, M, perm, blob, b.X0,
-                                                                b.ic);
-    if ((e = forward(blob, b, M, s)) != cudaSuccess) return e;
+                                                                b.X0T, b.ic);
+    if ((e = forward(blob, b, M, err, s)) != cudaSuccess) return e;
     int nloss = 0;
     if ((e = loss_and_dy(b, M, M, perm, params, blob, &nloss, s)) != cudaSuccess) return e;
-    if ((e = backward(b, M, loss_hist ? loss_hist + t : nullptr, nloss, s)) != cudaSuccess)
+    if ((e = backward(b, M, loss_hist ? loss_hist + t : nullptr, nloss, err, s)) != cudaSuccess)
       return e;
     const double lr = lr0 * 0.5 * (1.0 + cos(3.14159265358979323846 * (double)t / (double)total));
     p1 *= b1;

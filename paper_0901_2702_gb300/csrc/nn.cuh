@@ -14,7 +14,7 @@ namespace nn {
 constexpr int IN = VFISV_NN_NIN, HID = VFISV_NN_NHID, OUT = VFISV_NN_NOUT;
 constexpr int K0P = 64;      // input width padded for the tensor-core tiles
 constexpr int N3P = 64;      // output width padded likewise
-constexpr int kSplits = 16;  // split-K factor of the weight-gradient GEMMs
+constexpr int kSplits = 32;  // most split-K CTAs per tile of the weight-gradient products
 
 constexpr size_t OFF_W0 = 0;
 constexpr size_t OFF_B0 = OFF_W0 + (size_t)IN * HID;
@@ -47,9 +47,10 @@ struct Perm {
   int64_t offset, n;
 };
 
+// BF16 weight copies in the tiled layout of the training products (nn_tc.cuh)
 struct PackedNet {
-  __nv_bfloat16* Wt[4];  // [Np][Kp]
-  __nv_bfloat16* Wn[4];  // [Kp][Np]
+  uint8_t* Wt[4];  // element (output, input): forward B operand
+  uint8_t* Wn[4];  // element (input, output): input-gradient B operand (layers 1-3)
 };
 
 size_t workspace_bytes(int64_t rows);

@@ -10,6 +10,13 @@ events, after --warmup untimed ones) and its throughput in FLOP/s counted
 over the unpadded layers (2 x (24x256 + 2x256x256 + 256x11) per pixel).
 
     python -m paper_0901_2702_gb300.nn_bench --npix 4194304
+
+With --train it times vfisv_nn_train instead: --epochs passes over the
+--npix profiles in batches of --batch, reported per Adam step and as FLOP/s
+over the unpadded products of a step (forward, input gradients of layers
+1-3, weight gradients: 827,904 flops per sample).
+
+    python -m paper_0901_2702_gb300.nn_bench --train --npix 1048576 --epochs 2
 """
 from __future__ import annotations
 
@@ -22,6 +29,8 @@ if __package__ in (None, ""):
     sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
 
 FLOP_PER_PIXEL = 2 * (24 * 256 + 2 * 256 * 256 + 256 * 11)
+# one training sample: forward, input gradients of layers 3..1, weight gradients
+FLOP_PER_TRAIN_SAMPLE = FLOP_PER_PIXEL + 2 * (256 * 11 + 2 * 256 * 256) + FLOP_PER_PIXEL
 
 
 def main():
@@ -30,6 +39,9 @@ def main():
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--iters", type=int, default=10)
+    ap.add_argument("--train", action="store_true", help="time training instead of inference")
+    ap.add_argument("--epochs", type=int, default=2)
+    ap.add_argument("--batch", type=int, default=8192)
     args = ap.parse_args()
 
     import numpy as np
@@ -48,6 +60,26 @@ def main():
     syn = v.vfisv_synth(h, p, tf, tx, W.FE6173).reshape(n, 24)
     obs = (syn + 1e-3 * (p[:, 7] + p[:, 8])[:, None] * t32(W.noise(n, 24, args.seed))).contiguous()
     blob = v.vfisv_nn_init(h, obs, p, seed=args.seed)
+    if args.train:
+        v.vfisv_nn_train(h, blob, obs, p, batch=args.batch, epochs=1, lr0=1e-3, seed=2)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        loss = v.vfisv_nn_train(h, blob, obs, p, batch=args.batch, epochs=args.epochs, lr0=1e-3,
+                                seed=3)
+        e1.record()
+        torch.cuda.synchronize()
+        v.vfisv_check(h)
+        ms = e0.elapsed_time(e1)
+        steps = (n // args.batch) * args.epochs
+        print(json.dumps({"npix": n, "batch": args.batch, "epochs": args.epochs, "steps": steps,
+                          "ms": ms, "ms_per_step": ms / steps,
+                          "tflops": FLOP_PER_TRAIN_SAMPLE * args.batch * steps / (ms / 1e3) / 1e12,
+                          "loss_first": float(loss[:8].mean().item()),
+                          "loss_last": float(loss[-8:].mean().item())}))
+        h.close()
+        return
     init = torch.empty((n, 10), dtype=torch.float32, device=dev)
     for _ in range(args.warmup):
         v.vfisv_nn_infer(h, blob, obs, W.FE6173, want_conf=False, init=init)
