@@ -92,38 +92,60 @@ cudaError_t route_by_confidence(const float* conf, int64_t npix, float conf_rout
   return cudaGetLastError();
 }
 
+__device__ __forceinline__ void merge_one(int64_t j, int lane, const int64_t* __restrict__ index,
+                                          const float* __restrict__ p2, const float* __restrict__ c2,
+                                          const int32_t* __restrict__ i2,
+                                          const int32_t* __restrict__ s2,
+                                          const float* __restrict__ cov2, float* __restrict__ params,
+                                          float* __restrict__ chi2, int32_t* __restrict__ iters,
+                                          int32_t* __restrict__ status, float* __restrict__ cov) {
+  const int64_t p = index[j];
+  int act = 0;  // 1: take the plain result, 2: no valid result (zero covariance)
+  if (lane == 0) {
+    iters[p] += i2[j];
+    const int sp = s2[j];
+    const bool plain_ok = (sp != VFISV_PIX_NAN_STATE) && isfinite(c2[j]);
+    const bool nn_ok = (status[p] != VFISV_PIX_NAN_STATE) && isfinite(chi2[p]);
+    if (plain_ok && (!nn_ok || c2[j] < chi2[p])) {
+      for (int q = 0; q < 10; ++q) params[p * 10 + q] = p2[j * 10 + q];
+      chi2[p] = c2[j];
+      status[p] = sp;
+      act = 1;
+    } else if (status[p] == VFISV_PIX_NAN_STATE) {
+      // no valid result from either run (a routed pixel's row was never written)
+      act = 2;
+    }
+  }
+  act = __shfl_sync(0xffffffffu, act, 0);
+  if (!cov || act == 0) return;
+  for (int q = lane; q < 100; q += 32)
+    cov[p * 100 + q] = (act == 1 && cov2) ? cov2[j * 100 + q] : 0.0f;
+}
+
+// One warp per re-inverted pixel: lane 0 takes the decision, the warp copies
+// the 100-float covariance row with coalesced loads and stores.
 __global__ void merge_kernel(const int64_t* __restrict__ count, const int64_t* __restrict__ index,
                              const float* __restrict__ p2, const float* __restrict__ c2,
                              const int32_t* __restrict__ i2, const int32_t* __restrict__ s2,
                              const float* __restrict__ cov2, float* __restrict__ params,
                              float* __restrict__ chi2, int32_t* __restrict__ iters,
                              int32_t* __restrict__ status, float* __restrict__ cov) {
-  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= *count) return;
-  const int64_t p = index[j];
-  iters[p] += i2[j];
-  const int sp = s2[j];
-  const bool plain_ok = (sp != VFISV_PIX_NAN_STATE) && isfinite(c2[j]);
-  const bool nn_ok = (status[p] != VFISV_PIX_NAN_STATE) && isfinite(chi2[p]);
-  if (plain_ok && (!nn_ok || c2[j] < chi2[p])) {
-    for (int q = 0; q < 10; ++q) params[p * 10 + q] = p2[j * 10 + q];
-    chi2[p] = c2[j];
-    status[p] = sp;
-    if (cov && cov2)
-      for (int q = 0; q < 100; ++q) cov[p * 100 + q] = cov2[j * 100 + q];
-  } else if (cov && status[p] == VFISV_PIX_NAN_STATE) {
-    // no valid result from either run (a routed pixel's row was never written)
-    for (int q = 0; q < 100; ++q) cov[p * 100 + q] = 0.0f;
-  }
+  const int lane = threadIdx.x & 31;
+  const int64_t n = *count;
+  const int64_t stride = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < n; j += stride)
+    merge_one(j, lane, index, p2, c2, i2, s2, cov2, params, chi2, iters, status, cov);
 }
 
 cudaError_t merge_plain(const int64_t* count, const int64_t* index, int64_t npix_max,
                         const float* p2, const float* c2, const int32_t* i2, const int32_t* s2,
                         const float* cov2, float* params, float* chi2, int32_t* iters,
                         int32_t* status, float* cov, cudaStream_t s) {
-  const unsigned nb = (unsigned)((npix_max + 255) / 256);
-  merge_kernel<<<nb, 256, 0, s>>>(count, index, p2, c2, i2, s2, cov2, params, chi2, iters, status,
-                                  cov);
+  int64_t nb = (npix_max * 32 + 255) / 256;
+  if (nb > 152 * 32) nb = 152 * 32;  // grid-stride over the device-side count
+  if (nb < 1) nb = 1;
+  merge_kernel<<<(unsigned)nb, 256, 0, s>>>(count, index, p2, c2, i2, s2, cov2, params, chi2, iters,
+                                            status, cov);
   return cudaGetLastError();
 }
 

@@ -40,3 +40,41 @@ def test_reference_line():
 def test_reference_other_ranks_silent():
     r = _run({"RANK": "1", "WORLD_SIZE": "2"})
     assert r.returncode == 0 and r.stdout.strip() == ""
+
+
+def test_calibration_emulates_the_mixed_inversion():
+    """The benchmark chooses the routing threshold from two deterministic
+    ingredients (LM from the network's guess, plain LM) without rerunning the
+    mixed pipeline; its composition must give the oracle's mixed inversion
+    for every threshold: the routed pixels' plain result, the others' first
+    result unless flagged, then the lower chi2."""
+    import numpy as np
+    import torch
+
+    import bench
+    import workloads as W
+    from oracle import lm, me, mlp
+
+    x = W.wavelength_grid()
+    T = W.hmi_filters(x)
+    p = W.quiet_and_active_params(12, 71)
+    s = me.synth(p, T, x, W.FE6173).reshape(12, -1)
+    o, w = W.observe(s, p, W.noise(12, 24, 71))
+    rng = np.random.default_rng(2)
+    weights = [(rng.uniform(-1, 1, (a, b)) * np.sqrt(6.0 / a), rng.normal(0, 0.05, b))
+               for a, b in zip(mlp.LAYERS[:-1], mlp.LAYERS[1:])]
+    blob = mlp.pack(weights, mlp.statistics(o, p))
+    wq, st = mlp.unpack(blob)
+    y, _ = mlp.forward(wq, mlp.features(o, st))
+    first = lm.invert(o, w, T, x, W.FE6173, init=mlp.decode(y, o, st), max_iter=8)
+    plain = lm.invert(o, w, T, x, W.FE6173, max_iter=15)
+    tt = lambda r: {"chi2": torch.tensor(r["chi2"]), "status": torch.tensor(r["status"])}  # noqa: E731
+    conf = torch.tensor(y[:, 10])
+    for k in (-np.inf, float(np.median(y[:, 10])), np.inf):
+        ref = lm.invert_mixed(o, w, T, x, W.FE6173, blob, nn_cap=8, plain_cap=15, chi2_flag=1.5,
+                              flag_unconverged=True, conf_route=k)
+        c2, st_, ran = bench.mixed_outcome(conf > k, tt(first), tt(plain), 1.5, True)
+        ok = np.isfinite(ref["chi2"])
+        np.testing.assert_array_equal(c2.numpy()[ok], ref["chi2"][ok])
+        np.testing.assert_array_equal(st_.numpy()[ok], ref["status"][ok])
+        np.testing.assert_array_equal(ran.numpy(), ref["flagged"].astype(bool))
