@@ -3,8 +3,9 @@
 // launch of tc_gemm_kernel: a CTA computes a 128-row tile of D = A B^T over a
 // range of K (split-K for the weight gradients), BF16 operands streamed by 1D
 // bulk copies through a four-stage shared-memory ring, FP32 accumulators in
-// tensor memory, and an epilogue (four warps, one accumulator lane = one row
-// each) that writes the next product's operands directly.
+// tensor memory, and an epilogue (16 warps, each a quarter of the
+// accumulator lanes -- one row per thread -- and a quarter of the columns)
+// that writes the next product's operands directly.
 //
 // Operand layout in global memory, "tiled canonical" TL(R, C) for an R x C
 // BF16 matrix (R a multiple of 8, C of 64): K-chunks of 64 columns one after
@@ -40,8 +41,10 @@ constexpr int KCH = 64;       // K per stage
 constexpr int NSTAGE = 4;     // ring depth
 constexpr uint32_t kAChunk = TMR * KCH * 2;  // 16384
 
+constexpr int kThreads = 512;  // 16 warps: 4 accumulator lane quarters x 4 column quarters
+
 template <int N, int EPI>
-__global__ void __launch_bounds__(128, 1) tc_gemm_kernel(TcGemmArgs g) {
+__global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(TcGemmArgs g) {
   static_assert(N == 16 || N == 32 || N == 256, "tile width");
   constexpr uint32_t kBChunk = N * KCH * 2;
   constexpr uint32_t kStage = kAChunk + kBChunk;
@@ -128,10 +131,17 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(TcGemmArgs g) {
     }
   } else {
     tc_after_sync();
-    const int row = tid;  // accumulator lane = tile row
+    // warp w reads accumulator lanes 32 (w % 4) .. + 31 (its lane quarter)
+    // and the column quarter w / 4 (for N <= 32 the first quarter takes all)
+    const int lq = warp & 3, cq = warp >> 2;
+    const int row = 32 * lq + (tid & 31);  // accumulator lane = tile row
     const int64_t m = (int64_t)mt * TMR + row;
-    const uint32_t lane_addr = tmem + ((uint32_t)(32 * warp) << 16);
+    const uint32_t lane_addr = tmem + ((uint32_t)(32 * lq) << 16);
+    constexpr int kCols = N >= 128 ? N / 4 : N;  // columns per warp
+    const int cbeg = (N >= 128) ? cq * kCols : 0;
+    const bool active = (N >= 128) || cq == 0;
     if constexpr (N == 16) {
+      if (!active) goto done;
       float v[16];
       tmem_ld16(lane_addr, v);
       if constexpr (EPI == EPI_OUT) {
@@ -150,8 +160,9 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(TcGemmArgs g) {
           *reinterpret_cast<float4*>(pp + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
       }
     } else {
+      if (!active) goto done;
 #pragma unroll 1
-      for (int c0 = 0; c0 < N; c0 += 32) {
+      for (int c0 = cbeg; c0 < cbeg + kCols; c0 += 32) {
         float v[32];
         tmem_ld32(lane_addr + (uint32_t)c0, v);
         if constexpr (EPI == EPI_PARTIAL) {
@@ -206,6 +217,7 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(TcGemmArgs g) {
       }
     }
   }
+done:
   tc_before_sync();
   __syncthreads();
   if (warp == 0) {
@@ -227,7 +239,7 @@ cudaError_t launch_n(const TcGemmArgs& g, int mtiles, int splits, cudaStream_t s
   const size_t sm = gemm_smem<N>();
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
-  kern<<<dim3((unsigned)mtiles, (unsigned)splits), 128, sm, s>>>(g);
+  kern<<<dim3((unsigned)mtiles, (unsigned)splits), kThreads, sm, s>>>(g);
   return cudaGetLastError();
 }
 
