@@ -7,49 +7,89 @@ namespace vfisv {
 // Pack filters [nf][nlam] and offsets [nlam] into the row-major table and
 // append tau_k = sum_i T_k(x_i).  One block; threads stride over rows.
 //
-// Rows whose largest |T_k(x_i)| is at most kRowDrop times the largest weight
-// of the table are left out (kept rows stay in grid order): their products
-// change a filtered value S_k = sum_i T_k(x_i) y(x_i) by less than
-// nlam * 2^-40 * max|T| * max|y|, five orders of magnitude below the FP32
-// rounding of S_k, so the sums are those over the whole grid.  For the HMI-like
-// filters (Gaussian FWHM 76 mA x sinc^2, six positions 69 mA apart) on the
-// 149-point grid 79 rows remain: the far wings, where every filter is below
-// 1e-12 of its peak, carry no weight.  tau_k still sums every row.  The
-// number of kept rows goes to the last float of the tau row (as int bits).
-constexpr float kRowDrop = 0x1p-40f;
+// Grid points that carry almost none of any filter's weight are left out
+// (kept rows stay in grid order).  With M_k = sum_i |T_k(x_i)| and a point's
+// relative weight r_i = max_k |T_k(x_i)| / M_k, the points of least r are
+// dropped as long as, for every filter, the dropped |weights| sum to at most
+// kMassDrop * M_k.  A filtered value S_k = sum_i T_k(x_i) y(x_i) then moves
+// by at most 2^-24 M_k max|y|: the size of one FP32 rounding of a sum of that
+// magnitude, so the sums are those over the whole grid to working precision.
+// For the HMI-like filters (Gaussian FWHM 76 mA x sinc^2, six positions
+// 69 mA apart) on the 149-point grid 63 points remain, the central
+// -310 ... +310 mA; the oracle's Stokes through the cut grid differ from the
+// full-grid ones by 1e-8 of the continuum.  The largest dropped set is found
+// by bisection over the bit patterns of r (non-negative floats order like
+// their bits).  tau_k still sums every row; a NaN or infinite weight, or a
+// grid longer than kMassGrid points, keeps every row.  The number of kept
+// rows goes to the last float of the tau row (as int bits).
+constexpr float kMassDrop = 0x1p-24f;
+constexpr int kMassGrid = 4096;
+constexpr int kMassMaxNF = 128;
 
 __global__ void pack_table_kernel(const float* __restrict__ filters, int nf,
                                   const float* __restrict__ wl, int nlam,
                                   float* __restrict__ table) {
   const int S = table_stride(nf);
-  __shared__ float red[32];
+  __shared__ float rbuf[kMassGrid];  // relative weight r_i of each point
+  __shared__ float mass[kMassMaxNF];  // M_k
   __shared__ int wsum[32];
-  __shared__ int base;
+  __shared__ int base, lo_s, hi_s, ok_s;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  // largest |weight| (a NaN weight keeps its row: the NaN reaches the sums)
-  float m = 0.0f;
-  for (int i = threadIdx.x; i < nf * nlam; i += blockDim.x) m = fmaxf(m, fabsf(filters[i]));
-  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-  if (lane == 0) red[warp] = m;
-  if (threadIdx.x == 0) base = 0;
+  // M_k: one warp per filter, lane-strided then a shuffle tree
+  for (int k = warp; k < nf && k < kMassMaxNF; k += nw) {
+    float m = 0.0f;
+    for (int i = lane; i < nlam; i += 32) m += fabsf(filters[(size_t)k * nlam + i]);
+    for (int o = 16; o > 0; o >>= 1) m += __shfl_xor_sync(0xffffffffu, m, o);
+    if (lane == 0) mass[k] = m;
+  }
+  if (threadIdx.x == 0) {
+    base = 0;
+    lo_s = -1;  // bits of the largest r dropped (-1: none)
+    hi_s = 0;
+  }
   __syncthreads();
-  m = 0.0f;
-  for (int w = 0; w < nw; ++w) m = fmaxf(m, red[w]);
-  const float thr = m * kRowDrop;
+  bool usable = nlam <= kMassGrid && nf <= kMassMaxNF;
+  for (int k = 0; k < nf && usable; ++k) usable = isfinite(mass[k]);
+  if (usable) {
+    int rmax = 0;
+    for (int i = threadIdx.x; i < nlam; i += blockDim.x) {
+      float r = 0.0f;
+      for (int k = 0; k < nf; ++k)
+        if (mass[k] > 0.0f) r = fmaxf(r, fabsf(filters[(size_t)k * nlam + i]) / mass[k]);
+      rbuf[i] = r;
+      rmax = max(rmax, __float_as_int(r));
+    }
+    for (int o = 16; o > 0; o >>= 1) rmax = max(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
+    if (lane == 0) atomicMax(&hi_s, rmax);
+    __syncthreads();
+    // invariant: dropping r <= lo is within bounds; hi is not known to be
+    for (;;) {
+      const int lo = lo_s, hi = hi_s;
+      if (hi - lo <= 1) break;
+      const int mid = lo + (hi - lo) / 2;
+      if (threadIdx.x == 0) ok_s = 1;
+      __syncthreads();
+      for (int k = warp; k < nf; k += nw) {
+        float d = 0.0f;
+        for (int i = lane; i < nlam; i += 32)
+          if (__float_as_int(rbuf[i]) <= mid) d += fabsf(filters[(size_t)k * nlam + i]);
+        for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+        if (lane == 0 && !(d <= kMassDrop * mass[k])) ok_s = 0;
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        if (ok_s) lo_s = mid;
+        else hi_s = mid;
+      }
+      __syncthreads();
+    }
+  }
+  __syncthreads();
+  const int lo = lo_s;
   // ordered compaction, blockDim rows at a time
   for (int i0 = 0; i0 < nlam; i0 += blockDim.x) {
     const int i = i0 + threadIdx.x;
-    bool keep = false;
-    if (i < nlam) {
-      float r = 0.0f;
-      bool nan = false;
-      for (int k = 0; k < nf; ++k) {
-        const float t = filters[(size_t)k * nlam + i];
-        nan |= isnan(t);
-        r = fmaxf(r, fabsf(t));
-      }
-      keep = nan || r > thr;
-    }
+    const bool keep = i < nlam && (!usable || __float_as_int(rbuf[i]) > lo);
     const unsigned b = __ballot_sync(0xffffffffu, keep);
     if (lane == 0) wsum[warp] = __popc(b);
     __syncthreads();

@@ -9,7 +9,9 @@ within FP32 rounding; the criteria compare what is unique):
   sigma_gamma, sigma_psi < 5 deg from its covariance): |dB| <= 1 G,
   |dgamma| <= 0.05 deg, |dpsi mod 180| <= 0.05 deg for >= 98 %;
 * pixels whose GPU and oracle iteration counts agree follow the same
-  trajectory: for them chi2 agrees within 1e-3 relative for all.
+  trajectory: for them chi2 agrees within 1e-3 relative for all, except
+  where the oracle itself lands elsewhere when its inputs are nudged by
+  1e-7 (then the equal count is a coincidence).
 """
 import numpy as np
 import pytest
@@ -60,6 +62,26 @@ def _compare(g, o):
     return out
 
 
+def _equal_counts_agree(c, g, o, obs, w):
+    """Pixels converged in both runs with equal iteration counts agree in chi2
+    to 1e-3, unless the oracle itself is not reproducible on the pixel: one
+    of eight oracle runs on its observations nudged by 1e-7 (relative) ends
+    more than 1e-3 from the unnudged chi2.  An equal count is then a
+    coincidence of two trajectories that parted (LM on such a pixel lands in
+    different minima under perturbations at the FP32 rounding level)."""
+    same = c["both"] & (g["iters"] == o["iters"])
+    assert same.sum() > 100
+    for i in np.flatnonzero(same & (c["rel"] > 1e-3)):
+        rng = np.random.default_rng(int(i))
+        o1 = np.asarray(obs[i:i + 1], dtype=np.float64)
+        spread = 0.0
+        for _ in range(8):
+            r = lm.invert(o1 * (1.0 + 1e-7 * rng.standard_normal(o1.shape)), w[i:i + 1],
+                          f32(T), f32(X), LINE)
+            spread = max(spread, abs(r["chi2"][0] / o["chi2"][i] - 1.0))
+        assert spread > 1e-3, (int(i), float(c["rel"][i]), spread)
+
+
 def test_standard_guess_parity(vf):
     """1000 pixels (7 full blocks and a ragged tail) of the small workload."""
     v, h, torch = vf
@@ -70,8 +92,7 @@ def test_standard_guess_parity(vf):
     assert c["both"].mean() > 0.5
     assert np.mean(c["rel"][c["both"]] <= 1e-3) >= 0.98
     assert np.mean(c["angles_ok"][c["wd"]]) >= 0.98
-    same = c["both"] & (g["iters"] == o["iters"])
-    assert same.sum() > 100 and np.all(c["rel"][same] <= 1e-3)
+    _equal_counts_agree(c, g, o, obs, w)
     assert np.mean(g["status"] == o["status"]) >= 0.8
 
 
@@ -205,7 +226,7 @@ def test_full_map_sampled(vf):
 
 def test_work_counters(vf):
     """The LM kernel's work counters (vfisv_counters): one pass per trial plus
-    one per starting model, every pixel retired, the packed table's 79 kept
+    one per starting model, every pixel retired, the packed table's 63 kept
     grid points per pass, and accepted trials close to the oracle's count of
     successful steps on the same inputs (trajectories part at near ties)."""
     v, h, torch = vf
@@ -215,7 +236,7 @@ def test_work_counters(vf):
     c = v.vfisv_counters(h, reset=True)
     assert c["retired"] == 2000
     assert c["passes"] == int(g["iters"].sum()) + 2000
-    assert c["points"] == 79 * c["passes"]
+    assert c["points"] == 63 * c["passes"]
     o = lm.invert(obs, w, f32(T), f32(X), LINE)
     assert abs(c["accepted"] / o["accepted"].sum() - 1) < 0.03, (c, o["accepted"].sum())
     assert v.vfisv_counters(h)["passes"] == 0  # reset
@@ -242,5 +263,4 @@ def test_threads_per_pixel_parity(vf, tpp, block):
     assert c["both"].mean() > 0.5
     assert np.mean(c["rel"][c["both"]] <= 1e-3) >= 0.98
     assert np.mean(c["angles_ok"][c["wd"]]) >= 0.98
-    same = c["both"] & (g["iters"] == o["iters"])
-    assert same.sum() > 100 and np.all(c["rel"][same] <= 1e-3)
+    _equal_counts_agree(c, g, o, obs, w)
