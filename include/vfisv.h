@@ -272,25 +272,32 @@ void vfisv_graph_destroy(vfisv_graph* g);
  * workload asks for pixels per CTA and threads per pixel to be tuned): time
  * an inversion of the given sample (arguments as vfisv_invert, no
  * covariance) with 64, 128 and 256 threads per CTA and 1, 2 and 4 threads
- * per pixel, keep the fastest shape for this handle's later inversions and
- * return it in best_block (threads per CTA) and best_tpp (threads per
- * pixel, may be NULL); ms_out (may be NULL) receives the nine times,
- * threads-per-pixel-major: ms_out[3 * i + j] for tpp = {1, 2, 4}[i], block =
- * {64, 128, 256}[j].  With tpp threads per pixel the lanes of a pixel split
- * its wavelength points: a pass has tpp times as many threads, so small
- * maps (fewer pixels than resident slots) finish sooner, while the solve
- * and the normal equations are repeated on every lane of the pixel.
- * Restarts and a free filling factor always run 128 x 1.  Results do not
+ * per pixel, and with the warp-specialised kernel (384 threads per CTA, one
+ * pixel per thread of its two consumer warpgroups, one CTA per SM), keep the
+ * fastest shape for this handle's later inversions and return it in
+ * best_block (threads per CTA) and best_tpp (threads per pixel, may be
+ * NULL); ms_out (may be NULL) receives the ten times: ms_out[3 * i + j] for
+ * tpp = {1, 2, 4}[i], block = {64, 128, 256}[j], then ms_out[9] for 384 x 1.
+ * With tpp threads per pixel the lanes of a pixel split its wavelength
+ * points: a pass has tpp times as many threads, so small maps (fewer pixels
+ * than resident slots) finish sooner, while the solve and the normal
+ * equations are repeated on every lane of the pixel.  The warp-specialised
+ * kernel runs the wavelength pass in one warpgroup and the chi2, normal
+ * equations and FP64 solve in the other two, handing the filtered rows over
+ * through tensor memory; it takes the default configuration (restarts, a
+ * free filling factor and fast_solve run the 128 x 1 kernel instead).
+ * Results do not
  * depend on the shape beyond FP32 summation order.  Synchronises `stream`. */
 int vfisv_autotune(vfisv_handle* h, const float* obs, const float* weights,
                    int32_t weights_per_pixel, const float* filters, int32_t nfilt,
                    const float* wl_mA, int32_t nlam, const vfisv_line* line,
                    const vfisv_config* cfg, int64_t npix, int32_t* best_block, int32_t* best_tpp,
-                   float* ms_out, void* stream);
+                   float* ms_out /*[10]*/, void* stream);
 
 /* Set the launch shape of the handle's filter-position LM kernel directly:
- * block in {64, 128, 256} threads per CTA, tpp in {1, 2, 4} threads per
- * pixel (default 128 x 1).  VFISV_E_ARG for any other value. */
+ * block in {64, 128, 256} threads per CTA with tpp in {1, 2, 4} threads per
+ * pixel, or block = 384 with tpp = 1 for the warp-specialised kernel
+ * (default 128 x 1).  VFISV_E_ARG for any other value. */
 int vfisv_set_launch_shape(vfisv_handle* h, int32_t block, int32_t tpp);
 
 /* Persistent launches of this handle (the LM, wide, covariance and network

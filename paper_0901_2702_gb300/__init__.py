@@ -485,14 +485,15 @@ def vfisv_graph_destroy(g: Graph) -> None:
 
 def vfisv_autotune(h: Handle, obs, weights, filters, wl_mA, line, config=None, stream=None):
     """Pick the LM kernel's launch shape on a sample; returns (threads per CTA,
-    threads per pixel, [ms x 9] threads-per-pixel-major)."""
+    threads per pixel, [ms x 10]: threads-per-pixel-major over 64/128/256 x
+    1/2/4, then the warp-specialised 384 x 1)."""
     npix = int(obs.shape[0])
     nfilt, nlam = int(filters.shape[0]), int(filters.shape[1])
     per_pixel = 1 if (len(weights.shape) >= 2 and int(weights.shape[0]) == npix) else 0
     cfg = config if isinstance(config, vfisv_config) else vfisv_config_default(**(config or {}))
     ptrs = [_ptr(x, np.float32) for x in (obs, weights, filters, wl_mA)]
     best, tpp = ctypes.c_int32(), ctypes.c_int32()
-    ms = np.zeros(9, np.float32)
+    ms = np.zeros(10, np.float32)
     ln = _line(line)
     _check(load().vfisv_autotune(h.ptr, ptrs[0][0], ptrs[1][0], per_pixel, ptrs[2][0], nfilt,
                                  ptrs[3][0], nlam, ctypes.byref(ln), ctypes.byref(cfg), npix,
@@ -502,7 +503,8 @@ def vfisv_autotune(h: Handle, obs, weights, filters, wl_mA, line, config=None, s
 
 
 def vfisv_set_launch_shape(h: Handle, block: int, tpp: int = 1) -> None:
-    """Threads per CTA (64, 128, 256) and per pixel (1, 2, 4) of the LM kernel."""
+    """Threads per CTA (64, 128, 256) and per pixel (1, 2, 4) of the LM kernel,
+    or 384 x 1: the warp-specialised kernel."""
     _check(load().vfisv_set_launch_shape(h.ptr, int(block), int(tpp)), "vfisv_set_launch_shape")
 
 

@@ -13,7 +13,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libvfisv.so")
-SOURCES = ["api.cu", "synth.cu", "invert.cu", "nn.cu", "nn_tc.cu", "mlp_tc.cu", "mixed.cu", "noalloc.cu",
+SOURCES = ["api.cu", "synth.cu", "invert.cu", "invert_ws.cu", "nn.cu", "nn_tc.cu", "mlp_tc.cu", "mixed.cu", "noalloc.cu",
            "voigt.cu", "prep.cu", "wide.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]

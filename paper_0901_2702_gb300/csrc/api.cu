@@ -752,16 +752,21 @@ int vfisv_autotune(vfisv_handle* h, const float* obs, const float* weights,
   int rc = grow(&h->mixws, &h->mixws_bytes, off);
   if (rc) return rc;
   char* mw = (char*)h->mixws;
-  // threads per CTA x threads per pixel, threads-per-pixel-major
+  // threads per CTA x threads per pixel, threads-per-pixel-major, then the
+  // warp-specialised kernel (kInvWsBlock threads, one pixel per consumer
+  // thread)
   const int cand_b[3] = {64, 128, 256}, cand_t[3] = {1, 2, 4};
+  auto shape = [&](int c, int* b, int* t) {
+    *b = (c < 9) ? cand_b[c % 3] : kInvWsBlock;
+    *t = (c < 9) ? cand_t[c / 3] : 1;
+  };
   float best = 0.0f;
   int best_b = 128, best_t = 1;
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  for (int c = 0; c < 9; ++c) {
-    h->lm_block = cand_b[c % 3];
-    h->lm_tpp = cand_t[c / 3];
+  for (int c = 0; c < 10; ++c) {
+    shape(c, &h->lm_block, &h->lm_tpp);
     float ms = 0.0f;
     for (int rep = 0; rep < 2; ++rep) {  // the first run warms up
       cudaEventRecord(e0, s);
@@ -777,8 +782,7 @@ int vfisv_autotune(vfisv_handle* h, const float* obs, const float* weights,
     if (ms_out) ms_out[c] = ms;
     if (c == 0 || ms < best) {
       best = ms;
-      best_b = cand_b[c % 3];
-      best_t = cand_t[c / 3];
+      shape(c, &best_b, &best_t);
     }
   }
   cudaEventDestroy(e0);
@@ -791,8 +795,8 @@ int vfisv_autotune(vfisv_handle* h, const float* obs, const float* weights,
 }
 
 int vfisv_set_launch_shape(vfisv_handle* h, int32_t block, int32_t tpp) {
-  if (!h || !(block == 64 || block == 128 || block == 256) || !(tpp == 1 || tpp == 2 || tpp == 4))
-    return VFISV_E_ARG;
+  const bool plain = (block == 64 || block == 128 || block == 256) && (tpp == 1 || tpp == 2 || tpp == 4);
+  if (!h || !(plain || (block == kInvWsBlock && tpp == 1))) return VFISV_E_ARG;
   h->lm_block = block;
   h->lm_tpp = tpp;
   return VFISV_OK;

@@ -16,7 +16,13 @@ extern thread_local int t_sm_limit;
 inline int sm_budget(int nsm) { return (t_sm_limit > 0 && t_sm_limit < nsm) ? t_sm_limit : nsm; }
 
 // Device error codes written to the handle's error word.
-enum : int { kDevErrNone = 0, kDevErrTableWait = 1, kDevErrNnWait = 2, kDevErrPoolWait = 3 };
+enum : int {
+  kDevErrNone = 0,
+  kDevErrTableWait = 1,
+  kDevErrNnWait = 2,
+  kDevErrPoolWait = 3,
+  kDevErrWsWait = 4,  // a hand-off wait of the warp-specialised LM kernel gave up
+};
 
 // Filter table layout in global and shared memory: nlam rows of `stride`
 // floats {T_0(x_i), ..., T_{nf-1}(x_i), x_i, pad...}, then one row holding
@@ -234,6 +240,14 @@ cudaError_t launch_restart_perturb(const float* in, int64_t n, int64_t pix0, int
 // Upload the Weideman coefficients to the LM kernel's constant bank on the
 // current device (once per device).
 cudaError_t invert_set_constants(const Weideman& W);
+// The warp-specialised LM kernel (invert_ws.cu): CTAs of kInvWsBlock threads
+// (one producer warpgroup, two consumer warpgroups), 256 pixel slots each,
+// one per SM; the default configuration only (6 filters, FP64 solve, no
+// restarts, filling factor held).
+constexpr int kInvWsBlock = 384;
+cudaError_t invert_ws_set_constants(const Weideman& W);
+cudaError_t invert_ws_slots(int nlam, int64_t npix, int64_t* nslots, int* grid, size_t* smem);
+cudaError_t launch_invert_ws(const InvertArgs& a, int grid, size_t smem, cudaStream_t s);
 cudaError_t launch_covariance(float* cov, const int32_t* status, int64_t npix,
                               const int64_t* npix_dev, uint32_t free_mask, int fast_solve,
                               cudaStream_t s);

@@ -12,27 +12,12 @@
 
 #include "common.cuh"
 #include "dfloat.cuh"
+#include "lm_device.cuh"
 #include "solve.cuh"
 
 namespace vfisv {
 
 constexpr int kInvThreadsDefault = 128;  // pixel slots per CTA unless autotuned
-
-// Compensated accumulation of a product: s + c tracks sum(a*b) to about
-// twice the working precision (TwoProduct via FMA, TwoSum).
-struct Dot2 {
-  float s, c;
-  __device__ __forceinline__ void add(float a, float b) {
-    const float p = a * b;
-    const float ep = fmaf(a, b, -p);
-    const float t = s + p;
-    const float bp = t - s;
-    const float es = (s - (t - bp)) + (p - bp);
-    s = t;
-    c += es + ep;
-  }
-  __device__ __forceinline__ float value() const { return s + c; }
-};
 
 // The same factorisation and solve in double-float arithmetic (the fast
 // path of the damped step; FP64 is kept for the rare singular fallback).
@@ -673,73 +658,26 @@ __global__ void __launch_bounds__(BS, 1) invert_kernel(InvertArgs A) {
 #pragma unroll
       for (int j = 0; j < 10; ++j) ST(sM, j) = ST(sMt, j);
       sChi[ps] = c2;
-      Dot2 a[NPK], g[NP];
-#pragma unroll
-      for (int i = 0; i < NPK; ++i) a[i] = Dot2{0.0f, 0.0f};
-#pragma unroll
-      for (int i = 0; i < NP; ++i) g[i] = Dot2{0.0f, 0.0f};
-      constexpr int rowOf[10] = {kRowB, kRowG, -1, kRowE, kRowD, kRowA, kRowV, -1, -1, -1};
-      // rows of the non-magnetic profile for eta0, dlambdaD, a, v (AF)
-      constexpr int nmRowOf[10] = {-1, -1, -1, 1, 2, 3, 4, -1, -1, -1};
-      const float mu = A.lk.mu;
-      const RowScale R = row_scale(A.lk, ST(sMt, 3), ST(sMt, 4));
       // Hessian reuse (Sec. 4.4): this and the previous accepted step both
       // close to the minimum -> keep J^T W J, rebuild J^T W r only
       const bool near = rel_acc < A.hess_reuse;
       const bool keepA = near && near_in;
       sNear[ps] = near;
-      // Runtime loops over (filter, Stokes) keep this block small: it runs
-      // on accepted steps only and must not evict the wavelength loop from
-      // the instruction cache.  Observable (s, k) of row r is
-      // fmaf(cA, D(r, sa, k), cB * D(r, sb, k)), the psi rotation of Q0/U0.
-#pragma unroll 1
-      for (int k = 0; k < NF; ++k) {
-        const float q0 = alf * D(0, 1, k), u0 = alf * D(0, 2, k);
-        const float Qk = mus1 * fmaf(c2p, q0, -s2p * u0);
-        const float Uk = mus1 * fmaf(s2p, q0, c2p * u0);
-#pragma unroll 1
-        for (int s = 0; s < 4; ++s) {
-          const int sa = (s == 0) ? 0 : (s == 3 ? 3 : 1);
-          const int sb = (s == 0) ? 0 : (s == 3 ? 3 : 2);
-          const float cA = (s == 1) ? c2p : (s == 2 ? s2p : 1.0f);
-          const float cB = (s == 1) ? -s2p : (s == 2 ? c2p : 0.0f);
-          float J[NP];
+      auto fetch = [&](int k, int s, ObsRows& rw) {
+        const int sa = obs_sa(s), sb = obs_sb(s);
 #pragma unroll
-          for (int p = 0; p < NP; ++p)
-            if (rowOf[p] >= 0) {
-              J[p] = (alf * mus1 * R.s[rowOf[p]]) *
-                     fmaf(cA, D(rowOf[p], sa, k), cB * D(rowOf[p], sb, k));
-              if (AF && nmRowOf[p] > 0 && s == 0)
-                J[p] = fmaf((1.0f - alf) * mus1 * R.s[rowOf[p]], N(nmRowOf[p], k), J[p]);
-            }
-          J[2] = (s == 1) ? -2.0f * kDeg * Uk : (s == 2 ? 2.0f * kDeg * Qk : 0.0f);
-          J[7] = (s == 0) ? tau[k] : 0.0f;
-          const float linm = fmaf(cA, D(0, sa, k), cB * D(0, sb, k));  // magnetic
-          const float lin = AF ? ((s == 0) ? fmaf(alf, linm - N(0, k), N(0, k)) : alf * linm)
-                               : linm;
-          J[8] = mu * lin;
-          if constexpr (AF) J[NP - 1] = mus1 * ((s == 0) ? linm - N(0, k) : linm);
-          const float sv = (s == 0) ? fmaf(s0, tau[k], mus1 * lin) : mus1 * lin;
-          const int ob = s * NF + k;
-          const float ww = wv[ob];
-          const float rr = o[ob] - sv;
-#pragma unroll
-          for (int p = 0; p < NP; ++p) {
-            const float wj = ww * J[p];
-            g[p].add(wj, rr);
-            if (!keepA) {
-#pragma unroll
-              for (int q = 0; q <= p; ++q) a[tri(p, q)].add(wj, J[q]);
-            }
-          }
+        for (int r = 0; r < kRows; ++r) {
+          rw.a[r] = D(r, sa, k);
+          rw.b[r] = D(r, sb, k);
         }
-      }
-      if (!keepA) {
+        if constexpr (AF)
 #pragma unroll
-        for (int i = 0; i < NPK; ++i) scr[(int64_t)i * ns] = a[i].value();
-      }
-#pragma unroll
-      for (int i = 0; i < NP; ++i) scr[(int64_t)(NPK + i) * ns] = g[i].value();
+          for (int r = 0; r < kNmRows; ++r) rw.n[r] = N(r, k);
+      };
+      build_normal_equations<NF, NP, AF, false>(fetch, o, wv, tau, scr, ns, mus1, c2p, s2p, s0,
+                                                alf, A.lk.mu,
+                                                row_scale(A.lk, ST(sMt, 3), ST(sMt, 4)), keepA,
+                                                true, !keepA);
       if (RS && c2 < *rsBest) {
         // a new best over all segments: keep it with its normal equations
         *rsBest = c2;
@@ -946,12 +884,20 @@ cudaError_t invert_slots(int nf, int nlam, int64_t npix, int restarts, int fast_
     *tpp = 1;
     return slots_for<kInvThreadsDefault, false, false, true>(nlam, npix, nslots, grid, smem);
   }
+  if (*block == kInvWsBlock) {
+    if (!restarts && !fast_solve) {  // the warp-specialised kernel
+      *tpp = 1;
+      return invert_ws_slots(nlam, npix, nslots, grid, smem);
+    }
+    *block = kInvThreadsDefault;  // not compiled for this configuration
+  }
   return fast_solve ? invert_slots_t<true>(nlam, npix, restarts, nslots, grid, block, tpp, smem)
                     : invert_slots_t<false>(nlam, npix, restarts, nslots, grid, block, tpp, smem);
 }
 
 cudaError_t invert_set_constants(const Weideman& W) {
-  return cudaMemcpyToSymbol(c_W, &W, sizeof(W));
+  const cudaError_t e = cudaMemcpyToSymbol(c_W, &W, sizeof(W));
+  return e != cudaSuccess ? e : invert_ws_set_constants(W);
 }
 
 template <bool DF, int TPP>
@@ -990,6 +936,10 @@ cudaError_t launch_invert(const InvertArgs& a, int nf, int grid, int block, int 
       return cudaErrorInvalidValue;
     invert_kernel<6, kInvThreadsDefault, false, false, true><<<grid, block, smem, s>>>(a);
     return cudaGetLastError();
+  }
+  if (block == kInvWsBlock) {
+    if (a.restarts || a.fast_solve || tpp != 1) return cudaErrorInvalidValue;
+    return launch_invert_ws(a, grid, smem, s);
   }
   return a.fast_solve ? launch_invert_t<true>(a, grid, block, tpp, smem, s)
                       : launch_invert_t<false>(a, grid, block, tpp, smem, s);

@@ -226,8 +226,9 @@ __device__ __forceinline__ void scaled_system(const float* scr, int64_t ns, uint
 // 1e-10) takes the unit-diagonal Jacobi scaling and the truncated
 // eigen-decomposition.
 template <int N = kNP>
-static __device__ __noinline__ void damped_step_fp64(const float* scr, int64_t ns, uint32_t free_mask, double eps,
-                            double (&delta)[N]) {
+__device__ __forceinline__ void damped_step_fp64_body(const float* scr, int64_t ns,
+                                                      uint32_t free_mask, double eps,
+                                                      double (&delta)[N]) {
   double L[(N * (N + 1) / 2)];
   int ex[N];  // P_ii = 2^-ex[i]
   bool held[N];
@@ -275,6 +276,15 @@ static __device__ __noinline__ void damped_step_fp64(const float* scr, int64_t n
   jacobi_pinv<N>(L, b, y, nullptr);
 #pragma unroll
   for (int i = 0; i < N; ++i) delta[i] = held[i] ? 0.0 : sc[i] * y[i];
+}
+
+// The same step kept out of line (the LM kernel that calls it from the
+// middle of its iteration gives it the whole register file).
+template <int N = kNP>
+static __device__ __noinline__ void damped_step_fp64(const float* scr, int64_t ns,
+                                                     uint32_t free_mask, double eps,
+                                                     double (&delta)[N]) {
+  damped_step_fp64_body<N>(scr, ns, free_mask, eps, delta);
 }
 
 // Covariance (J^T W J)^+ at the final model, in parameter units, from the

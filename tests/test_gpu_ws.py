@@ -1,0 +1,91 @@
+"""The warp-specialised LM kernel (launch shape 384 x 1: a producer warpgroup
+running the fused wavelength pass, two consumer warpgroups running chi2,
+the normal equations and the FP64 solve, the filtered rows handed over in
+tensor memory) against the one-warpgroup kernel (128 x 1).  Both run the
+same passes, decisions and sums in the same order, so every output must
+agree bit for bit; parity with the oracle then carries over from the tests
+of the 128 x 1 kernel.  Cases: a map with more pixels than the resident
+slots (152 SMs x 256) so slots refill from the queue, tiny maps that leave
+most slots and whole consumer warps idle, initial models, Hessian reuse,
+an iteration cap of 0 and 1, bad input pixels, the work counters, and the
+autotuner's tenth shape."""
+import numpy as np
+import pytest
+
+import workloads as W
+from gpu_common import LINE, T, X, vf  # noqa: F401
+
+pytestmark = pytest.mark.gpu
+
+
+def _map(v, h, torch, n, seed, bad=()):
+    dev = torch.device("cuda:0")
+    t = lambda a: torch.tensor(np.asarray(a, np.float32), device=dev)  # noqa: E731
+    p = W.quiet_and_active_params(n, seed)
+    tf, tx = t(T), t(X)
+    syn = v.vfisv_synth(h, t(p), tf, tx, LINE).reshape(n, 24)
+    sig = 1e-3 * t(W.continuum(p))[:, None]
+    obs = (syn + sig * t(W.noise(n, 24, seed))).contiguous()
+    w = (1.0 / (sig * sig)).expand(n, 24).contiguous()
+    for i in bad:
+        obs[i, 3] = float("nan")
+    torch.cuda.synchronize()
+    return p, obs, w, tf, tx
+
+
+def _both(v, h, obs, w, tf, tx, **kw):
+    out = []
+    for block in (128, 384):
+        v.vfisv_set_launch_shape(h, block, 1)
+        try:
+            v.vfisv_counters(h, reset=True)
+            r = v.vfisv_invert(h, obs, w, tf, tx, LINE, **kw)
+            v.vfisv_check(h)
+            out.append((r, v.vfisv_counters(h, reset=True)))
+        finally:
+            v.vfisv_set_launch_shape(h, 128, 1)
+    return out
+
+
+def _same(torch, a, b):
+    for k in a:
+        if a[k] is None:
+            assert b[k] is None
+            continue
+        assert torch.equal(a[k], b[k]), k
+
+
+@pytest.mark.parametrize("n", [1, 37, 300, 40077])
+def test_same_results_as_one_warpgroup_kernel(vf, n):
+    v, h, torch = vf
+    p, obs, w, tf, tx = _map(v, h, torch, n, 500 + n, bad=(0,) if n > 1 else ())
+    (a, ca), (b, cb) = _both(v, h, obs, w, tf, tx)
+    _same(torch, a, b)
+    assert ca == cb, (ca, cb)
+    assert cb["retired"] == n - (1 if n > 1 else 0)
+    if n > 1:
+        assert int(b["status"][0]) == 3  # the NaN pixel: bad input
+
+
+def test_same_results_with_initial_models_and_options(vf):
+    v, h, torch = vf
+    n = 5000
+    p, obs, w, tf, tx = _map(v, h, torch, n, 77)
+    init = torch.tensor(np.asarray(p, np.float32), device="cuda:0")
+    init[:, 0] *= 1.2
+    init[:, 3] *= 0.8
+    for cfg in ({"max_iter": 20}, {"hess_reuse": 1e-2}, {"max_iter": 0}, {"max_iter": 1}):
+        (a, ca), (b, cb) = _both(v, h, obs, w, tf, tx, init=init, config=cfg)
+        _same(torch, a, b)
+        assert ca == cb, (cfg, ca, cb)
+    (a, _), (b, _) = _both(v, h, obs, w, tf, tx, want_cov=False)
+    _same(torch, a, b)
+
+
+def test_configurations_it_does_not_take_fall_back(vf):
+    """fast_solve and restarts run the one-warpgroup kernel whatever the shape."""
+    v, h, torch = vf
+    p, obs, w, tf, tx = _map(v, h, torch, 2000, 91)
+    for cfg in ({"fast_solve": 1}, {"restarts": 1, "seed": 77, "max_iter": 30}):
+        (a, _), (b, _) = _both(v, h, obs, w, tf, tx, config=cfg)
+        _same(torch, a, b)
