@@ -107,6 +107,14 @@ FLOP_NORMAL_EQ = 24 * 30 + 24 * (9 + 2 * 54)
 # + 52 B written (model, chi2, counts); the extra writes are spilled
 # registers and the FP64 solve's call stack written back from L2.
 TRAFFIC_BYTES_PER_PIXEL = (54_240_512 + 153_698_048) / 262_144
+# The same for the warp-specialised LM kernel (invert_ws_kernel, the shape the
+# autotuner picks): one ncu capture on 1,048,576 pixels of the 1024^2
+# distributions (212.6 MB read + 119.2 MB write; profiles/invert_ws_kernel_1m_px.md):
+# 316 B per pixel, the extra writes over the algorithmic 52 B being the FP64
+# eigen fallback's stack and the consumers' few spills.
+TRAFFIC_BYTES_PER_PIXEL_WS = (212_609_280 + 119_202_048) / 1_048_576
+LM_KERNEL_FUSED = "invert_kernel<6>"
+LM_KERNEL_WS = "invert_ws_kernel<6> (warp-specialised)"
 
 
 def fp32_peak_tflops(sm_mhz: float, nsm: int = 152) -> float:
@@ -458,9 +466,9 @@ def run_ours(args, rank, world):
                  "(STALLED not counted)",
         "launch": {"cuda_graph": "whole map per step", "lm_threads_per_cta": best_block,
                    "lm_threads_per_pixel": best_tpp,
-                   "autotune_ms": {f"{t}x{b}": m for (t, b), m in
-                                   zip([(t, b) for t in (1, 2, 4) for b in (64, 128, 256)],
-                                       tune_ms)},
+                   "autotune_ms": {k: m for k, m in
+                                   zip([f"{t}x{b}" for t in (1, 2, 4) for b in (64, 128, 256)] +
+                                       ["ws384 (warp-specialised)"], tune_ms)},
                    "autotune_sample_pixels": ns},
         "routing": {"conf_route": conf_route, "calibration": calib},
         "converged_fraction": conv(out_m) / npix,
@@ -495,13 +503,19 @@ def run_ours(args, rank, world):
         "gpu_launches": None,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak,
-                     "traffic": int(TRAFFIC_BYTES_PER_PIXEL * npix),
-                     "traffic_note": "dram read+write bytes per launch, scaled by pixels from a "
-                                     "262,144-pixel ncu capture (793 B/px; algorithmic 244 "
-                                     "B/px: reads 207 vs 192, writes 586 B/px, mostly spilled "
-                                     "registers and the FP64 solve's call stack written back "
-                                     "from L2; ~6 GB/s over the launch)",
-                     "kernel": "invert_kernel<6> (plain LM pass, no covariance)",
+                     "traffic": int((TRAFFIC_BYTES_PER_PIXEL_WS if best_block == 384
+                                     else TRAFFIC_BYTES_PER_PIXEL) * npix),
+                     "traffic_note": ("dram read+write bytes per launch, scaled by pixels from a "
+                                      "1,048,576-pixel ncu capture of invert_ws_kernel (316 B/px; "
+                                      "algorithmic 244 B/px: reads 203 vs 192, writes 114 vs 52)"
+                                      if best_block == 384 else
+                                      "dram read+write bytes per launch, scaled by pixels from a "
+                                      "262,144-pixel ncu capture of invert_kernel (793 B/px; "
+                                      "algorithmic 244 B/px: reads 207 vs 192, writes 586 B/px, "
+                                      "mostly spilled registers and the FP64 solve's call stack "
+                                      "written back from L2)"),
+                     "kernel": (LM_KERNEL_WS if best_block == 384 else LM_KERNEL_FUSED) +
+                               " (plain LM pass, no covariance)",
                      "kernel_ms": ms_lm,
                      "work": work,
                      "flops_method": fl_method,

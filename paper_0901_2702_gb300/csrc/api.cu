@@ -392,6 +392,9 @@ struct DevInvert {
   unsigned long long *map_done = nullptr, *map_t = nullptr;
   // invert only the listed pixels (*npix_dev of them) of a map of npix
   const int64_t* pix_list = nullptr;
+  // leave each pixel's J^T W J parked in its covariance row (the caller runs
+  // the covariance kernel once over the final rows)
+  bool park_cov = false;
 };
 
 // Pack the filter table, zero the work queue, run the persistent LM kernel
@@ -458,7 +461,8 @@ int invert_device_wide(vfisv_handle* h, const DevInvert& d, int nfilt, int nlam,
   a.map_t = d.map_t;
   if (launch_wide_invert(a, nfilt, s) != cudaSuccess) return VFISV_E_CUDA;
   // the kernel parks each pixel's J^T W J in its covariance row
-  if (d.cov && launch_covariance(d.cov, d.status, npix, npix_dev, cfg->free_mask, 0, s) !=
+  if (d.cov && !d.park_cov &&
+      launch_covariance(d.cov, d.status, npix, npix_dev, cfg->free_mask, 0, s) !=
                    cudaSuccess)
     return VFISV_E_CUDA;
   return VFISV_OK;
@@ -542,8 +546,9 @@ int invert_device(vfisv_handle* h, const DevInvert& d, int nfilt, int nlam,
   if (launch_invert(a, nfilt, grid, block, tpp, smem, s) != cudaSuccess) return VFISV_E_CUDA;
   // with a pixel list the listed pixels lie anywhere in [0, npix): the
   // covariance kernel sweeps the whole map (it skips rows by status)
-  if (d.cov && launch_covariance(d.cov, d.status, npix, d.pix_list ? nullptr : npix_dev,
-                                cfg->free_mask, cfg->fast_solve, s) !=
+  if (d.cov && !d.park_cov &&
+      launch_covariance(d.cov, d.status, npix, d.pix_list ? nullptr : npix_dev, cfg->free_mask,
+                        cfg->fast_solve, s) !=
                    cudaSuccess)
     return VFISV_E_CUDA;
   return VFISV_OK;
@@ -1321,6 +1326,11 @@ int vfisv_invert_nn(vfisv_handle* h, const float* blob, const float* obs, const 
   d.iters = (int32_t*)st.bufs[7].dev;
   d.status = (int32_t*)st.bufs[8].dev;
   d.cov = (float*)st.bufs[9].dev;
+  // with the same solve settings in both runs the covariance is computed once,
+  // over the merged rows, from the J^T W J each run parks there
+  const bool one_cov = cov && cfg_nn->free_mask == cfg_plain->free_mask &&
+                       cfg_nn->fast_solve == cfg_plain->fast_solve;
+  d.park_cov = one_cov;
   int64_t* cnt = (int64_t*)(mw + o_cnt);
   int64_t* idx = (int64_t*)(mw + o_idx);
   const int64_t* n_first = nullptr;
@@ -1354,9 +1364,13 @@ int vfisv_invert_nn(vfisv_handle* h, const float* blob, const float* obs, const 
   d2.iters = (int32_t*)(mw + o_i);
   d2.status = (int32_t*)(mw + o_s);
   d2.cov = cov ? (float*)(mw + o_v) : nullptr;
+  d2.park_cov = one_cov;
   if ((rc = invert_device(h, d2, nfilt, nlam, line, cfg_plain, npix, cnt, s))) return rc;
   if (nn::merge_plain(cnt, idx, npix, d2.params, d2.chi2, d2.iters, d2.status, d2.cov, d.params,
                       d.chi2, d.iters, d.status, d.cov, s) != cudaSuccess)
+    return VFISV_E_CUDA;
+  if (one_cov && launch_covariance(d.cov, d.status, npix, nullptr, cfg_plain->free_mask,
+                                   cfg_plain->fast_solve, s) != cudaSuccess)
     return VFISV_E_CUDA;
   return st.finish(s);
 }

@@ -25,8 +25,8 @@
 // observables follow contiguously for the chi2.  Hand-offs are mbarriers
 // with bounded waits: full[b] (rows of batch b written), empty[b] (rows
 // read and the next trial models of batch b written).  Registers: the
-// producers raise their limit to 240 (the pass's accumulators without
-// spills), the consumers drop to 128 (setmaxnreg): three warps per
+// producers raise their limit to 232 (the pass's accumulators without
+// spills), the consumers drop to 136 (setmaxnreg): three warps per
 // sub-partition against two for invert_kernel.
 #include <math.h>
 
@@ -45,7 +45,7 @@ constexpr int kWsWarps = 12;
 constexpr int kWsThreadsN = kWsWarps * 32;
 constexpr int kWsBatches = 8;                  // consumer warps
 constexpr int kWsSlotsN = kWsBatches * 32;     // pixel slots per CTA
-constexpr int kWsProdRegs = 240, kWsConsRegs = 128;
+constexpr int kWsProdRegs = 232, kWsConsRegs = 136;
 constexpr int kWsTmemCols = 512;
 constexpr int kWsGroup = 8;                    // columns per (filter, Stokes) group
 constexpr int kWsBatchCols = 256;              // batch 1 of a producer starts here

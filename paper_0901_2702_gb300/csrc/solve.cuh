@@ -115,9 +115,11 @@ static __device__ __noinline__ void jacobi_pinv(const double* Mp /*packed*/, con
 }
 
 // In-place Cholesky of a packed 9x9 matrix; false if a pivot is not
-// comfortably positive (the matrix has unit-scale diagonal here).
+// comfortably positive (the matrix has unit-scale diagonal here).  The
+// diagonal receives the reciprocal pivots 1 / L_jj, which is all the
+// substitutions and the inverse use of it (one array fewer in registers).
 template <int N = kNP>
-__device__ __forceinline__ bool cholesky9(double (&L)[(N * (N + 1) / 2)], double (&ri)[N]) {
+__device__ __forceinline__ bool cholesky9(double (&L)[(N * (N + 1) / 2)]) {
 #pragma unroll
   for (int j = 0; j < N; ++j) {
     double d = L[tri(j, j)];
@@ -125,8 +127,7 @@ __device__ __forceinline__ bool cholesky9(double (&L)[(N * (N + 1) / 2)], double
     for (int k = 0; k < j; ++k) d = fma(-L[tri(j, k)], L[tri(j, k)], d);
     if (!(d > 1e-10)) return false;
     const double r = rsqrt(d);
-    ri[j] = r;
-    L[tri(j, j)] = d * r;
+    L[tri(j, j)] = r;
 #pragma unroll
     for (int i = j + 1; i < N; ++i) {
       double s = L[tri(i, j)];
@@ -138,33 +139,33 @@ __device__ __forceinline__ bool cholesky9(double (&L)[(N * (N + 1) / 2)], double
   return true;
 }
 
-// Forward and back substitution with the factor and its reciprocal pivots.
+// Forward and back substitution with the factor (reciprocal pivots on its
+// diagonal).
 template <int N = kNP>
-__device__ __forceinline__ void chol_solve9(const double (&L)[(N * (N + 1) / 2)], const double (&ri)[N],
-                                            double (&x)[N]) {
+__device__ __forceinline__ void chol_solve9(const double (&L)[(N * (N + 1) / 2)], double (&x)[N]) {
 #pragma unroll
   for (int i = 0; i < N; ++i) {
     double s = x[i];
 #pragma unroll
     for (int k = 0; k < i; ++k) s = fma(-L[tri(i, k)], x[k], s);
-    x[i] = s * ri[i];
+    x[i] = s * L[tri(i, i)];
   }
 #pragma unroll
   for (int i = N - 1; i >= 0; --i) {
     double s = x[i];
 #pragma unroll
     for (int k = i + 1; k < N; ++k) s = fma(-L[tri(k, i)], x[k], s);
-    x[i] = s * ri[i];
+    x[i] = s * L[tri(i, i)];
   }
 }
 
-// In place, from the Cholesky factor L (reciprocal pivots ri) of M: first
+// In place, from the Cholesky factor L (reciprocal pivots on its diagonal) of M: first
 // the triangular inverse W = L^-1 (columns right to left, each from the
 // already inverted trailing block), then M^-1 = W^T W (columns left to
 // right: entry (i, j) needs only rows >= i of columns j and i, which are
 // still W) -- ~285 FMAs against ~810 for N solves with unit vectors.
 template <int N = kNP>
-__device__ __forceinline__ void chol_inverse(double (&L)[(N * (N + 1) / 2)], const double (&ri)[N]) {
+__device__ __forceinline__ void chol_inverse(double (&L)[(N * (N + 1) / 2)]) {
 #pragma unroll
   for (int j = N - 1; j >= 0; --j) {
     // W[i][j] = -ri[j] * sum_{k=j+1..i} W[i][k] L[k][j]   (i > j)
@@ -173,9 +174,8 @@ __device__ __forceinline__ void chol_inverse(double (&L)[(N * (N + 1) / 2)], con
       double s = 0.0;
 #pragma unroll
       for (int k = j + 1; k <= i; ++k) s = fma(L[tri(i, k)], L[tri(k, j)], s);
-      L[tri(i, j)] = -s * ri[j];
+      L[tri(i, j)] = -s * L[tri(j, j)];
     }
-    L[tri(j, j)] = ri[j];
   }
 #pragma unroll
   for (int j = 0; j < N; ++j)
@@ -230,15 +230,16 @@ __device__ __forceinline__ void damped_step_fp64_body(const float* scr, int64_t 
                                                       uint32_t free_mask, double eps,
                                                       double (&delta)[N]) {
   double L[(N * (N + 1) / 2)];
-  int ex[N];  // P_ii = 2^-ex[i]
-  bool held[N];
+  int ex[N];         // P_ii = 2^-ex[i]
+  uint32_t hm = 0;   // bit i: parameter i held
 #pragma unroll
   for (int i = 0; i < N; ++i) {
     const float d = scr[(int64_t)tri(i, i) * ns];
-    held[i] = !((free_mask >> i) & 1u) || !(d > 0.0f) || !isfinite(d);
+    const bool h = !((free_mask >> i) & 1u) || !(d > 0.0f) || !isfinite(d);
+    hm |= (h ? 1u : 0u) << i;
     int k = 0;
-    frexpf(held[i] ? 1.0f : d, &k);  // d = m 2^k, m in [1/2, 1)
-    ex[i] = (k + 1) >> 1;            // d 2^-2ex in [1/4, 1)
+    frexpf(h ? 1.0f : d, &k);  // d = m 2^k, m in [1/2, 1)
+    ex[i] = (k + 1) >> 1;      // d 2^-2ex in [1/4, 1)
   }
   const double one_eps = 1.0 + eps;
   float pw[N];
@@ -248,32 +249,33 @@ __device__ __forceinline__ void damped_step_fp64_body(const float* scr, int64_t 
   for (int i = 0; i < N; ++i)
 #pragma unroll
     for (int j = 0; j <= i; ++j) {
+      const bool hi = (hm >> i) & 1u, hj = (hm >> j) & 1u;
       double m;
       if (i == j)
-        m = held[i] ? 1.0 : (double)(scr[(int64_t)tri(i, i) * ns] * pw[i] * pw[i]) * one_eps;
+        m = hi ? 1.0 : (double)(scr[(int64_t)tri(i, i) * ns] * pw[i] * pw[i]) * one_eps;
       else
-        m = (held[i] || held[j]) ? 0.0 : (double)(scr[(int64_t)tri(i, j) * ns] * pw[i] * pw[j]);
+        m = (hi || hj) ? 0.0 : (double)(scr[(int64_t)tri(i, j) * ns] * pw[i] * pw[j]);
       L[tri(i, j)] = m;
     }
   double y[N];
 #pragma unroll
   for (int i = 0; i < N; ++i)
-    y[i] = held[i] ? 0.0 : (double)(scr[(int64_t)((N * (N + 1) / 2) + i) * ns] * pw[i]);
-  double ri[N];
-  if (cholesky9<N>(L, ri)) {
-    chol_solve9<N>(L, ri, y);
+    y[i] = ((hm >> i) & 1u) ? 0.0 : (double)(scr[(int64_t)((N * (N + 1) / 2) + i) * ns] * pw[i]);
+  if (cholesky9<N>(L)) {
+    chol_solve9<N>(L, y);
 #pragma unroll
-    for (int i = 0; i < N; ++i) delta[i] = held[i] ? 0.0 : y[i] * pow2d(-ex[i]);
+    for (int i = 0; i < N; ++i) delta[i] = ((hm >> i) & 1u) ? 0.0 : y[i] * pow2d(-ex[i]);
     return;
   }
   // numerically singular: unit-diagonal Jacobi scaling, truncated
   // eigen-decomposition
-  double sc[N], b[N];
+  double sc[N], bv[N];
+  bool held[N];
   scaled_system<N>(scr, ns, free_mask, eps, L, sc, held);
 #pragma unroll
   for (int i = 0; i < N; ++i)
-    b[i] = held[i] ? 0.0 : (double)scr[(int64_t)((N * (N + 1) / 2) + i) * ns] * sc[i];
-  jacobi_pinv<N>(L, b, y, nullptr);
+    bv[i] = held[i] ? 0.0 : (double)scr[(int64_t)((N * (N + 1) / 2) + i) * ns] * sc[i];
+  jacobi_pinv<N>(L, bv, y, nullptr);
 #pragma unroll
   for (int i = 0; i < N; ++i) delta[i] = held[i] ? 0.0 : sc[i] * y[i];
 }
@@ -298,9 +300,8 @@ static __device__ __noinline__ bool covariance_fp64(const float* scr, int64_t ns
   double L[(N * (N + 1) / 2)], sc[N];
   bool held[N];
   scaled_system<N>(scr, ns, free_mask, 0.0, L, sc, held);
-  double ri[N];
-  if (cholesky9<N>(L, ri)) {
-    chol_inverse<N>(L, ri);  // L now holds the scaled inverse
+  if (cholesky9<N>(L)) {
+    chol_inverse<N>(L);  // L now holds the scaled inverse
   } else {
     if (try_only) return false;
     double P[(N * (N + 1) / 2)];
