@@ -330,8 +330,9 @@ int vfisv_check(vfisv_handle* h, void* stream);
  *   out[1] accepted trials, each followed by a J^T W J / J^T W r build
  *   out[2] pixels retired
  *   out[3] wavelength points evaluated: passes x grid points in use (the
- *          packed filter table leaves out points where every filter weight
- *          is below 2^-40 of the largest, which cannot change an FP32 sum)
+ *          packed filter table leaves out the grid points of least weight
+ *          while every filter keeps all but 2^-24 of its summed |weight|,
+ *          which moves a filtered value by at most one FP32 rounding)
  * Synchronises `stream` first; reset != 0 zeroes the counters afterwards.
  * Replays of a captured graph add to them like direct calls. */
 int vfisv_counters(vfisv_handle* h, void* stream, uint64_t* out, int32_t reset);  /* out[4] */
