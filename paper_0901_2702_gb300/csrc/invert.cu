@@ -663,17 +663,22 @@ __global__ void __launch_bounds__(BS, 1) invert_kernel(InvertArgs A) {
       const bool near = rel_acc < A.hess_reuse;
       const bool keepA = near && near_in;
       sNear[ps] = near;
-      auto fetch = [&](int k, int s, ObsRows& rw) {
-        const int sa = obs_sa(s), sb = obs_sb(s);
+      // rows from the lane's column of the dump buffer (shared memory)
+      struct {
+        const float* dump;
+        __device__ void issue(int, int) {}
+        __device__ void take(int k, int s, ObsRows& rw) {
+          const int sa = obs_sa(s), sb = obs_sb(s);
 #pragma unroll
-        for (int r = 0; r < kRows; ++r) {
-          rw.a[r] = D(r, sa, k);
-          rw.b[r] = D(r, sb, k);
+          for (int r = 0; r < kRows; ++r) {
+            rw.a[r] = dump[((r * 4 + sa) * NF + k) * 32];
+            rw.b[r] = dump[((r * 4 + sb) * NF + k) * 32];
+          }
+          if constexpr (AF)
+#pragma unroll
+            for (int r = 0; r < kNmRows; ++r) rw.n[r] = dump[(kRows * 4 * NF + r * NF + k) * 32];
         }
-        if constexpr (AF)
-#pragma unroll
-          for (int r = 0; r < kNmRows; ++r) rw.n[r] = N(r, k);
-      };
+      } fetch{dump};
       build_normal_equations<NF, NP, AF, false>(fetch, o, wv, tau, scr, ns, mus1, c2p, s2p, s0,
                                                 alf, A.lk.mu,
                                                 row_scale(A.lk, ST(sMt, 3), ST(sMt, 4)), keepA,

@@ -381,17 +381,24 @@ __device__ __forceinline__ bool ws_consumer(const InvertArgs& A, int b, uint32_t
     // whole warp takes part in the tensor-memory loads ----
     __syncwarp();
     if (__any_sync(0xffffffffu, accept)) {
-      auto fetch = [&](int k, int s, ObsRows& rw) {
+      // rows from tensor memory: the next observable's two loads are in
+      // flight while the current one is summed
+      struct {
+        uint32_t tc;
         uint32_t ra[8], rb[8];
-        tm_ld8(tc + (uint32_t)((k * 4 + obs_sa(s)) * kWsGroup), ra);
-        tm_ld8(tc + (uint32_t)((k * 4 + obs_sb(s)) * kWsGroup), rb);
-        tm_wait16(ra, rb);
-#pragma unroll
-        for (int r = 0; r < kRows; ++r) {
-          rw.a[r] = __uint_as_float(ra[r]);
-          rw.b[r] = __uint_as_float(rb[r]);
+        __device__ void issue(int k, int s) {
+          tm_ld8(tc + (uint32_t)((k * 4 + obs_sa(s)) * kWsGroup), ra);
+          tm_ld8(tc + (uint32_t)((k * 4 + obs_sb(s)) * kWsGroup), rb);
         }
-      };
+        __device__ void take(int, int, ObsRows& rw) {
+          tm_wait16(ra, rb);
+#pragma unroll
+          for (int r = 0; r < kRows; ++r) {
+            rw.a[r] = __uint_as_float(ra[r]);
+            rw.b[r] = __uint_as_float(rb[r]);
+          }
+        }
+      } fetch{tc, {}, {}};
       const RowScale R = row_scale(A.lk, live ? Mt[3 * kWsSlotsN] : 1.0f,
                                    live ? Mt[4 * kWsSlotsN] : 1.0f);
       build_normal_equations<NF, NP, false, true>(

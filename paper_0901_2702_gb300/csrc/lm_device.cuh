@@ -44,28 +44,29 @@ __device__ __forceinline__ int obs_sb(int s) { return (s == 0) ? 0 : (s == 3 ? 3
 
 // J^T W J (packed lower triangle, e < NPK) and J^T W r (after it) of the
 // 4 NF observables in compensated FP32 sums, written to scr[e * ns] where
-// `store` holds (J^T W J only without keepA).  fetch(k, s, rows) supplies
-// the filtered rows; psi, S0 and S1 enter after filtering.  With SPLIT the
-// sums are built in two passes over the observables (J^T W r and the first
-// rows of J^T W J, then the rest), half of them live at a time; the second
-// pass runs where `second` holds and recomputes the Jacobian rows.  The
-// observables run in runtime loops so the block stays small in the
-// instruction cache.
+// `store` holds (J^T W J only without keepA).  The filtered rows come from
+// `fetch`: fetch.issue(k, s) starts reading the rows of observable (Stokes
+// s, filter k) and fetch.take(k, s, rows) completes that read; the next
+// observable's read is issued before the current one is summed, so a
+// source with latency (tensor memory) overlaps the arithmetic.  psi, S0
+// and S1 enter after filtering.  With SPLIT the sums are built in two
+// passes over the observables (J^T W r and the first rows of J^T W J, then
+// the rest), half of them live at a time; the second pass runs where
+// `second` holds and recomputes the Jacobian rows.  The observables run in
+// a runtime loop so the block stays small in the instruction cache.
 template <int NF, int NP, bool AF, bool SPLIT, class Fetch>
 __device__ __forceinline__ void build_normal_equations(
-    Fetch&& fetch, const float* __restrict__ o, const float* __restrict__ wv,
+    Fetch& fetch, const float* __restrict__ o, const float* __restrict__ wv,
     const float* __restrict__ tau, float* __restrict__ scr, int64_t ns, float mus1, float c2p,
     float s2p, float s0, float alf, float mu, const RowScale& R, bool keepA, bool store,
     bool second) {
   constexpr int NPK = NP * (NP + 1) / 2;
   // Jacobian row and residual of observable (s, k): row r gives
   // fmaf(cA, a[r], cB * b[r]), the psi rotation of Q0/U0.
-  auto jac = [&](int k, int s, float (&J)[NP], float& rr, float& ww) {
+  auto jac = [&](int k, int s, const ObsRows& rows, float (&J)[NP], float& rr, float& ww) {
     constexpr int rowOf[10] = {kRowB, kRowG, -1, kRowE, kRowD, kRowA, kRowV, -1, -1, -1};
     // rows of the non-magnetic profile for eta0, dlambdaD, a, v (AF)
     constexpr int nmRowOf[10] = {-1, -1, -1, 1, 2, 3, 4, -1, -1, -1};
-    ObsRows rows;
-    fetch(k, s, rows);
     const float cA = (s == 1) ? c2p : (s == 2 ? s2p : 1.0f);
     const float cB = (s == 1) ? -s2p : (s == 2 ? c2p : 0.0f);
 #pragma unroll
@@ -101,22 +102,25 @@ __device__ __forceinline__ void build_normal_equations(
     Dot2 acc[NA];
 #pragma unroll
     for (int i = 0; i < NA; ++i) acc[i] = Dot2{0.0f, 0.0f};
+    // observables filter-major (k outer, s inner)
+    fetch.issue(0, 0);
 #pragma unroll 1
-    for (int k = 0; k < NF; ++k) {
-#pragma unroll 1
-      for (int s = 0; s < 4; ++s) {
-        float J[NP], rr, ww;
-        jac(k, s, J, rr, ww);
+    for (int i = 0; i < 4 * NF; ++i) {
+      const int k = i >> 2, s = i & 3;
+      ObsRows rows;
+      fetch.take(k, s, rows);
+      if (i + 1 < 4 * NF) fetch.issue((i + 1) >> 2, (i + 1) & 3);
+      float J[NP], rr, ww;
+      jac(k, s, rows, J, rr, ww);
 #pragma unroll
-        for (int p = 0; p < NP; ++p) {
-          const float wj = ww * J[p];
-          if constexpr (H != 1) acc[p].add(wj, rr);
+      for (int p = 0; p < NP; ++p) {
+        const float wj = ww * J[p];
+        if constexpr (H != 1) acc[p].add(wj, rr);
 #pragma unroll
-          for (int q = 0; q <= p; ++q) {
-            const int e = tri(p, q);
-            if (H != 1 && e < kSplit && !keepA) acc[NP + e].add(wj, J[q]);
-            if (H == 1 && e >= kSplit) acc[e - kSplit].add(wj, J[q]);
-          }
+        for (int q = 0; q <= p; ++q) {
+          const int e = tri(p, q);
+          if (H != 1 && e < kSplit && !keepA) acc[NP + e].add(wj, J[q]);
+          if (H == 1 && e >= kSplit) acc[e - kSplit].add(wj, J[q]);
         }
       }
     }
