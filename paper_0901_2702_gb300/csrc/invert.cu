@@ -666,8 +666,13 @@ __global__ void __launch_bounds__(BS, 1) invert_kernel(InvertArgs A) {
       // rows from the lane's column of the dump buffer (shared memory)
       struct {
         const float* dump;
-        __device__ void issue(int, int) {}
+        const float* o;
+        const float* wv;
+        ObsRead<NF> ov;
+        __device__ void issue(int k, int s) { ov.issue(o, wv, k, s); }
         __device__ void take(int k, int s, ObsRows& rw) {
+          rw.obs = ov.o;
+          rw.w = ov.w;
           const int sa = obs_sa(s), sb = obs_sb(s);
 #pragma unroll
           for (int r = 0; r < kRows; ++r) {
@@ -678,8 +683,8 @@ __global__ void __launch_bounds__(BS, 1) invert_kernel(InvertArgs A) {
 #pragma unroll
             for (int r = 0; r < kNmRows; ++r) rw.n[r] = dump[(kRows * 4 * NF + r * NF + k) * 32];
         }
-      } fetch{dump};
-      build_normal_equations<NF, NP, AF, false>(fetch, o, wv, tau, scr, ns, mus1, c2p, s2p, s0,
+      } fetch{dump, o, wv, {}};
+      build_normal_equations<NF, NP, AF, false>(fetch, tau, scr, ns, mus1, c2p, s2p, s0,
                                                 alf, A.lk.mu,
                                                 row_scale(A.lk, ST(sMt, 3), ST(sMt, 4)), keepA,
                                                 true, !keepA);

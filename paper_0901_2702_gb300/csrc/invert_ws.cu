@@ -385,12 +385,18 @@ __device__ __forceinline__ bool ws_consumer(const InvertArgs& A, int b, uint32_t
       // flight while the current one is summed
       struct {
         uint32_t tc;
+        const float* o;
+        const float* wv;
         uint32_t ra[8], rb[8];
+        ObsRead<NF> ov;
         __device__ void issue(int k, int s) {
           tm_ld8(tc + (uint32_t)((k * 4 + obs_sa(s)) * kWsGroup), ra);
           tm_ld8(tc + (uint32_t)((k * 4 + obs_sb(s)) * kWsGroup), rb);
+          ov.issue(o, wv, k, s);
         }
         __device__ void take(int, int, ObsRows& rw) {
+          rw.obs = ov.o;
+          rw.w = ov.w;
           tm_wait16(ra, rb);
 #pragma unroll
           for (int r = 0; r < kRows; ++r) {
@@ -398,11 +404,11 @@ __device__ __forceinline__ bool ws_consumer(const InvertArgs& A, int b, uint32_t
             rw.b[r] = __uint_as_float(rb[r]);
           }
         }
-      } fetch{tc, {}, {}};
+      } fetch{tc, o, wv, {}, {}, {}};
       const RowScale R = row_scale(A.lk, live ? Mt[3 * kWsSlotsN] : 1.0f,
                                    live ? Mt[4 * kWsSlotsN] : 1.0f);
       build_normal_equations<NF, NP, false, true>(
-          fetch, o, wv, tau, scr, ns, mus1, c2p, s2p, s0, 1.0f, A.lk.mu, R, keepA, accept,
+          fetch, tau, scr, ns, mus1, c2p, s2p, s0, 1.0f, A.lk.mu, R, keepA, accept,
           __any_sync(0xffffffffu, accept && !keepA));
     }
     if (live) {

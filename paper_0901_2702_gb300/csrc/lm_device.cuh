@@ -37,6 +37,19 @@ struct Half {
 struct ObsRows {
   float a[kRows], b[kRows];
   float n[kNmRows];
+  float obs, w;  // the observed value and its weight
+};
+
+// Observed value and weight of observable (s, k) of a pixel (row-major
+// [4][NF] rows o and wv), read by a row source's issue() with the rows.
+template <int NF>
+struct ObsRead {
+  float o, w;
+  __device__ __forceinline__ void issue(const float* __restrict__ obs,
+                                        const float* __restrict__ wv, int k, int s) {
+    o = obs[s * NF + k];
+    w = wv[s * NF + k];
+  }
 };
 
 __device__ __forceinline__ int obs_sa(int s) { return (s == 0) ? 0 : (s == 3 ? 3 : 1); }
@@ -46,7 +59,8 @@ __device__ __forceinline__ int obs_sb(int s) { return (s == 0) ? 0 : (s == 3 ? 3
 // 4 NF observables in compensated FP32 sums, written to scr[e * ns] where
 // `store` holds (J^T W J only without keepA).  The filtered rows come from
 // `fetch`: fetch.issue(k, s) starts reading the rows of observable (Stokes
-// s, filter k) and fetch.take(k, s, rows) completes that read; the next
+// s, filter k) with its observed value and weight, and fetch.take(k, s,
+// rows) completes that read; the next
 // observable's read is issued before the current one is summed, so a
 // source with latency (tensor memory) overlaps the arithmetic.  psi, S0
 // and S1 enter after filtering.  With SPLIT the sums are built in two
@@ -56,8 +70,7 @@ __device__ __forceinline__ int obs_sb(int s) { return (s == 0) ? 0 : (s == 3 ? 3
 // a runtime loop so the block stays small in the instruction cache.
 template <int NF, int NP, bool AF, bool SPLIT, class Fetch>
 __device__ __forceinline__ void build_normal_equations(
-    Fetch& fetch, const float* __restrict__ o, const float* __restrict__ wv,
-    const float* __restrict__ tau, float* __restrict__ scr, int64_t ns, float mus1, float c2p,
+    Fetch& fetch, const float* __restrict__ tau, float* __restrict__ scr, int64_t ns, float mus1, float c2p,
     float s2p, float s0, float alf, float mu, const RowScale& R, bool keepA, bool store,
     bool second) {
   constexpr int NPK = NP * (NP + 1) / 2;
@@ -90,9 +103,8 @@ __device__ __forceinline__ void build_normal_equations(
     J[8] = mu * lin;
     if constexpr (AF) J[NP - 1] = mus1 * ((s == 0) ? linm - rows.n[0] : linm);
     const float sv = (s == 0) ? fmaf(s0, tau[k], mus1 * lin) : mus1 * lin;
-    const int ob = s * NF + k;
-    ww = wv[ob];
-    rr = o[ob] - sv;
+    ww = rows.w;
+    rr = rows.obs - sv;
   };
   // J^T W J entries of pass 0 (all of them without the split: pass 2)
   constexpr int kSplit = SPLIT ? (NPK + NP) / 2 - NP : NPK;
