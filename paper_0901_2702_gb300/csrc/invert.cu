@@ -687,7 +687,7 @@ __global__ void __launch_bounds__(BS, 1) invert_kernel(InvertArgs A) {
       build_normal_equations<NF, NP, AF, false>(fetch, tau, scr, ns, mus1, c2p, s2p, s0,
                                                 alf, A.lk.mu,
                                                 row_scale(A.lk, ST(sMt, 3), ST(sMt, 4)), keepA,
-                                                true, !keepA);
+                                                true);
       if (RS && c2 < *rsBest) {
         // a new best over all segments: keep it with its normal equations
         *rsBest = c2;

@@ -408,8 +408,7 @@ __device__ __forceinline__ bool ws_consumer(const InvertArgs& A, int b, uint32_t
       const RowScale R = row_scale(A.lk, live ? Mt[3 * kWsSlotsN] : 1.0f,
                                    live ? Mt[4 * kWsSlotsN] : 1.0f);
       build_normal_equations<NF, NP, false, true>(
-          fetch, tau, scr, ns, mus1, c2p, s2p, s0, 1.0f, A.lk.mu, R, keepA, accept,
-          __any_sync(0xffffffffu, accept && !keepA));
+          fetch, tau, scr, ns, mus1, c2p, s2p, s0, 1.0f, A.lk.mu, R, keepA, accept);
     }
     if (live) {
       if (accept) {

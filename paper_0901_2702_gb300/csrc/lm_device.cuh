@@ -23,6 +23,32 @@ struct Dot2 {
   __device__ __forceinline__ float value() const { return s + c; }
 };
 
+// Two compensated sums advanced together by the packed FP32x2 instructions
+// of sm_100 and later: each lane performs exactly Dot2::add's IEEE
+// operations (the error term is carried negated: fma(-a, b, p) is
+// -(a b - p) with the same single rounding, and c - (-e) is c + e).
+__device__ __forceinline__ float2 fsub2(float2 a, float2 b) {
+  unsigned long long r;
+  asm("sub.rn.f32x2 %0, %1, %2;"
+      : "=l"(r)
+      : "l"(*reinterpret_cast<const unsigned long long*>(&a)),
+        "l"(*reinterpret_cast<const unsigned long long*>(&b)));
+  return *reinterpret_cast<const float2*>(&r);
+}
+
+struct Dot2x2 {
+  float2 s, c;
+  __device__ __forceinline__ void add(float2 a, float2 na, float2 b) {
+    const float2 p = __fmul2_rn(a, b);
+    const float2 e = __ffma2_rn(na, b, p);  // -(a b - p)
+    const float2 t = __fadd2_rn(s, p);
+    const float2 bp = fsub2(t, s);
+    const float2 es = __fadd2_rn(fsub2(s, fsub2(t, bp)), fsub2(p, bp));
+    s = t;
+    c = __fadd2_rn(c, fsub2(es, e));
+  }
+};
+
 // Compile-time index of a pass (template argument of a generic lambda).
 template <int H>
 struct Half {
@@ -64,15 +90,14 @@ __device__ __forceinline__ int obs_sb(int s) { return (s == 0) ? 0 : (s == 3 ? 3
 // observable's read is issued before the current one is summed, so a
 // source with latency (tensor memory) overlaps the arithmetic.  psi, S0
 // and S1 enter after filtering.  With SPLIT the sums are built in two
-// passes over the observables (J^T W r and the first rows of J^T W J, then
-// the rest), half of them live at a time; the second pass runs where
-// `second` holds and recomputes the Jacobian rows.  The observables run in
-// a runtime loop so the block stays small in the instruction cache.
+// passes over the observables (the first parameter rows, then the rest),
+// half of them live at a time; the second pass recomputes the Jacobian
+// rows.  The observables run in a runtime loop so the block stays small in
+// the instruction cache.
 template <int NF, int NP, bool AF, bool SPLIT, class Fetch>
 __device__ __forceinline__ void build_normal_equations(
     Fetch& fetch, const float* __restrict__ tau, float* __restrict__ scr, int64_t ns, float mus1, float c2p,
-    float s2p, float s0, float alf, float mu, const RowScale& R, bool keepA, bool store,
-    bool second) {
+    float s2p, float s0, float alf, float mu, const RowScale& R, bool keepA, bool store) {
   constexpr int NPK = NP * (NP + 1) / 2;
   // Jacobian row and residual of observable (s, k): row r gives
   // fmaf(cA, a[r], cB * b[r]), the psi rotation of Q0/U0.
@@ -106,14 +131,26 @@ __device__ __forceinline__ void build_normal_equations(
     ww = rows.w;
     rr = rows.obs - sv;
   };
-  // J^T W J entries of pass 0 (all of them without the split: pass 2)
-  constexpr int kSplit = SPLIT ? (NPK + NP) / 2 - NP : NPK;
+  // The sums of parameter row p are J^T W r_p and J^T W J_pq, q <= p: all
+  // take the product with w J_p, so they are advanced in pairs by packed
+  // instructions: (J^T W r_p, J^T W J_p0), (J^T W J_p1, J^T W J_p2), ...,
+  // the last pair of an odd row holding a lane that is not stored.  With
+  // SPLIT, pass 0 takes rows 0 .. PS - 1 and pass 1 the others (27 sums
+  // each for 9 parameters); otherwise one pass takes every row.
+  constexpr int NB = (NP + 2) / 2;                  // pairs of (r, J_0, ..., J_{NP-1})
+  constexpr int PS = SPLIT ? (NP == 9 ? 6 : NP) : NP;
+  auto pairs = [](int p) { return (p + 3) / 2; };  // pairs of row p
   auto build = [&](auto half) {
     constexpr int H = decltype(half)::value;
-    constexpr int NA = (H == 1) ? NPK - kSplit : NP + kSplit;
-    Dot2 acc[NA];
+    constexpr int P0 = (H == 1) ? PS : 0, P1 = (H == 0 && SPLIT) ? PS : NP;
+    constexpr int NS = [] {
+      int n = 0;
+      for (int p = P0; p < P1; ++p) n += (p + 3) / 2;
+      return n;
+    }();
+    Dot2x2 acc[NS];
 #pragma unroll
-    for (int i = 0; i < NA; ++i) acc[i] = Dot2{0.0f, 0.0f};
+    for (int i = 0; i < NS; ++i) acc[i] = Dot2x2{make_float2(0.0f, 0.0f), make_float2(0.0f, 0.0f)};
     // observables filter-major (k outer, s inner)
     fetch.issue(0, 0);
 #pragma unroll 1
@@ -124,37 +161,43 @@ __device__ __forceinline__ void build_normal_equations(
       if (i + 1 < 4 * NF) fetch.issue((i + 1) >> 2, (i + 1) & 3);
       float J[NP], rr, ww;
       jac(k, s, rows, J, rr, ww);
+      // (r, J_0), (J_1, J_2), ...; a lane past J_{NP-1} is zero
+      float2 bq[NB];
 #pragma unroll
-      for (int p = 0; p < NP; ++p) {
+      for (int m = 0; m < NB; ++m)
+        bq[m] = make_float2(m == 0 ? rr : J[2 * m - 1], (2 * m < NP) ? J[2 * m] : 0.0f);
+      int base = 0;
+#pragma unroll
+      for (int p = P0; p < P1; ++p) {
         const float wj = ww * J[p];
-        if constexpr (H != 1) acc[p].add(wj, rr);
+        const float2 a = make_float2(wj, wj), na = make_float2(-wj, -wj);
 #pragma unroll
-        for (int q = 0; q <= p; ++q) {
-          const int e = tri(p, q);
-          if (H != 1 && e < kSplit && !keepA) acc[NP + e].add(wj, J[q]);
-          if (H == 1 && e >= kSplit) acc[e - kSplit].add(wj, J[q]);
-        }
+        for (int m = 0; m < pairs(p); ++m) acc[base + m].add(a, na, bq[m]);
+        base += pairs(p);
       }
     }
-    if constexpr (H != 1) {
-      if (store) {
+    if (store) {
+      int base = 0;
 #pragma unroll
-        for (int i = 0; i < NP; ++i) scr[(int64_t)(NPK + i) * ns] = acc[i].value();
-        if (!keepA) {
+      for (int p = P0; p < P1; ++p) {
 #pragma unroll
-          for (int e = 0; e < kSplit; ++e) scr[(int64_t)e * ns] = acc[NP + e].value();
+        for (int m = 0; m < pairs(p); ++m) {
+          const Dot2x2& d = acc[base + m];
+          // lane x: J^T W r_p (m = 0) or J^T W J_p,2m-1; lane y: J^T W J_p,2m
+          const float vx = d.s.x + d.c.x, vy = d.s.y + d.c.y;
+          if (m == 0)
+            scr[(int64_t)(NPK + p) * ns] = vx;
+          else if (!keepA)
+            scr[(int64_t)tri(p, 2 * m - 1) * ns] = vx;
+          if (2 * m <= p && !keepA) scr[(int64_t)tri(p, 2 * m) * ns] = vy;
         }
-      }
-    } else {
-      if (store && !keepA) {
-#pragma unroll
-        for (int e = kSplit; e < NPK; ++e) scr[(int64_t)e * ns] = acc[e - kSplit].value();
+        base += pairs(p);
       }
     }
   };
   if constexpr (SPLIT) {
     build(Half<0>{});
-    if (second) build(Half<1>{});
+    build(Half<1>{});
   } else {
     build(Half<2>{});
   }
