@@ -49,16 +49,21 @@ constexpr int kWsProdRegs = 232, kWsConsRegs = 136;
 constexpr int kWsTmemCols = 512;
 constexpr int kWsGroup = 8;                    // columns per (filter, Stokes) group
 constexpr int kWsBatchCols = 256;              // batch 1 of a producer starts here
+constexpr int kFlagNear = 1, kFlagFresh = 2;
 
 // Shared memory after the filter table (byte offsets from the end of it).
 struct WsSmem {
-  size_t mt, m, scr, pix, fin, cnt, tslot, bars, tbar, total;
+  size_t mt, m, scr, pix, eps, chi2, it, flags, fin, cnt, tslot, bars, tbar, total;
   __host__ __device__ explicit WsSmem(int tabf) {
     size_t o = (size_t)tabf * 4;
     mt = o;   o += (size_t)10 * kWsSlotsN * 4;          // trial models [10][slots]
     m = o;    o += (size_t)10 * kWsSlotsN * 4;          // best models [10][slots]
     scr = o;  o += (size_t)(kNPk + kNP) * kWsSlotsN * 4;  // normal equations [54][slots]
     pix = o;  o += (size_t)kWsSlotsN * 8;               // pixel of each slot (-1: idle)
+    eps = o;  o += (size_t)kWsSlotsN * 8;               // damping
+    chi2 = o; o += (size_t)kWsSlotsN * 8;               // chi2 of the best model
+    it = o;   o += (size_t)kWsSlotsN * 4;               // iterations
+    flags = o; o += (size_t)kWsSlotsN * 4;              // kFlagNear | kFlagFresh
     fin = o;  o += 16 * 4;                               // batch finished flags
     cnt = o;  o += 4 * 8;                                // work counters
     tslot = o; o += 16;                                  // tensor-memory base address
@@ -208,6 +213,7 @@ template <int NF>
 __device__ __forceinline__ bool ws_consumer(const InvertArgs& A, int b, uint32_t tc,
                                             const float* __restrict__ tab, int nrows,
                                             float* sMt, float* sM, float* sScr, long long* sPix,
+                                            double* sEps, double* sChi, int* sIt, int* sFlags,
                                             int* fin, unsigned long long* cnt, uint32_t bar_full,
                                             uint32_t bar_empty) {
   constexpr int NOBS = 4 * NF;
@@ -222,10 +228,9 @@ __device__ __forceinline__ bool ws_consumer(const InvertArgs& A, int b, uint32_t
   const float* tau = tab + (size_t)A.nlam * table_stride(NF);
   const int dof = NOBS - A.nfree;
   const int64_t npix = A.npix_dev ? *A.npix_dev : A.npix;
+  // the slot's LM state stays in shared memory between passes (fewer live
+  // registers beside the FP64 solve)
   long long pix = -1;
-  int it = 0;
-  double chi2b = 0.0, eps = A.eps0;
-  bool near = false, fresh = false;
 
   // the next pixel of the queue into this slot: its starting model as the
   // trial model (bad inputs are answered on the spot); -1 when none is left
@@ -279,10 +284,9 @@ __device__ __forceinline__ bool ws_consumer(const InvertArgs& A, int b, uint32_t
 #pragma unroll
       for (int j = 0; j < 10; ++j) Mt[j * kWsSlotsN] = m[j];
       pix = pq;
-      it = 0;
-      eps = A.eps0;
-      near = false;
-      fresh = true;
+      sIt[slot] = 0;
+      sEps[slot] = A.eps0;
+      sFlags[slot] = kFlagFresh;
       return;
     }
   };
@@ -321,6 +325,9 @@ __device__ __forceinline__ bool ws_consumer(const InvertArgs& A, int b, uint32_t
     double c2 = 0.0;
     float c2p = 1.0f, s2p = 0.0f, mus1 = 0.0f, s0 = 0.0f;
     if (live) {
+      int it = sIt[slot], fl = sFlags[slot];
+      double eps = sEps[slot];
+      const double chi2b = sChi[slot];
       // ---- model, residual and chi-square (Eq. 1, FP64) ----
       sincosf(2.0f * Mt[2 * kWsSlotsN] * kDeg, &s2p, &c2p);
       mus1 = A.lk.mu * Mt[8 * kWsSlotsN];
@@ -344,7 +351,7 @@ __device__ __forceinline__ bool ws_consumer(const InvertArgs& A, int b, uint32_t
       atomicAdd(&cnt[0], 1ull);
       atomicAdd(&cnt[3], (unsigned long long)nrows);
       double rel_acc = INFINITY;
-      if (fresh) {
+      if (fl & kFlagFresh) {
         accept = isfinite(c2);
         if (!accept) {
           retire = true;
@@ -369,13 +376,19 @@ __device__ __forceinline__ bool ws_consumer(const InvertArgs& A, int b, uint32_t
         }
         if (accept) atomicAdd(&cnt[1], 1ull);
       }
+      fl &= ~kFlagFresh;
       if (accept) {
         // Hessian reuse (Sec. 4.4): this and the previous accepted step both
         // close to the minimum -> keep J^T W J, rebuild J^T W r only
         const bool nr = rel_acc < A.hess_reuse;
-        keepA = nr && near;
-        near = nr;
+        keepA = nr && (fl & kFlagNear);
+        fl = nr ? (fl | kFlagNear) : (fl & ~kFlagNear);
       }
+      if (!retire && it >= A.max_iter) retire = true;  // status stays MAXITER
+      sIt[slot] = it;
+      sEps[slot] = eps;
+      sFlags[slot] = fl;
+      if (accept) sChi[slot] = c2;
     }
     // ---- J^T W J and J^T W r at an accepted model (compensated FP32); the
     // whole warp takes part in the tensor-memory loads ----
@@ -414,16 +427,13 @@ __device__ __forceinline__ bool ws_consumer(const InvertArgs& A, int b, uint32_t
       if (accept) {
 #pragma unroll
         for (int j = 0; j < 10; ++j) M[j * kWsSlotsN] = Mt[j * kWsSlotsN];
-        chi2b = c2;
       }
-      fresh = false;
-      if (!retire && it >= A.max_iter) retire = true;  // status stays MAXITER
       if (retire) {
         const bool nan = status == VFISV_PIX_NAN_STATE;
         const float* src = nan ? Mt : M;
         for (int j = 0; j < 10; ++j) A.params_out[pix * 10 + j] = src[j * kWsSlotsN];
-        A.chi2_out[pix] = (float)(nan ? c2 : chi2b);
-        A.iters_out[pix] = it;
+        A.chi2_out[pix] = (float)(nan ? c2 : sChi[slot]);
+        A.iters_out[pix] = sIt[slot];
         A.status_out[pix] = status;
         if (A.cov_out) {
           // the covariance itself is computed by covariance_kernel for all
@@ -453,7 +463,7 @@ __device__ __forceinline__ bool ws_consumer(const InvertArgs& A, int b, uint32_t
       } else {
         // ---- next trial model: FP64 damped solve (Eqs. 3-5) ----
         double d[NP];
-        damped_step_fp64_body<NP>(scr, ns, A.free_mask, eps, d);
+        damped_step_fp64_body<NP, true>(scr, ns, A.free_mask, sEps[slot], d);
         float m[10];
 #pragma unroll
         for (int j = 0; j < NP; ++j) m[j] = (float)((double)M[j * kWsSlotsN] + d[j]);
@@ -485,6 +495,10 @@ __global__ void __launch_bounds__(kWsThreadsN, 1) invert_ws_kernel(InvertArgs A)
   float* sM = reinterpret_cast<float*>(base + L.m);
   float* sScr = reinterpret_cast<float*>(base + L.scr);
   long long* sPix = reinterpret_cast<long long*>(base + L.pix);
+  double* sEps = reinterpret_cast<double*>(base + L.eps);
+  double* sChi = reinterpret_cast<double*>(base + L.chi2);
+  int* sIt = reinterpret_cast<int*>(base + L.it);
+  int* sFlags = reinterpret_cast<int*>(base + L.flags);
   int* fin = reinterpret_cast<int*>(base + L.fin);
   unsigned long long* cnt = reinterpret_cast<unsigned long long*>(base + L.cnt);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(base + L.tslot);
@@ -523,8 +537,8 @@ __global__ void __launch_bounds__(kWsThreadsN, 1) invert_ws_kernel(InvertArgs A)
       const int b = warp - 4;  // batch: producer b % 4, its batch b / 4
       const uint32_t tc = tmem + ((uint32_t)(32 * (b & 3)) << 16) +
                           ((b >> 2) ? (uint32_t)kWsBatchCols : 0u);
-      good = ws_consumer<NF>(A, b, tc, tab, nrows, sMt, sM, sScr, sPix, fin, cnt, bar_full,
-                             bar_empty);
+      good = ws_consumer<NF>(A, b, tc, tab, nrows, sMt, sM, sScr, sPix, sEps, sChi, sIt, sFlags,
+                             fin, cnt, bar_full, bar_empty);
     }
   }
   if (!good) atomicExch(A.err, kDevErrWsWait);

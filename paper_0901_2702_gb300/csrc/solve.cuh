@@ -225,7 +225,10 @@ __device__ __forceinline__ void scaled_system(const float* scr, int64_t ns, uint
 // factorisation and the substitutions; the rare fallback (a pivot below
 // 1e-10) takes the unit-diagonal Jacobi scaling and the truncated
 // eigen-decomposition.
-template <int N = kNP>
+// LEAN: the scaling exponents are read again from scr for the last step
+// instead of staying live through the factorisation (for callers short of
+// registers; scr must not change meanwhile).
+template <int N = kNP, bool LEAN = false>
 __device__ __forceinline__ void damped_step_fp64_body(const float* scr, int64_t ns,
                                                       uint32_t free_mask, double eps,
                                                       double (&delta)[N]) {
@@ -263,6 +266,15 @@ __device__ __forceinline__ void damped_step_fp64_body(const float* scr, int64_t 
     y[i] = ((hm >> i) & 1u) ? 0.0 : (double)(scr[(int64_t)((N * (N + 1) / 2) + i) * ns] * pw[i]);
   if (cholesky9<N>(L)) {
     chol_solve9<N>(L, y);
+    if constexpr (LEAN) {
+      asm volatile("" ::: "memory");  // read the diagonal again (no register kept)
+#pragma unroll
+      for (int i = 0; i < N; ++i) {
+        int k = 0;
+        frexpf(((hm >> i) & 1u) ? 1.0f : scr[(int64_t)tri(i, i) * ns], &k);
+        ex[i] = (k + 1) >> 1;
+      }
+    }
 #pragma unroll
     for (int i = 0; i < N; ++i) delta[i] = ((hm >> i) & 1u) ? 0.0 : y[i] * pow2d(-ex[i]);
     return;
