@@ -109,10 +109,10 @@ FLOP_NORMAL_EQ = 24 * 30 + 24 * (9 + 2 * 54)
 TRAFFIC_BYTES_PER_PIXEL = (54_240_512 + 153_698_048) / 262_144
 # The same for the warp-specialised LM kernel (invert_ws_kernel, the shape the
 # autotuner picks): one ncu capture on 1,048,576 pixels of the 1024^2
-# distributions (212.6 MB read + 119.2 MB write; profiles/invert_ws_kernel_1m_px.md):
-# 316 B per pixel, the extra writes over the algorithmic 52 B being the FP64
-# eigen fallback's stack and the consumers' few spills.
-TRAFFIC_BYTES_PER_PIXEL_WS = (212_609_280 + 119_202_048) / 1_048_576
+# distributions (210.3 MB read + 92.8 MB write; profiles/invert_ws_kernel_1m_px.md):
+# 289 B per pixel, the extra writes over the algorithmic 52 B being the
+# consumers' spilled registers written back.
+TRAFFIC_BYTES_PER_PIXEL_WS = (210_325_504 + 92_827_392) / 1_048_576
 LM_KERNEL_FUSED = "invert_kernel<6>"
 LM_KERNEL_WS = "invert_ws_kernel<6> (warp-specialised)"
 
@@ -506,8 +506,8 @@ def run_ours(args, rank, world):
                      "traffic": int((TRAFFIC_BYTES_PER_PIXEL_WS if best_block == 384
                                      else TRAFFIC_BYTES_PER_PIXEL) * npix),
                      "traffic_note": ("dram read+write bytes per launch, scaled by pixels from a "
-                                      "1,048,576-pixel ncu capture of invert_ws_kernel (316 B/px; "
-                                      "algorithmic 244 B/px: reads 203 vs 192, writes 114 vs 52)"
+                                      "1,048,576-pixel ncu capture of invert_ws_kernel (289 B/px; "
+                                      "algorithmic 244 B/px: reads 201 vs 192, writes 89 vs 52)"
                                       if best_block == 384 else
                                       "dram read+write bytes per launch, scaled by pixels from a "
                                       "262,144-pixel ncu capture of invert_kernel (793 B/px; "
