@@ -22,9 +22,11 @@
 // sub-partition (warp id mod 4) and read the same lanes.  Within a batch's
 // range, the seven rows of Stokes s of filter k fill the 8-column group
 // k * 4 + s (row r at column r), and the unit-S1 Stokes values of all
-// observables follow contiguously for the chi2.  Hand-offs are mbarriers
-// with bounded waits: full[b] (rows of batch b written), empty[b] (rows
-// read and the next trial models of batch b written).  Registers: the
+// observables follow contiguously for the chi2.  The slots' LM state
+// (models, normal equations, damping, best chi2, iteration, flags) lives in
+// shared memory.  Hand-offs are mbarriers with bounded waits: full[b] (rows
+// of batch b written), empty[b] (rows read and the next trial models of
+// batch b written).  Registers: the
 // producers raise their limit to 232 (the pass's accumulators without
 // spills), the consumers drop to 136 (setmaxnreg): three warps per
 // sub-partition against two for invert_kernel.
@@ -51,7 +53,8 @@ constexpr int kWsGroup = 8;                    // columns per (filter, Stokes) g
 constexpr int kWsBatchCols = 256;              // batch 1 of a producer starts here
 constexpr int kFlagNear = 1, kFlagFresh = 2;
 
-// Shared memory after the filter table (byte offsets from the end of it).
+// Shared-memory layout: the filter table, then these arrays (byte offsets
+// from the start of shared memory), structure of arrays over the slots.
 struct WsSmem {
   size_t mt, m, scr, pix, eps, chi2, it, flags, fin, cnt, tslot, bars, tbar, total;
   __host__ __device__ explicit WsSmem(int tabf) {
