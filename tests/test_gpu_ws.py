@@ -7,8 +7,8 @@ agree bit for bit; parity with the oracle then carries over from the tests
 of the 128 x 1 kernel.  Cases: a map with more pixels than the resident
 slots (152 SMs x 256) so slots refill from the queue, tiny maps that leave
 most slots and whole consumer warps idle, initial models, Hessian reuse,
-an iteration cap of 0 and 1, bad input pixels, the work counters, and the
-autotuner's tenth shape."""
+an iteration cap of 0 and 1, bad input pixels, the work counters, a handle
+limited to fewer SMs, and graph replay."""
 import numpy as np
 import pytest
 
@@ -89,3 +89,45 @@ def test_configurations_it_does_not_take_fall_back(vf):
     for cfg in ({"fast_solve": 1}, {"restarts": 1, "seed": 77, "max_iter": 30}):
         (a, _), (b, _) = _both(v, h, obs, w, tf, tx, config=cfg)
         _same(torch, a, b)
+
+
+def test_sm_limit_and_graph_replay(vf):
+    """Execution-only changes with the warp-specialised shape: a handle
+    limited to 19 SMs (fewer CTAs, the same queue) and a captured graph
+    replayed on new observations give the unlimited direct call's results
+    bit for bit."""
+    v, h, torch = vf
+    n = 20000
+    p, obs, w, tf, tx = _map(v, h, torch, n, 71)
+    _, obs2, _, _, _ = _map(v, h, torch, n, 72)
+    v.vfisv_set_launch_shape(h, 384, 1)
+    try:
+        ref = v.vfisv_invert(h, obs, w, tf, tx, LINE)
+        v.vfisv_set_sm_limit(h, 19)
+        try:
+            lim = v.vfisv_invert(h, obs, w, tf, tx, LINE)
+            v.vfisv_check(h)
+        finally:
+            v.vfisv_set_sm_limit(h, 0)
+        _same(torch, ref, lim)
+        dev = torch.device("cuda:0")
+        s = torch.cuda.Stream(dev)
+        out = {k: torch.empty_like(t_) for k, t_ in ref.items()}
+        src = obs.clone()
+        with torch.cuda.stream(s):
+            v.vfisv_invert(h, src, w, tf, tx, LINE, out=out, stream=s)  # sizes the workspaces
+            s.synchronize()
+            v.vfisv_graph_begin(h, s)
+            v.vfisv_invert(h, src, w, tf, tx, LINE, out=out, stream=s)
+            g = v.vfisv_graph_end(h, s)
+            for data in (obs, obs2):
+                src.copy_(data)
+                g.launch(s)
+                s.synchronize()
+                direct = v.vfisv_invert(h, data, w, tf, tx, LINE, stream=s)
+                s.synchronize()
+                _same(torch, out, direct)
+        g.close()
+        v.vfisv_check(h)
+    finally:
+        v.vfisv_set_launch_shape(h, 128, 1)
