@@ -724,6 +724,11 @@ def run_serving(args):
         v.vfisv_invert_batch(hS, obsS, wS, offS, tfS, txS, W.FE6302, config=cfgS, out=oS,
                              stream=sS)
 
+    # the filtergram half's LM launch shape, tuned on its largest map (the
+    # tail of the smallest-first queue) with that map's weights
+    ntune = min(nF, 1 << 18)
+    shapeF = v.vfisv_autotune(hF, obsF[nF - ntune:], wF[-1], tfF, txF, W.FE6173, config=cfg,
+                              stream=sF)[:2]
     for _ in range(max(1, args.warmup)):
         stepF()
         stepS()
@@ -805,7 +810,9 @@ def run_serving(args):
                                      "captured CUDA graph, on two concurrent streams; maps "
                                      "queued smallest first",
                       "sm_split": {"filter": smF, "spectrograph": smS,
-                                   "alone_ms": {"filter": tF, "spectrograph": tS}}},
+                                   "alone_ms": {"filter": tF, "spectrograph": tS}},
+                      "filter_lm_launch": {"threads_per_cta": int(shapeF[0]),
+                                           "threads_per_pixel": int(shapeF[1])}},
            "converged_fraction": {"filter": cF / max(nF, 1), "spectrograph": cS / max(nS, 1)},
            "latency_ms": {"p50": float(np.percentile(lat, 50)),
                           "p99": float(np.percentile(lat, 99)),

@@ -131,3 +131,31 @@ def test_sm_limit_and_graph_replay(vf):
         v.vfisv_check(h)
     finally:
         v.vfisv_set_launch_shape(h, 128, 1)
+
+
+def test_batched_maps_same_results(vf):
+    """Many maps in one launch (vfisv_invert_batch, per-map weights and
+    completion stamps) with the warp-specialised shape: the per-pixel outputs
+    equal the one-warpgroup kernel's bit for bit, every map gets a stamp."""
+    v, h, torch = vf
+    sizes = [1, 700, 33, 5000, 129]
+    parts = [_map(v, h, torch, n, 900 + i) for i, n in enumerate(sizes)]
+    obs = torch.cat([q[1] for q in parts]).contiguous()
+    w = torch.stack([q[2][0] * (1.0 + 0.1 * i) for i, q in enumerate(parts)]).contiguous()
+    tf, tx = parts[0][3], parts[0][4]
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    res = []
+    for block in (128, 384):
+        v.vfisv_set_launch_shape(h, block, 1)
+        try:
+            r = v.vfisv_invert_batch(h, obs, w, off, tf, tx, LINE)
+            v.vfisv_check(h)
+            res.append(r)
+        finally:
+            v.vfisv_set_launch_shape(h, 128, 1)
+    a, b = res
+    for k in a:
+        if k == "latency_ms":
+            assert bool((b[k] > 0).all()), b[k]
+            continue
+        assert torch.equal(a[k], b[k]), k
