@@ -8,7 +8,8 @@ of the 128 x 1 kernel.  Cases: a map with more pixels than the resident
 slots (152 SMs x 256) so slots refill from the queue, tiny maps that leave
 most slots and whole consumer warps idle, initial models, Hessian reuse,
 an iteration cap of 0 and 1, bad input pixels, the work counters, a handle
-limited to fewer SMs, and graph replay."""
+limited to fewer SMs, graph replay, batched maps, and the mixed inversion
+with confidence routing (pixel list and device-side count)."""
 import numpy as np
 import pytest
 
@@ -159,3 +160,36 @@ def test_batched_maps_same_results(vf):
             assert bool((b[k] > 0).all()), b[k]
             continue
         assert torch.equal(a[k], b[k]), k
+
+
+def test_mixed_inversion_with_routing_same_results(vf):
+    """The mixed inversion (network guess, confidence routing to plain LM
+    through the LM kernel's device-side pixel list and count, flagged pixels
+    re-inverted, one covariance pass over the merged rows) with the
+    warp-specialised shape equals the one-warpgroup kernel's bit for bit.
+    An untrained network serves: only the equality of the two shapes is
+    tested, whatever it routes."""
+    v, h, torch = vf
+    n = 6000
+    p, obs, w, tf, tx = _map(v, h, torch, n, 131)
+    blob = v.vfisv_nn_init(h, obs, torch.tensor(np.asarray(p, np.float32), device="cuda:0"),
+                           seed=5)
+    conf = v.vfisv_nn_infer(h, blob, obs, LINE)["conf"]
+    k = float(conf.median().item())  # about half the pixels routed
+    res = []
+    for block in (128, 384):
+        v.vfisv_set_launch_shape(h, block, 1)
+        try:
+            r = v.vfisv_invert_nn(h, blob, obs, w, tf, tx, LINE, config_nn={"max_iter": 20},
+                                  config_plain={"max_iter": 50}, chi2_flag=3.0,
+                                  flag_unconverged=True, conf_route=k)
+            v.vfisv_check(h)
+            res.append(r)
+        finally:
+            v.vfisv_set_launch_shape(h, 128, 1)
+    a, b = res
+    assert 0.2 < float((conf > k).float().mean().item()) < 0.8
+    for key in a:
+        if a[key] is None:
+            continue
+        assert torch.equal(a[key], b[key]), key
