@@ -91,14 +91,18 @@ __device__ __forceinline__ bool ws_try(uint32_t bar, uint32_t parity) {
   return done != 0;
 }
 
-// Wait for the phase of parity `parity`; false after ~1 s.
+// Wait for the phase of parity `parity`; false after ~1 s.  Called by whole
+// warps, and the answer is the warp's: a lane that reaches the limit just as
+// another sees the phase complete must not split the warp ahead of the
+// warp-wide tensor-memory instructions that follow.
 __device__ __forceinline__ bool ws_wait(uint32_t bar, uint32_t parity) {
   const long long t0 = clock64();
-  for (int it = 0; it < (1 << 26); ++it) {
-    if (ws_try(bar, parity)) return true;
-    if (clock64() - t0 > (1ll << 31)) return false;
+  bool ok = false;
+  for (int it = 0; it < (1 << 26) && !ok; ++it) {
+    ok = ws_try(bar, parity);
+    if (!ok && clock64() - t0 > (1ll << 31)) break;
   }
-  return false;
+  return __all_sync(0xffffffffu, ok) != 0;
 }
 
 __device__ __forceinline__ void tc_before() {
