@@ -52,6 +52,14 @@ constexpr int kWsTmemCols = 512;
 constexpr int kWsGroup = 8;                    // columns per (filter, Stokes) group
 constexpr int kWsBatchCols = 256;              // batch 1 of a producer starts here
 constexpr int kFlagNear = 1, kFlagFresh = 2;
+static_assert(kWsWarps == 4 + kWsBatches, "one producer warp per sub-partition");
+static_assert(kWsBatches == 8, "each producer warp serves two consumer warps");
+// a batch's 7-row groups and its row-0 copy fit its column range, and both
+// batches fit the allocation (a power of two, at most 512 columns)
+static_assert(4 * 6 * kWsGroup + 4 * 6 <= kWsBatchCols, "batch columns");
+static_assert(kWsBatchCols + 4 * 6 * kWsGroup + 4 * 6 <= kWsTmemCols && kWsTmemCols <= 512,
+              "tensor-memory columns");
+static_assert(kWsProdRegs % 8 == 0 && kWsConsRegs % 8 == 0, "setmaxnreg counts");
 
 // Shared-memory layout: the filter table, then these arrays (byte offsets
 // from the start of shared memory), structure of arrays over the slots.
@@ -580,6 +588,15 @@ cudaError_t invert_ws_slots(int nlam, int64_t npix, int64_t* nslots, int* grid, 
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, invert_ws_kernel<6>, kWsThreadsN, sm);
   if (e != cudaSuccess) return e;
   if (per < 1) return cudaErrorLaunchOutOfResources;
+  // setmaxnreg moves registers within the CTA's launch allocation: the
+  // producers' raise waits for registers the consumers' drop frees, so the
+  // split must fit the registers the kernel is launched with
+  cudaFuncAttributes fa;
+  e = cudaFuncGetAttributes(&fa, invert_ws_kernel<6>);
+  if (e != cudaSuccess) return e;
+  if ((int64_t)fa.numRegs * kWsThreadsN <
+      (int64_t)32 * (4 * kWsProdRegs + kWsBatches * kWsConsRegs))
+    return cudaErrorInvalidConfiguration;
   int64_t g = nsm;  // one CTA per SM (it holds all of the SM's tensor memory)
   const int64_t need = (npix + kWsSlotsN - 1) / kWsSlotsN;
   if (need < g) g = need;
