@@ -320,7 +320,14 @@ int vfisv_set_sm_limit(vfisv_handle* h, int32_t nsm);
 int vfisv_set_pipeline_chunks(vfisv_handle* h, int32_t chunks);
 
 /* Synchronise `stream` and report any error a kernel of this handle flagged
- * on the device since the last check (VFISV_E_DEVICE) or a CUDA error. */
+ * on the device since the last check (VFISV_E_DEVICE) or a CUDA error.  A
+ * device error is a bounded wait (about a second) that gave up: the filter
+ * table's copy into shared memory, a network operand copy or tensor-core
+ * completion, a filtered-row buffer of the one-warpgroup LM kernel, or a
+ * producer/consumer hand-off of the warp-specialised LM kernel.  The kernel
+ * then stops and returns, so the context stays usable, but the outputs of
+ * the calls since the last check are not valid.  The error words are
+ * cleared. */
 int vfisv_check(vfisv_handle* h, void* stream);
 
 /* Work done by this handle's filter-position LM launches (nfilt = 6; the
