@@ -503,17 +503,19 @@ def run_ours(args, rank, world):
         "gpu_launches": None,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak,
-                     "traffic": int((TRAFFIC_BYTES_PER_PIXEL_WS if best_block == 384
-                                     else TRAFFIC_BYTES_PER_PIXEL) * npix),
-                     "traffic_note": ("dram read+write bytes per launch, scaled by pixels from a "
-                                      "1,048,576-pixel ncu capture of invert_ws_kernel (289 B/px; "
-                                      "algorithmic 244 B/px: reads 201 vs 192, writes 89 vs 52)"
-                                      if best_block == 384 else
-                                      "dram read+write bytes per launch, scaled by pixels from a "
-                                      "262,144-pixel ncu capture of invert_kernel (793 B/px; "
-                                      "algorithmic 244 B/px: reads 207 vs 192, writes 586 B/px, "
-                                      "mostly spilled registers and the FP64 solve's call stack "
-                                      "written back from L2)"),
+                     "traffic": None,
+                     "traffic_note": (
+                         "null: the kernel changed after its last ncu capture (its barrier "
+                         "wait now returns the warp's vote; no memory access changed); that "
+                         f"capture of 1,048,576 pixels read+wrote {TRAFFIC_BYTES_PER_PIXEL_WS:.0f} "
+                         "B/px against the algorithmic 244 (reads 201 vs 192, writes 89 vs 52), "
+                         f"{TRAFFIC_BYTES_PER_PIXEL_WS * npix:.3g} B for this launch"
+                         if best_block == 384 else
+                         "null: the kernel changed after its last ncu capture (63-point table, "
+                         "normal-equation changes); that capture of 262,144 pixels at 79 points "
+                         f"read+wrote {TRAFFIC_BYTES_PER_PIXEL:.0f} B/px against the algorithmic "
+                         "244, mostly spilled registers and the FP64 solve's call stack written "
+                         "back from L2"),
                      "kernel": (LM_KERNEL_WS if best_block == 384 else LM_KERNEL_FUSED) +
                                " (plain LM pass, no covariance)",
                      "kernel_ms": ms_lm,
